@@ -1,0 +1,55 @@
+"""Every plausible mistake planted in a copy of the oracle must fail some pin.
+
+Each mutant is the committed oracle source with one textual change (a wrong
+sign, a transposed index, convolution instead of correlation, a dropped term,
+a wrong border rule, ...), compiled into a temporary library.  The pins of
+``oracle_checks.py`` are then run on it; at least one must fail.  This shows
+the pins are strong enough to catch the mistakes they are meant to catch.
+"""
+import os
+
+import pytest
+
+import oracle
+import oracle_checks as oc
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "sobel4_oracle.c")
+
+MUTANTS = {
+    "gd_sign_flip": ("{-2, 0, 8, 12, 4},", "{-2, 0, 8, 12, -4},"),
+    "gx_swapped_taps": ("{-4, -8, 0, 8, 4},\n     {-6", "{-8, -4, 0, 8, 4},\n     {-6"),
+    "gdt_row_swap": ("{2, 0, -8, -12, -4},", "{0, 2, -8, -12, -4},"),
+    "transposed_mask": ("ORACLE_MASKS[k][i][j] * v", "ORACLE_MASKS[k][j][i] * v"),
+    "convolution_order": ("read_pixel(src, sp, H, W, y + i - 2, x + j - 2, border)",
+                          "read_pixel(src, sp, H, W, y - i + 2, x - j + 2, border)"),
+    "row_offset": ("sp, H, W, y + i - 2, x + j - 2, border);", "sp, H, W, y + i - 1, x + j - 2, border);"),
+    "dropped_dt_term": ("+ r[3] * r[3];", ";"),
+    "reflect_not_101": ("if (i < 0) return -i;", "if (i < 0) return -i - 1;"),
+    "replicate_edge": ("return i < 0 ? 0 : n - 1;", "return i < 0 ? 0 : n - 2;"),
+    "constant_reads_edge": ("case OR_CONSTANT0:\n      return -1;", "case OR_CONSTANT0:\n      return i < 0 ? 0 : n - 1;"),
+    "valid_frame_off_by_one": ("y <= H - 3 && x >= 2", "y <= H - 2 && x >= 2"),
+    "sqrt_in_double": ("((float *)row)[x] = sqrtf((float)s);",
+                       "((float *)row)[x] = (float)sqrt((double)s);"),
+    "u8_truncates": ("if ((uint32_t)s > n * n + n) n += 1;", "if ((uint32_t)s > n * n) n += 0;"),
+    "u8_no_saturation": ("return (uint8_t)(n > 255u ? 255u : n);", "return (uint8_t)n;"),
+    "s16_plane_stride": ("(size_t)k * (size_t)jb->H * jb->dp", "(size_t)k * (size_t)jb->W * jb->dp"),
+    "band_split_gap": ("(int)((int64_t)H * (t + 1) / nthreads)}", "(int)((int64_t)H * (t + 1) / nthreads) - (t + 1 < nthreads)}"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    before, after = MUTANTS[name]
+    text = open(SRC).read()
+    assert text.count(before) == 1, f"mutation site for {name} not found exactly once"
+    src = tmp_path / "mutant.c"
+    src.write_text(text.replace(before, after))
+    lib = oracle.build(str(src), str(tmp_path / "libmutant.so"), force=True)
+    o = oracle.Oracle(lib)
+    failed = []
+    for check in oc.ALL_CHECKS:
+        try:
+            check(o)
+        except (AssertionError, ValueError):
+            failed.append(check.__name__)
+    assert failed, f"no pin caught mutant {name}"
