@@ -1,0 +1,182 @@
+/*
+ * sobel4.h — C ABI of the GB300 (sm_103a) four-directional 5x5 Sobel library.
+ *
+ * The operator (Section 3.1 of "Multi-directional Sobel operator kernel on
+ * GPUs"): for every pixel of an 8-bit grayscale image, the four 5x5 integer
+ * masks G_x, G_y, G_d, G_dt of Eq. (3) are applied in correlation order
+ * (mask row 0 meets input row y-2, mask column 0 meets input column x-2, the
+ * orientation of Eq. (6) and Eq. (13)), giving the responses
+ *     R_k(y,x) = sum_{i,j} K_k[i][j] * I(y+i-2, x+j-2),  k in {x, y, d, dt},
+ * and the magnitude of Eq. (4),
+ *     G = sqrt(R_x^2 + R_y^2 + R_d^2 + R_dt^2).
+ * All integer work is exact (|R_k| <= 12240, S = sum R_k^2 <= 599,270,400).
+ * The F32 output is sqrtf((float)S): int -> fp32 round-to-nearest-even, then
+ * the IEEE-754 correctly rounded single-precision square root.  It matches a
+ * plain CPU evaluation of that definition bit for bit.
+ *
+ * Conventions for every entry point below:
+ *  - Image pointers passed to sobel4_run / sobel4_run_batched are DEVICE
+ *    pointers owned by the caller.  A handle owns only its own scratch.
+ *  - Calls that take a cudaStream_t are asynchronous: they validate their
+ *    arguments on the host, enqueue work on `stream` (0 = legacy default
+ *    stream) and return.  A call that returns an error enqueued nothing.
+ *  - Device faults surface on the caller's next synchronisation, as with any
+ *    CUDA library.
+ *  - One handle per host thread, or serialise calls on a handle externally.
+ */
+#ifndef SOBEL4_H_
+#define SOBEL4_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifndef __DRIVER_TYPES_H__
+struct CUstream_st;
+typedef struct CUstream_st *cudaStream_t;
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque handle; created by sobel4_create, released by sobel4_destroy. */
+typedef struct sobel4_ctx *sobel4_handle;
+
+typedef enum {
+  SOBEL4_OK = 0,
+  SOBEL4_ERR_INVALID_ARG = 1, /* an argument broke a rule stated below */
+  SOBEL4_ERR_UNSUPPORTED = 2, /* valid request this build cannot serve */
+  SOBEL4_ERR_OOM = 3,         /* device or pinned host allocation failed */
+  SOBEL4_ERR_CUDA = 4,        /* a CUDA call failed; see sobel4_last_cuda_error */
+  SOBEL4_ERR_TIMEOUT = 5      /* a bounded wait ran out */
+} sobel4_status;
+
+/*
+ * Border rules.  VALID is the paper's: the kernel output is 2r = 4 rows and
+ * columns smaller than its input (Section 4.3.2); here the 2-pixel frame is
+ * written as 0 so input and output have the same shape.  The three padded
+ * rules evaluate every pixel with the missing neighbours supplied by:
+ *   REPLICATE  : the nearest edge pixel (indices clamped),
+ *   REFLECT101 : reflection about the edge pixel (-1 -> 1, -2 -> 2,
+ *                n -> n-2, n+1 -> n-3); needs height, width >= 3,
+ *   CONSTANT0  : zeros.
+ */
+typedef enum {
+  SOBEL4_BORDER_VALID = 0,
+  SOBEL4_BORDER_REPLICATE = 1,
+  SOBEL4_BORDER_REFLECT101 = 2,
+  SOBEL4_BORDER_CONSTANT0 = 3
+} sobel4_border;
+
+/*
+ * Output formats (dst element type and layout; rows are dst_pitch bytes apart):
+ *   F32   : float G = sqrtf((float)S), 4 bytes per pixel.
+ *   U8    : uint8 min(255, round(sqrt(S))), 1 byte per pixel.
+ *   S16X4 : the four responses R_x, R_y, R_d, R_dt as int16, in four planes;
+ *           plane k starts at dst + k * height * dst_pitch.
+ */
+typedef enum { SOBEL4_OUT_F32 = 0, SOBEL4_OUT_U8 = 1, SOBEL4_OUT_S16X4 = 2 } sobel4_format;
+
+/*
+ * Kernel variants.  AUTO picks the fastest for the request (autotuned when
+ * enabled).  DIRECT evaluates the 25-tap sums of Eq. (3) per output pixel from
+ * global memory (the paper's "GM" kernel, Section 5.2).  RG is the
+ * register-window kernel (Section 4.3): threads across columns, rows walked
+ * sequentially, the x/y masks factored into 1x5 passes (Eq. 6-7), the
+ * diagonals through K_d+ / K_d- (Eq. 10-19), next rows prefetched.
+ */
+typedef enum { SOBEL4_VARIANT_AUTO = 0, SOBEL4_VARIANT_DIRECT = 1, SOBEL4_VARIANT_RG = 2 } sobel4_variant;
+
+/* Creation options; pass NULL for defaults (all fields 0). */
+typedef struct {
+  int32_t variant;               /* sobel4_variant; 0 = AUTO */
+  int32_t rows_per_strip;        /* RG strip height R (rows per thread per strip); 0 = auto */
+  int32_t persistent_ctas_per_sm;/* batched kernel CTAs per SM; 0 = auto */
+  int32_t reserved;              /* must be 0 */
+} sobel4_options;
+
+/* One image of a batch (all pointers are device pointers). */
+typedef struct {
+  const uint8_t *src; /* height rows of width bytes, src_pitch bytes apart */
+  size_t src_pitch;
+  void *dst;          /* output in the batch's format, dst_pitch bytes apart */
+  size_t dst_pitch;
+  int32_t height;
+  int32_t width;
+} sobel4_image;
+
+/*
+ * Create a handle bound to CUDA device `device` (made current for the call).
+ * `opt` may be NULL.  Allocates the handle's scratch (a small device buffer
+ * for batch descriptors and the work-queue counter, and pinned host staging).
+ * Errors: INVALID_ARG (out == NULL, bad option values, bad device),
+ * OOM, CUDA.  On error *out is set to NULL.
+ */
+sobel4_status sobel4_create(sobel4_handle *out, int32_t device, const sobel4_options *opt);
+
+/*
+ * Gradient output of one image (Eq. 3 and Eq. 4 for every pixel).
+ *   d_src     : device pointer to height rows of width uint8 pixels.
+ *   src_pitch : bytes between rows; >= width.  Any alignment is accepted.
+ *   d_dst     : device pointer to the output (layout per `fmt`).
+ *   dst_pitch : bytes between output rows; >= width * element size; for F32 a
+ *               multiple of 4 and d_dst 4-byte aligned; for S16X4 a multiple of
+ *               2 and d_dst 2-byte aligned.
+ *   height, width >= 1 (REFLECT101: >= 3).
+ *   The source and destination ranges must not overlap.
+ * Asynchronous on `stream`.  Errors: INVALID_ARG (nothing enqueued), CUDA.
+ */
+sobel4_status sobel4_run(sobel4_handle h, const uint8_t *d_src, size_t src_pitch, void *d_dst,
+                         size_t dst_pitch, int32_t height, int32_t width, sobel4_border border,
+                         sobel4_format fmt, cudaStream_t stream);
+
+/*
+ * Many images of uneven sizes in ONE persistent launch: CTAs pull tiles of
+ * all images from a device-side work queue.  `h_images` is HOST memory with
+ * n >= 1 descriptors (each obeying sobel4_run's rules, all with the batch's
+ * `border` and `fmt`); it is copied before the call returns.  No two images
+ * may write overlapping output, and no output may overlap any input.
+ * Asynchronous on `stream`; calls on one handle must not overlap on the GPU
+ * (they share the handle's queue counter).  Each image's output is identical
+ * to its output from sobel4_run.
+ * Errors: INVALID_ARG (nothing enqueued), OOM (descriptor buffer growth), CUDA.
+ */
+sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *h_images, int32_t n,
+                                 sobel4_border border, sobel4_format fmt, cudaStream_t stream);
+
+/*
+ * End-to-end form with HOST buffers (the paper's "runtime including data
+ * loading", Table 2): copies h_src to the device, runs, copies the result
+ * into h_dst and waits for completion.  Pitches follow sobel4_run.  Device
+ * buffers are held by the handle and reused across calls.  Pinned host
+ * memory (cudaHostAlloc / cudaHostRegister) gives full link bandwidth;
+ * pageable memory works but is slower.  Synchronous.
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+sobel4_status sobel4_run_host(sobel4_handle h, const uint8_t *h_src, size_t src_pitch,
+                              void *h_dst, size_t dst_pitch, int32_t height, int32_t width,
+                              sobel4_border border, sobel4_format fmt);
+
+/* Release the handle (waits for its own internal work only).  NULL is a no-op. */
+sobel4_status sobel4_destroy(sobel4_handle h);
+
+/* Static English text for a status code (never NULL). */
+const char *sobel4_status_string(sobel4_status s);
+
+/* The cudaError_t of the handle's most recent SOBEL4_ERR_CUDA (0 if none). */
+int32_t sobel4_last_cuda_error(sobel4_handle h);
+
+/* Number of kernels this handle has launched so far (for launch accounting). */
+uint64_t sobel4_launch_count(sobel4_handle h);
+
+/* Select the kernel variant for later calls (sobel4_variant); INVALID_ARG if unknown. */
+sobel4_status sobel4_set_variant(sobel4_handle h, int32_t variant);
+
+/* Library version as "major.minor.patch" (static string). */
+const char *sobel4_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SOBEL4_H_ */

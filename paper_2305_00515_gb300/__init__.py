@@ -1,0 +1,252 @@
+"""Python binding of the GB300 four-directional 5x5 Sobel library (``include/sobel4.h``).
+
+Argument marshalling only: every step of the operator runs in the sm_103a
+kernels of ``_build/libsobel4.so``.  The functions named ``sobel4_*`` mirror
+the C ABI one to one and take raw pointers; :class:`Sobel4` wraps them for
+PyTorch CUDA tensors (PyTorch provides device memory and streams, nothing
+else) and numpy host arrays.
+
+The library must have been built (``python -m paper_2305_00515_gb300.build``
+or ``__graft_entry__.build()``); loading fails loudly otherwise.  There is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+__all__ = [
+    "BORDERS", "FORMATS", "VARIANTS", "Sobel4", "Sobel4Error", "Image", "Options",
+    "library_path", "load", "sobel4_create", "sobel4_destroy", "sobel4_run",
+    "sobel4_run_batched", "sobel4_run_host", "sobel4_status_string", "sobel4_last_cuda_error",
+    "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "EXPORTED_SYMBOLS",
+]
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+BORDERS = {"valid": 0, "replicate": 1, "reflect101": 2, "constant0": 3}
+FORMATS = {"f32": 0, "u8": 1, "s16x4": 2}
+VARIANTS = {"auto": 0, "direct": 1, "rg": 2}
+ELEM_SIZE = {"f32": 4, "u8": 1, "s16x4": 2}
+STATUS = {0: "SOBEL4_OK", 1: "SOBEL4_ERR_INVALID_ARG", 2: "SOBEL4_ERR_UNSUPPORTED",
+          3: "SOBEL4_ERR_OOM", 4: "SOBEL4_ERR_CUDA", 5: "SOBEL4_ERR_TIMEOUT"}
+
+EXPORTED_SYMBOLS = (
+    "sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_batched", "sobel4_run_host",
+    "sobel4_status_string", "sobel4_last_cuda_error", "sobel4_launch_count",
+    "sobel4_set_variant", "sobel4_version",
+)
+
+
+class Sobel4Error(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)}")
+
+
+class Image(ctypes.Structure):
+    """``sobel4_image``: one image of a batch (device pointers)."""
+    _fields_ = [("src", ctypes.c_void_p), ("src_pitch", ctypes.c_size_t),
+                ("dst", ctypes.c_void_p), ("dst_pitch", ctypes.c_size_t),
+                ("height", ctypes.c_int32), ("width", ctypes.c_int32)]
+
+
+class Options(ctypes.Structure):
+    """``sobel4_options``."""
+    _fields_ = [("variant", ctypes.c_int32), ("rows_per_strip", ctypes.c_int32),
+                ("persistent_ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return os.path.join(_PKG, "_build", "libsobel4.so")
+
+
+def load() -> ctypes.CDLL:
+    """Load the built library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = library_path()
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with "
+                              "`python -m paper_2305_00515_gb300.build`")
+        lib = ctypes.CDLL(path)
+        vp, sz, i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32
+        lib.sobel4_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(Options)]
+        lib.sobel4_destroy.argtypes = [vp]
+        lib.sobel4_run.argtypes = [vp, vp, sz, vp, sz, i32, i32, i32, i32, vp]
+        lib.sobel4_run_batched.argtypes = [vp, ctypes.POINTER(Image), i32, i32, i32, vp]
+        lib.sobel4_run_host.argtypes = [vp, vp, sz, vp, sz, i32, i32, i32, i32]
+        lib.sobel4_status_string.argtypes = [ctypes.c_int]
+        lib.sobel4_status_string.restype = ctypes.c_char_p
+        lib.sobel4_last_cuda_error.argtypes = [vp]
+        lib.sobel4_last_cuda_error.restype = i32
+        lib.sobel4_launch_count.argtypes = [vp]
+        lib.sobel4_launch_count.restype = ctypes.c_uint64
+        lib.sobel4_set_variant.argtypes = [vp, i32]
+        lib.sobel4_version.restype = ctypes.c_char_p
+        for name in ("sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_batched",
+                     "sobel4_run_host", "sobel4_set_variant"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+# -- one-to-one C ABI wrappers (raw pointers; return the status code) ----------
+def sobel4_create(device: int = 0, variant: int = 0, rows_per_strip: int = 0,
+                  persistent_ctas_per_sm: int = 0):
+    h = ctypes.c_void_p()
+    opt = Options(variant, rows_per_strip, persistent_ctas_per_sm, 0)
+    st = load().sobel4_create(ctypes.byref(h), device, ctypes.byref(opt))
+    return st, h
+
+
+def sobel4_destroy(h) -> int:
+    return load().sobel4_destroy(h)
+
+
+def sobel4_run(h, d_src: int, src_pitch: int, d_dst: int, dst_pitch: int, height: int,
+               width: int, border: int, fmt: int, stream: int) -> int:
+    return load().sobel4_run(h, d_src, src_pitch, d_dst, dst_pitch, height, width, border, fmt,
+                             stream)
+
+
+def sobel4_run_batched(h, images, border: int, fmt: int, stream: int) -> int:
+    arr = images if isinstance(images, ctypes.Array) else (Image * len(images))(*images)
+    return load().sobel4_run_batched(h, arr, len(arr), border, fmt, stream)
+
+
+def sobel4_run_host(h, h_src: int, src_pitch: int, h_dst: int, dst_pitch: int, height: int,
+                    width: int, border: int, fmt: int) -> int:
+    return load().sobel4_run_host(h, h_src, src_pitch, h_dst, dst_pitch, height, width, border,
+                                  fmt)
+
+
+def sobel4_status_string(status: int) -> str:
+    return load().sobel4_status_string(status).decode()
+
+
+def sobel4_last_cuda_error(h) -> int:
+    return load().sobel4_last_cuda_error(h)
+
+
+def sobel4_launch_count(h) -> int:
+    return load().sobel4_launch_count(h)
+
+
+def sobel4_set_variant(h, variant: int) -> int:
+    return load().sobel4_set_variant(h, variant)
+
+
+def sobel4_version() -> str:
+    return load().sobel4_version().decode()
+
+
+# -- tensor-level convenience --------------------------------------------------
+def _check(st: int, what: str):
+    if st != 0:
+        raise Sobel4Error(st, what)
+
+
+class Sobel4:
+    """A library handle bound to one CUDA device."""
+
+    def __init__(self, device: int = 0, variant: str = "auto", rows_per_strip: int = 0,
+                 persistent_ctas_per_sm: int = 0):
+        st, h = sobel4_create(device, VARIANTS[variant], rows_per_strip, persistent_ctas_per_sm)
+        _check(st, "sobel4_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sobel4_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def launches(self) -> int:
+        return sobel4_launch_count(self.handle)
+
+    def set_variant(self, variant: str):
+        _check(sobel4_set_variant(self.handle, VARIANTS[variant]), "sobel4_set_variant")
+
+    @staticmethod
+    def _stream(stream) -> int:
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+    @staticmethod
+    def empty_output(src, fmt: str = "f32"):
+        import torch
+        H, W = src.shape
+        dtype = {"f32": torch.float32, "u8": torch.uint8, "s16x4": torch.int16}[fmt]
+        shape = (4, H, W) if fmt == "s16x4" else (H, W)
+        return torch.empty(shape, dtype=dtype, device=src.device)
+
+    @staticmethod
+    def _pitches(src, out, fmt):
+        import torch
+        if src.dtype != torch.uint8 or src.dim() != 2 or not src.is_cuda or src.stride(1) != 1:
+            raise ValueError("src must be a 2-D uint8 CUDA tensor with unit column stride")
+        if out.stride(-1) != 1:
+            raise ValueError("out must have unit column stride")
+        if fmt == "s16x4":
+            if out.dim() != 3 or out.shape[0] != 4 or out.stride(0) != out.shape[1] * out.stride(1):
+                raise ValueError("s16x4 output must be 4 stacked planes")
+        return src.stride(0), out.stride(-2) * ELEM_SIZE[fmt]
+
+    def run(self, src, out=None, border: str = "valid", fmt: str = "f32", stream=None):
+        """Gradient output of a uint8 CUDA tensor [H, W]; asynchronous on `stream`."""
+        if out is None:
+            out = self.empty_output(src, fmt)
+        sp, dp = self._pitches(src, out, fmt)
+        H, W = src.shape
+        _check(sobel4_run(self.handle, src.data_ptr(), sp, out.data_ptr(), dp, H, W,
+                          BORDERS[border], FORMATS[fmt], self._stream(stream)), "sobel4_run")
+        return out
+
+    def run_batched(self, srcs, outs=None, border: str = "valid", fmt: str = "f32",
+                    stream=None):
+        """Many images in one persistent launch; returns the outputs."""
+        if outs is None:
+            outs = [self.empty_output(s, fmt) for s in srcs]
+        imgs = (Image * len(srcs))()
+        for i, (s, o) in enumerate(zip(srcs, outs)):
+            sp, dp = self._pitches(s, o, fmt)
+            imgs[i] = Image(s.data_ptr(), sp, o.data_ptr(), dp, s.shape[0], s.shape[1])
+        _check(sobel4_run_batched(self.handle, imgs, BORDERS[border], FORMATS[fmt],
+                                  self._stream(stream)), "sobel4_run_batched")
+        return outs
+
+    def run_host(self, src, out=None, border: str = "valid", fmt: str = "f32"):
+        """End to end from a host numpy array (synchronous)."""
+        import numpy as np
+        if src.dtype != np.uint8 or src.ndim != 2 or src.strides[1] != 1:
+            raise ValueError("src must be a 2-D uint8 array with unit column stride")
+        H, W = src.shape
+        if out is None:
+            dtype = {"f32": np.float32, "u8": np.uint8, "s16x4": np.int16}[fmt]
+            out = np.empty((4, H, W) if fmt == "s16x4" else (H, W), dtype=dtype)
+        _check(sobel4_run_host(self.handle, src.ctypes.data, src.strides[0], out.ctypes.data,
+                               out.strides[-2], H, W, BORDERS[border], FORMATS[fmt]),
+               "sobel4_run_host")
+        return out

@@ -1,0 +1,410 @@
+// sobel4_api.cu — the C ABI of include/sobel4.h: argument validation, handle
+// state, batch descriptor staging and kernel selection.  Every step of the
+// operator itself runs in the kernels of sobel4_rg_*.cu / sobel4_direct.cu.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "sobel4.h"
+#include "sobel4_launch.h"
+
+namespace sobel4 {
+cudaError_t launch_rg_single_f32(const ImageDesc &, int, int, cudaStream_t);
+cudaError_t launch_rg_single_u8(const ImageDesc &, int, int, cudaStream_t);
+cudaError_t launch_rg_single_s16(const ImageDesc &, int, int, cudaStream_t);
+cudaError_t launch_rg_batched_f32(const ImageDesc *, int, int64_t, unsigned int *, int, int, int,
+                                  cudaStream_t);
+cudaError_t launch_rg_batched_u8(const ImageDesc *, int, int64_t, unsigned int *, int, int, int,
+                                 cudaStream_t);
+cudaError_t launch_rg_batched_s16(const ImageDesc *, int, int64_t, unsigned int *, int, int, int,
+                                  cudaStream_t);
+
+cudaError_t launch_rg_single(const ImageDesc &im, int border, int fmt, int R, cudaStream_t st) {
+  switch (fmt) {
+    case kF32: return launch_rg_single_f32(im, border, R, st);
+    case kU8: return launch_rg_single_u8(im, border, R, st);
+    default: return launch_rg_single_s16(im, border, R, st);
+  }
+}
+
+cudaError_t launch_rg_batched(const ImageDesc *d, int n, int64_t total, unsigned int *q,
+                              int border, int fmt, int R, int grid, cudaStream_t st) {
+  switch (fmt) {
+    case kF32: return launch_rg_batched_f32(d, n, total, q, border, R, grid, st);
+    case kU8: return launch_rg_batched_u8(d, n, total, q, border, R, grid, st);
+    default: return launch_rg_batched_s16(d, n, total, q, border, R, grid, st);
+  }
+}
+}  // namespace sobel4
+
+using namespace sobel4;
+
+namespace {
+
+constexpr int kSlots = 4;           // batch descriptor slots in flight per handle
+constexpr int kDefaultR = 32;       // RG strip height for large images
+constexpr int kBatchR = 16;         // RG strip height for batches
+constexpr int kMaxSide = 1 << 28;   // largest accepted height or width
+constexpr uint64_t kMaxPitch = (1ull << 31) - 1;
+
+struct BatchSlot {
+  ImageDesc *h_desc = nullptr;      // pinned host staging
+  ImageDesc *d_desc = nullptr;
+  unsigned int *d_queue = nullptr;  // work-queue head of the persistent kernel
+  int cap = 0;
+  cudaEvent_t done = nullptr;
+  bool pending = false;
+};
+
+size_t elem_size(int fmt) { return fmt == kF32 ? 4 : (fmt == kU8 ? 1 : 2); }
+int planes(int fmt) { return fmt == kS16x4 ? 4 : 1; }
+
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = -1;
+    if (prev_ != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev_ >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev_) cudaSetDevice(prev_);
+  }
+
+ private:
+  int prev_ = -1;
+};
+
+}  // namespace
+
+struct sobel4_ctx {
+  int device = 0;
+  int sm_count = 0;
+  int variant = SOBEL4_VARIANT_AUTO;
+  int rows_per_strip = 0;
+  int ctas_per_sm = 4;
+  uint64_t launches = 0;
+  int32_t last_err = 0;
+  BatchSlot slots[kSlots];
+  int next_slot = 0;
+  cudaStream_t own_stream = nullptr;
+  uint8_t *d_in = nullptr;
+  size_t d_in_bytes = 0;
+  uint8_t *d_out = nullptr;
+  size_t d_out_bytes = 0;
+};
+
+namespace {
+
+sobel4_status cuda_fail(sobel4_ctx *h, cudaError_t e) {
+  if (h) h->last_err = (int32_t)e;
+  return e == cudaErrorMemoryAllocation ? SOBEL4_ERR_OOM : SOBEL4_ERR_CUDA;
+}
+
+bool valid_enum(int border, int fmt) {
+  return border >= SOBEL4_BORDER_VALID && border <= SOBEL4_BORDER_CONSTANT0 &&
+         fmt >= SOBEL4_OUT_F32 && fmt <= SOBEL4_OUT_S16X4;
+}
+
+// Shape and pitch rules shared by every entry point (pointers checked separately).
+bool valid_shape(size_t src_pitch, size_t dst_pitch, int32_t H, int32_t W, int border, int fmt) {
+  if (!valid_enum(border, fmt)) return false;
+  if (H < 1 || W < 1 || H > kMaxSide || W > kMaxSide) return false;
+  if (border == SOBEL4_BORDER_REFLECT101 && (H < 3 || W < 3)) return false;
+  if (src_pitch < (size_t)W || src_pitch > kMaxPitch) return false;
+  if (dst_pitch < (size_t)W * elem_size(fmt) || dst_pitch > kMaxPitch) return false;
+  if (fmt == kF32 && dst_pitch % 4) return false;
+  if (fmt == kS16x4 && dst_pitch % 2) return false;
+  return true;
+}
+
+bool valid_dst_ptr(const void *dst, int fmt) {
+  if (!dst) return false;
+  if (fmt == kF32 && ((uintptr_t)dst % 4)) return false;
+  if (fmt == kS16x4 && ((uintptr_t)dst % 2)) return false;
+  return true;
+}
+
+// Byte ranges [begin, end) touched by one image's input and output.
+void ranges(const uint8_t *src, size_t sp, const void *dst, size_t dp, int32_t H, int32_t W,
+            int fmt, uintptr_t r[4]) {
+  r[0] = (uintptr_t)src;
+  r[1] = (uintptr_t)src + (uintptr_t)(H - 1) * sp + (uintptr_t)W;
+  r[2] = (uintptr_t)dst;
+  r[3] = (uintptr_t)dst + (uintptr_t)(planes(fmt) * (size_t)H - 1) * dp +
+         (uintptr_t)W * elem_size(fmt);
+}
+
+bool overlaps(uintptr_t a0, uintptr_t a1, uintptr_t b0, uintptr_t b1) { return a0 < b1 && b0 < a1; }
+
+int pick_R(const sobel4_ctx *h, int32_t H, int32_t W) {
+  if (h->rows_per_strip > 0) return h->rows_per_strip;
+  const int64_t n_seg = (W + kSegCols - 1) / kSegCols;
+  const int64_t target = 2ll * h->sm_count * h->ctas_per_sm * kWarpsPerCta;
+  int R = kDefaultR;
+  while (R > 4 && n_seg * ((H + 2 * R - 1) / (2 * R)) < target) R /= 2;
+  return R;
+}
+
+ImageDesc make_desc(const uint8_t *src, size_t sp, void *dst, size_t dp, int32_t H, int32_t W,
+                    int fmt, int R) {
+  ImageDesc d;
+  memset(&d, 0, sizeof(d));
+  d.src = src;
+  d.dst = dst;
+  d.sp = sp;
+  d.dp = dp;
+  d.H = H;
+  d.W = W;
+  d.n_seg = (W + kSegCols - 1) / kSegCols;
+  d.n_band = (H + 2 * R - 1) / (2 * R);
+  d.item0 = 0;
+  d.src_aligned = ((uintptr_t)src % 4 == 0) && (sp % 4 == 0);
+  const size_t vec = fmt == kF32 ? 16 : (fmt == kU8 ? 4 : 8);
+  d.dst_vec = ((uintptr_t)dst % vec == 0) && (dp % vec == 0);
+  return d;
+}
+
+sobel4_status launch_one(sobel4_ctx *h, const uint8_t *src, size_t sp, void *dst, size_t dp,
+                         int32_t H, int32_t W, int border, int fmt, cudaStream_t stream) {
+  cudaError_t e;
+  if (h->variant == SOBEL4_VARIANT_DIRECT) {
+    const ImageDesc im = make_desc(src, sp, dst, dp, H, W, fmt, 1);
+    e = launch_direct(im, border, fmt, stream);
+  } else {
+    const int R = pick_R(h, H, W);
+    const ImageDesc im = make_desc(src, sp, dst, dp, H, W, fmt, R);
+    e = launch_rg_single(im, border, fmt, R, stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  h->launches += 1;
+  return SOBEL4_OK;
+}
+
+void free_slot(BatchSlot &s) {
+  if (s.done && s.pending) cudaEventSynchronize(s.done);
+  if (s.h_desc) cudaFreeHost(s.h_desc);
+  if (s.d_desc) cudaFree(s.d_desc);
+  if (s.d_queue) cudaFree(s.d_queue);
+  if (s.done) cudaEventDestroy(s.done);
+  s = BatchSlot();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sobel4_version(void) { return "0.1.0"; }
+
+const char *sobel4_status_string(sobel4_status s) {
+  switch (s) {
+    case SOBEL4_OK: return "success";
+    case SOBEL4_ERR_INVALID_ARG: return "invalid argument";
+    case SOBEL4_ERR_UNSUPPORTED: return "unsupported request";
+    case SOBEL4_ERR_OOM: return "out of memory";
+    case SOBEL4_ERR_CUDA: return "CUDA error";
+    case SOBEL4_ERR_TIMEOUT: return "timeout";
+  }
+  return "unknown status";
+}
+
+sobel4_status sobel4_create(sobel4_handle *out, int32_t device, const sobel4_options *opt) {
+  if (!out) return SOBEL4_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (opt && (opt->variant < 0 || opt->variant > SOBEL4_VARIANT_RG || opt->rows_per_strip < 0 ||
+              opt->rows_per_strip > 4096 || opt->persistent_ctas_per_sm < 0 ||
+              opt->persistent_ctas_per_sm > 64 || opt->reserved != 0))
+    return SOBEL4_ERR_INVALID_ARG;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess) return SOBEL4_ERR_CUDA;
+  if (device < 0 || device >= count) return SOBEL4_ERR_INVALID_ARG;
+  DeviceGuard g(device);
+  sobel4_ctx *h = new (std::nothrow) sobel4_ctx();
+  if (!h) return SOBEL4_ERR_OOM;
+  h->device = device;
+  e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
+  for (int i = 0; i < kSlots && e == cudaSuccess; ++i)
+    e = cudaEventCreateWithFlags(&h->slots[i].done, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    sobel4_destroy(h);
+    return SOBEL4_ERR_CUDA;
+  }
+  if (opt) {
+    h->variant = opt->variant;
+    h->rows_per_strip = opt->rows_per_strip;
+    if (opt->persistent_ctas_per_sm > 0) h->ctas_per_sm = opt->persistent_ctas_per_sm;
+  }
+  *out = h;
+  return SOBEL4_OK;
+}
+
+sobel4_status sobel4_destroy(sobel4_handle h) {
+  if (!h) return SOBEL4_OK;
+  DeviceGuard g(h->device);
+  for (int i = 0; i < kSlots; ++i) free_slot(h->slots[i]);
+  if (h->own_stream) {
+    cudaStreamSynchronize(h->own_stream);
+    cudaStreamDestroy(h->own_stream);
+  }
+  if (h->d_in) cudaFree(h->d_in);
+  if (h->d_out) cudaFree(h->d_out);
+  delete h;
+  return SOBEL4_OK;
+}
+
+int32_t sobel4_last_cuda_error(sobel4_handle h) { return h ? h->last_err : 0; }
+
+uint64_t sobel4_launch_count(sobel4_handle h) { return h ? h->launches : 0; }
+
+sobel4_status sobel4_set_variant(sobel4_handle h, int32_t variant) {
+  if (!h || variant < SOBEL4_VARIANT_AUTO || variant > SOBEL4_VARIANT_RG)
+    return SOBEL4_ERR_INVALID_ARG;
+  h->variant = variant;
+  return SOBEL4_OK;
+}
+
+sobel4_status sobel4_run(sobel4_handle h, const uint8_t *d_src, size_t src_pitch, void *d_dst,
+                         size_t dst_pitch, int32_t height, int32_t width, sobel4_border border,
+                         sobel4_format fmt, cudaStream_t stream) {
+  if (!h || !d_src || !valid_dst_ptr(d_dst, fmt)) return SOBEL4_ERR_INVALID_ARG;
+  if (!valid_shape(src_pitch, dst_pitch, height, width, border, fmt))
+    return SOBEL4_ERR_INVALID_ARG;
+  uintptr_t r[4];
+  ranges(d_src, src_pitch, d_dst, dst_pitch, height, width, fmt, r);
+  if (overlaps(r[0], r[1], r[2], r[3])) return SOBEL4_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  return launch_one(h, d_src, src_pitch, d_dst, dst_pitch, height, width, border, fmt, stream);
+}
+
+sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int32_t n,
+                                 sobel4_border border, sobel4_format fmt, cudaStream_t stream) {
+  if (!h || !imgs || n < 1 || !valid_enum(border, fmt)) return SOBEL4_ERR_INVALID_ARG;
+  // Validate every descriptor and the pairwise overlap rule (sweep over sorted ranges).
+  struct Iv {
+    uintptr_t b, e;
+    bool out;
+  };
+  std::vector<Iv> iv;
+  iv.reserve((size_t)n * 2);
+  for (int32_t i = 0; i < n; ++i) {
+    const sobel4_image &m = imgs[i];
+    if (!m.src || !valid_dst_ptr(m.dst, fmt) ||
+        !valid_shape(m.src_pitch, m.dst_pitch, m.height, m.width, border, fmt))
+      return SOBEL4_ERR_INVALID_ARG;
+    uintptr_t r[4];
+    ranges(m.src, m.src_pitch, m.dst, m.dst_pitch, m.height, m.width, fmt, r);
+    iv.push_back({r[0], r[1], false});
+    iv.push_back({r[2], r[3], true});
+  }
+  std::sort(iv.begin(), iv.end(), [](const Iv &a, const Iv &b) { return a.b < b.b; });
+  uintptr_t end_out = 0, end_in = 0;
+  for (const Iv &v : iv) {
+    if (v.out ? (v.b < end_out || v.b < end_in) : (v.b < end_out)) return SOBEL4_ERR_INVALID_ARG;
+    if (v.out) end_out = std::max(end_out, v.e);
+    else end_in = std::max(end_in, v.e);
+  }
+  DeviceGuard g(h->device);
+  if (h->variant == SOBEL4_VARIANT_DIRECT) {
+    for (int32_t i = 0; i < n; ++i) {
+      const sobel4_image &m = imgs[i];
+      sobel4_status s = launch_one(h, m.src, m.src_pitch, m.dst, m.dst_pitch, m.height, m.width,
+                                   border, fmt, stream);
+      if (s != SOBEL4_OK) return s;
+    }
+    return SOBEL4_OK;
+  }
+  const int R = h->rows_per_strip > 0 ? h->rows_per_strip : kBatchR;
+  BatchSlot &slot = h->slots[h->next_slot];
+  h->next_slot = (h->next_slot + 1) % kSlots;
+  cudaError_t e = cudaSuccess;
+  if (slot.pending) {
+    e = cudaEventSynchronize(slot.done);  // the slot's previous batch has consumed its buffers
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    slot.pending = false;
+  }
+  if (slot.cap < n) {
+    int cap = std::max(n, 2 * slot.cap);
+    if (slot.h_desc) cudaFreeHost(slot.h_desc);
+    if (slot.d_desc) cudaFree(slot.d_desc);
+    slot.h_desc = nullptr;
+    slot.d_desc = nullptr;
+    slot.cap = 0;
+    e = cudaHostAlloc((void **)&slot.h_desc, sizeof(ImageDesc) * cap, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&slot.d_desc, sizeof(ImageDesc) * cap);
+    if (e == cudaSuccess && !slot.d_queue) e = cudaMalloc((void **)&slot.d_queue, 256);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    slot.cap = cap;
+  }
+  int64_t total = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    const sobel4_image &m = imgs[i];
+    ImageDesc d = make_desc(m.src, m.src_pitch, m.dst, m.dst_pitch, m.height, m.width, fmt, R);
+    d.item0 = total;
+    total += (int64_t)d.n_seg * d.n_band;
+    slot.h_desc[i] = d;
+  }
+  if (total >= (1ll << 31)) return SOBEL4_ERR_UNSUPPORTED;
+  e = cudaMemcpyAsync(slot.d_desc, slot.h_desc, sizeof(ImageDesc) * n, cudaMemcpyHostToDevice,
+                      stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(slot.d_queue, 0, sizeof(unsigned int), stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  const int64_t want = (total + kWarpsPerCta - 1) / kWarpsPerCta;
+  const int grid = (int)std::min<int64_t>(want, (int64_t)h->sm_count * h->ctas_per_sm);
+  e = launch_rg_batched(slot.d_desc, n, total, slot.d_queue, border, fmt, R, std::max(grid, 1),
+                        stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  h->launches += 1;
+  e = cudaEventRecord(slot.done, stream);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  slot.pending = true;
+  return SOBEL4_OK;
+}
+
+sobel4_status sobel4_run_host(sobel4_handle h, const uint8_t *h_src, size_t src_pitch,
+                              void *h_dst, size_t dst_pitch, int32_t height, int32_t width,
+                              sobel4_border border, sobel4_format fmt) {
+  if (!h || !h_src || !h_dst) return SOBEL4_ERR_INVALID_ARG;
+  if (!valid_shape(src_pitch, dst_pitch, height, width, border, fmt))
+    return SOBEL4_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  const size_t sp = ((size_t)width + 15) & ~(size_t)15;
+  const size_t row_out = (size_t)width * elem_size(fmt);
+  const size_t dp = (row_out + 15) & ~(size_t)15;
+  const size_t in_bytes = sp * (size_t)height;
+  const size_t out_bytes = dp * (size_t)height * planes(fmt);
+  cudaError_t e = cudaSuccess;
+  if (h->d_in_bytes < in_bytes) {
+    if (h->d_in) cudaFree(h->d_in);
+    h->d_in = nullptr;
+    h->d_in_bytes = 0;
+    e = cudaMalloc((void **)&h->d_in, in_bytes);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    h->d_in_bytes = in_bytes;
+  }
+  if (h->d_out_bytes < out_bytes) {
+    if (h->d_out) cudaFree(h->d_out);
+    h->d_out = nullptr;
+    h->d_out_bytes = 0;
+    e = cudaMalloc((void **)&h->d_out, out_bytes);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    h->d_out_bytes = out_bytes;
+  }
+  cudaStream_t st = h->own_stream;
+  e = cudaMemcpy2DAsync(h->d_in, sp, h_src, src_pitch, (size_t)width, (size_t)height,
+                        cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  sobel4_status s = launch_one(h, h->d_in, sp, h->d_out, dp, height, width, border, fmt, st);
+  if (s != SOBEL4_OK) return s;
+  e = cudaMemcpy2DAsync(h_dst, dst_pitch, h->d_out, dp, row_out, (size_t)height * planes(fmt),
+                        cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  return SOBEL4_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,55 @@
+// sobel4_direct.cu — the DIRECT kernel: Eq. (3) summed tap by tap per output
+// pixel straight from global memory (the paper's "GM" baseline, Section 5.2).
+#include "sobel4_launch.h"
+
+namespace sobel4 {
+
+template <int FMT>
+__global__ void __launch_bounds__(256) direct_kernel(ImageDesc im, int border) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int H = im.H, W = im.W;
+  if (x >= W || y >= H) return;
+  int32_t r[4] = {0, 0, 0, 0};
+  const bool computed = border != kValid || (y >= 2 && y <= H - 3 && x >= 2 && x <= W - 3);
+  if (computed) {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      bool zr;
+      const int yy = map_index(y + i - 2, H, border, &zr);
+      const uint8_t *row = im.src + (uint64_t)(uint32_t)yy * im.sp;
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        bool zc;
+        const int xx = map_index(x + j - 2, W, border, &zc);
+        const int32_t v = (zr || zc) ? 0 : (int32_t)__ldg(row + xx);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) r[k] += (int32_t)kMasks[k][i][j] * v;
+      }
+    }
+  }
+  const int32_t s = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3];
+  uint8_t *row = (uint8_t *)im.dst + (uint64_t)(uint32_t)y * im.dp;
+  if (FMT == kF32) {
+    ((float *)row)[x] = magnitude_f32(s);
+  } else if (FMT == kU8) {
+    row[x] = (uint8_t)magnitude_u8(s);
+  } else {
+    const uint64_t plane = (uint64_t)(uint32_t)H * im.dp;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ((int16_t *)(row + k * plane))[x] = (int16_t)r[k];
+  }
+}
+
+cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, cudaStream_t st) {
+  const dim3 block(32, 8);
+  const dim3 grid((im.W + 31) / 32, (im.H + 7) / 8);
+  switch (fmt) {
+    case kF32: direct_kernel<kF32><<<grid, block, 0, st>>>(im, border); break;
+    case kU8: direct_kernel<kU8><<<grid, block, 0, st>>>(im, border); break;
+    default: direct_kernel<kS16x4><<<grid, block, 0, st>>>(im, border); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace sobel4

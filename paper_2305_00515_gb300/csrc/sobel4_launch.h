@@ -1,0 +1,23 @@
+// sobel4_launch.h — internal launchers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sobel4_device.cuh"
+
+namespace sobel4 {
+
+// RG kernel over one image: ceil(items / 4) CTAs of 4 independent warps.
+cudaError_t launch_rg_single(const ImageDesc &im, int border, int fmt, int R, cudaStream_t st);
+
+// Persistent RG kernel over a batch: `grid` CTAs pull warp items from the
+// device counter *d_queue (reset to 0 by the caller before the launch).
+cudaError_t launch_rg_batched(const ImageDesc *d_descs, int n_img, int64_t total_items,
+                              unsigned int *d_queue, int border, int fmt, int R, int grid,
+                              cudaStream_t st);
+
+// DIRECT kernel (one thread per output pixel).
+cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, cudaStream_t st);
+
+}  // namespace sobel4

@@ -1,0 +1,12 @@
+// RG kernels instantiated for the u8 output format.
+#include "sobel4_rg.cuh"
+
+namespace sobel4 {
+cudaError_t launch_rg_single_u8(const ImageDesc &im, int border, int R, cudaStream_t st) {
+  return launch_rg_single_fmt<kU8>(im, border, R, st);
+}
+cudaError_t launch_rg_batched_u8(const ImageDesc *d, int n, int64_t total, unsigned int *q,
+                                   int border, int R, int grid, cudaStream_t st) {
+  return launch_rg_batched_fmt<kU8>(d, n, total, q, border, R, grid, st);
+}
+}  // namespace sobel4

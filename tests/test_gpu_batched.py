@@ -1,0 +1,100 @@
+"""The persistent batched kernel: every image of a ragged batch equals its
+single-image output and the CPU oracle, bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2305_00515_gb300 as pkg
+import synth
+from gpu_util import Output, Placed
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+NCPU = oracle.cpu_count()
+
+
+@pytest.fixture(scope="module")
+def h():
+    from paper_2305_00515_gb300 import build
+    build.build()
+    st, h = pkg.sobel4_create(0)
+    assert st == 0
+    yield h
+    pkg.sobel4_destroy(h)
+
+
+def run_batch(h, imgs, border, fmt, layout=None):
+    elem = {"f32": 4, "u8": 1, "s16x4": 2}[fmt]
+    srcs, outs, descs = [], [], []
+    for i, img in enumerate(imgs):
+        H, W = img.shape
+        spx, so, dpx, do = layout[i] if layout else (0, 0, 0, 0)
+        s = Placed(torch, img, W + spx, so)
+        o = Output(torch, H, W, fmt, (W + dpx) * elem, do)
+        srcs.append(s)
+        outs.append(o)
+        descs.append(pkg.Image(s.ptr, s.pitch, o.ptr, o.pitch, H, W))
+    rc = pkg.sobel4_run_batched(h, descs, pkg.BORDERS[border], pkg.FORMATS[fmt],
+                                torch.cuda.current_stream().cuda_stream)
+    assert rc == 0, pkg.sobel4_status_string(rc)
+    torch.cuda.synchronize()
+    return [o.read() for o in outs]
+
+
+def test_ragged_512_batch_matches_oracle(h):
+    """The 512-image ragged batch (sides U{37..2048}, seed 1) in one persistent launch."""
+    imgs = synth.batch_images(512, 1)
+    res = run_batch(h, imgs, "valid", "f32")
+    for i, (img, (got, guards)) in enumerate(zip(imgs, res)):
+        assert guards, f"image {i}: write outside its output"
+        want = oracle.sobel4(img, "valid", "f32", threads=NCPU)
+        assert np.array_equal(got, want), f"image {i} {img.shape} differs from the oracle"
+
+
+def test_batch_equals_single_runs_all_modes(h):
+    rng = np.random.default_rng(3)
+    shapes = [(int(a), int(b)) for a, b in rng.integers(3, 400, size=(24, 2))] + [(3, 3), (1000, 7)]
+    imgs = [synth.uniform(a, b, i) for i, (a, b) in enumerate(shapes)]
+    layout = [(int(rng.integers(0, 9)), int(rng.integers(0, 4)), int(rng.integers(0, 5)),
+               4 * int(rng.integers(0, 4))) for _ in imgs]
+    for border in ("valid", "replicate", "reflect101", "constant0"):
+        for fmt in ("f32", "u8", "s16x4"):
+            res = run_batch(h, imgs, border, fmt, layout)
+            for img, (got, guards) in zip(imgs, res):
+                assert guards
+                assert np.array_equal(got, oracle.sobel4(img, border, fmt)), (img.shape, border, fmt)
+
+
+def test_batch_of_one_and_shared_input(h):
+    img = synth.rects_noise(200, 300, 5)
+    (got, guards), = run_batch(h, [img], "replicate", "f32")
+    assert guards and np.array_equal(got, oracle.sobel4(img, "replicate", "f32"))
+    # the same input read by two images of one batch is allowed
+    s = Placed(torch, img, 300, 0)
+    o1 = Output(torch, 200, 300, "u8", 300, 0)
+    o2 = Output(torch, 200, 300, "u8", 300, 0)
+    descs = [pkg.Image(s.ptr, 300, o1.ptr, 300, 200, 300), pkg.Image(s.ptr, 300, o2.ptr, 300, 200, 300)]
+    assert pkg.sobel4_run_batched(h, descs, 0, 1, torch.cuda.current_stream().cuda_stream) == 0
+    torch.cuda.synchronize()
+    want = oracle.sobel4(img, "valid", "u8")
+    assert np.array_equal(o1.read()[0], want) and np.array_equal(o2.read()[0], want)
+
+
+def test_back_to_back_batches_reuse_slots(h):
+    """More batches in flight than descriptor slots: results must not mix."""
+    imgs = [synth.uniform(50 + 7 * i, 60 + 11 * i, i) for i in range(6)]
+    outs = []
+    keep = []
+    stream = torch.cuda.current_stream().cuda_stream
+    for k in range(10):
+        img = imgs[k % len(imgs)]
+        s = Placed(torch, img, img.shape[1], 0)
+        o = Output(torch, img.shape[0], img.shape[1], "f32", img.shape[1] * 4, 0)
+        keep.append(s)
+        outs.append((img, o))
+        assert pkg.sobel4_run_batched(h, [pkg.Image(s.ptr, s.pitch, o.ptr, o.pitch, *img.shape)],
+                                      0, 0, stream) == 0
+    torch.cuda.synchronize()
+    for img, o in outs:
+        got, guards = o.read()
+        assert guards and np.array_equal(got, oracle.sobel4(img))
