@@ -172,6 +172,17 @@ uint64_t sobel4_launch_count(sobel4_handle h);
 /* Select the kernel variant for later calls (sobel4_variant); INVALID_ARG if unknown. */
 sobel4_status sobel4_set_variant(sobel4_handle h, int32_t variant);
 
+/*
+ * Self-check of the magnitude step of Eq. (4) on the device: for every S in
+ * [s_begin, s_end) (0 <= s_begin <= s_end <= 599,270,401, the operator's whole
+ * range of S), compares the F32 magnitude with CUDA's IEEE sqrtf((float)S) and
+ * the U8 magnitude with min(255, round(sqrt(S))); *mismatches receives the
+ * number of disagreements (0 expected).  Synchronous; allocates 8 bytes of
+ * device memory for the count.  Errors: INVALID_ARG, OOM, CUDA.
+ */
+sobel4_status sobel4_check_magnitude(sobel4_handle h, int32_t s_begin, int32_t s_end,
+                                     uint64_t *mismatches);
+
 /* Library version as "major.minor.patch" (static string). */
 const char *sobel4_version(void);
 

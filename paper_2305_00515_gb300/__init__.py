@@ -20,7 +20,8 @@ __all__ = [
     "BORDERS", "FORMATS", "VARIANTS", "Sobel4", "Sobel4Error", "Image", "Options",
     "library_path", "load", "sobel4_create", "sobel4_destroy", "sobel4_run",
     "sobel4_run_batched", "sobel4_run_host", "sobel4_status_string", "sobel4_last_cuda_error",
-    "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "EXPORTED_SYMBOLS",
+    "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
+    "EXPORTED_SYMBOLS",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -34,7 +35,7 @@ STATUS = {0: "SOBEL4_OK", 1: "SOBEL4_ERR_INVALID_ARG", 2: "SOBEL4_ERR_UNSUPPORTE
 EXPORTED_SYMBOLS = (
     "sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_batched", "sobel4_run_host",
     "sobel4_status_string", "sobel4_last_cuda_error", "sobel4_launch_count",
-    "sobel4_set_variant", "sobel4_version",
+    "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
 )
 
 
@@ -90,8 +91,9 @@ def load() -> ctypes.CDLL:
         lib.sobel4_launch_count.restype = ctypes.c_uint64
         lib.sobel4_set_variant.argtypes = [vp, i32]
         lib.sobel4_version.restype = ctypes.c_char_p
+        lib.sobel4_check_magnitude.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_uint64)]
         for name in ("sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_batched",
-                     "sobel4_run_host", "sobel4_set_variant"):
+                     "sobel4_run_host", "sobel4_set_variant", "sobel4_check_magnitude"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -141,6 +143,13 @@ def sobel4_launch_count(h) -> int:
 
 def sobel4_set_variant(h, variant: int) -> int:
     return load().sobel4_set_variant(h, variant)
+
+
+def sobel4_check_magnitude(h, s_begin: int, s_end: int):
+    """(status, mismatches) of the on-device magnitude self-check over [s_begin, s_end)."""
+    n = ctypes.c_uint64()
+    st = load().sobel4_check_magnitude(h, s_begin, s_end, ctypes.byref(n))
+    return st, n.value
 
 
 def sobel4_version() -> str:

@@ -22,8 +22,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
 
-def _sources():
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+def _sources(csrc: str = CSRC):
+    return sorted(os.path.join(csrc, f) for f in os.listdir(csrc) if f.endswith(".cu"))
 
 
 def _headers():
@@ -31,10 +31,10 @@ def _headers():
     return hs + [os.path.join(INCLUDE, "sobel4.h")]
 
 
-def _compile(src: str, verbose: bool) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
+def _compile(src: str, verbose: bool, out_dir: str = BUILD, defines=(), csrc: str = CSRC) -> str:
+    obj = os.path.join(out_dir, os.path.basename(src).replace(".cu", ".o"))
     cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-           "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
+           "-I", INCLUDE, "-I", csrc, *[f"-D{d}" for d in defines], "-c", src, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -52,20 +52,26 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(f) <= t for f in _sources() + _headers())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, out_dir: str = None, defines=(),
+          src_dir: str = None) -> str:
+    """Compile and link; `out_dir`, `defines` (kernel tuning macros such as
+    SOBEL4_RG_MIN_CTAS=3) and `src_dir` build a separate copy for tuning sweeps."""
+    csrc = src_dir or CSRC
+    lib = LIB if out_dir is None else os.path.join(out_dir, "libsobel4.so")
+    out_dir = BUILD if out_dir is None else out_dir
+    if not force and out_dir == BUILD and not defines and src_dir is None and up_to_date():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    srcs = _sources()
+    os.makedirs(out_dir, exist_ok=True)
+    srcs = _sources(csrc)
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, verbose, out_dir, defines, csrc), srcs))
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [NVCC, *ARCH, "-shared", "-Xcompiler", "-fPIC", *objs, "-o", tmp]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

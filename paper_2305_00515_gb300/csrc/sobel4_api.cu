@@ -407,4 +407,28 @@ sobel4_status sobel4_run_host(sobel4_handle h, const uint8_t *h_src, size_t src_
   return SOBEL4_OK;
 }
 
+sobel4_status sobel4_check_magnitude(sobel4_handle h, int32_t s_begin, int32_t s_end,
+                                     uint64_t *mismatches) {
+  if (!h || !mismatches || s_begin < 0 || s_end < s_begin || s_end > 599270401)
+    return SOBEL4_ERR_INVALID_ARG;
+  *mismatches = 0;
+  DeviceGuard g(h->device);
+  unsigned long long *d_bad = nullptr;
+  cudaError_t e = cudaMalloc((void **)&d_bad, sizeof(unsigned long long));
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  unsigned long long bad = 0;
+  e = cudaMemsetAsync(d_bad, 0, sizeof(bad), h->own_stream);
+  if (e == cudaSuccess)
+    e = launch_check_magnitude(s_begin, s_end, d_bad, h->sm_count * 8, h->own_stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->own_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->own_stream);
+  cudaFree(d_bad);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  h->launches += 1;
+  *mismatches = bad;
+  return SOBEL4_OK;
+}
+
 }  // extern "C"
+

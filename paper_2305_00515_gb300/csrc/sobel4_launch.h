@@ -20,4 +20,8 @@ cudaError_t launch_rg_batched(const ImageDesc *d_descs, int n_img, int64_t total
 // DIRECT kernel (one thread per output pixel).
 cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, cudaStream_t st);
 
+// Self-check of the magnitude step over S in [s0, s1); mismatches added to *d_bad.
+cudaError_t launch_check_magnitude(int64_t s0, int64_t s1, unsigned long long *d_bad, int grid,
+                                   cudaStream_t st);
+
 }  // namespace sobel4

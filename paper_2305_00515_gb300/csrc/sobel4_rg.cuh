@@ -13,19 +13,22 @@ namespace sobel4 {
 template <int FMT>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, SOBEL4_RG_MIN_CTAS)
     rg_single_kernel(ImageDesc im, int border, int R, int n_items) {
+  __shared__ WarpRing rings[kWarpsPerCta];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int item = blockIdx.x * kWarpsPerCta + warp;
   if (item >= n_items) return;
   const int band = item / im.n_seg;
   const int seg = item - band * im.n_seg;
-  rg_dispatch<FMT>(im, border, seg, band, R, lane);
+  rg_dispatch<FMT>(im, border, seg, band, R, lane, rings[warp]);
 }
 
 template <int FMT>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, SOBEL4_RG_MIN_CTAS)
     rg_batched_kernel(const ImageDesc *__restrict__ descs, int n_img, int64_t total,
                       unsigned int *queue, int border, int R) {
+  __shared__ WarpRing rings[kWarpsPerCta];
   const int lane = threadIdx.x & 31;
+  WarpRing &ring = rings[threadIdx.x >> 5];
   for (;;) {
     unsigned int got = 0;
     if (lane == 0) got = atomicAdd(queue, 1u);
@@ -42,7 +45,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, SOBEL4_RG_MIN_CTAS)
     const int64_t local = item - im.item0;
     const int band = (int)(local / im.n_seg);
     const int seg = (int)(local - (int64_t)band * im.n_seg);
-    rg_dispatch<FMT>(im, border, seg, band, R, lane);
+    rg_dispatch<FMT>(im, border, seg, band, R, lane, ring);
   }
 }
 
