@@ -162,7 +162,8 @@ ImageDesc make_desc(const uint8_t *src, size_t sp, void *dst, size_t dp, int32_t
   d.n_seg = (W + kSegCols - 1) / kSegCols;
   d.n_band = (H + 2 * R - 1) / (2 * R);
   d.item0 = 0;
-  d.src_aligned = ((uintptr_t)src % 4 == 0) && (sp % 4 == 0);
+  d.src_aligned = ((uintptr_t)src % 16 == 0 && sp % 16 == 0) ? 16
+                  : (((uintptr_t)src % 4 == 0 && sp % 4 == 0) ? 4 : 1);
   const size_t vec = fmt == kF32 ? 16 : (fmt == kU8 ? 4 : 8);
   d.dst_vec = ((uintptr_t)dst % vec == 0) && (dp % vec == 0);
   return d;

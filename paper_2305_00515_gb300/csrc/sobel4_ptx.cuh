@@ -17,6 +17,13 @@ __device__ __forceinline__ void cp_async4(uint32_t dst, const void *src, uint32_
                : "memory");
 }
 
+// 16-byte global -> shared copy (both addresses 16-byte aligned); bytes beyond
+// `nbytes` (0 or 16) are zero-filled.  Bypasses L1 (.cg).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t nbytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(nbytes)
+               : "memory");
+}
+
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
