@@ -183,6 +183,35 @@ sobel4_status sobel4_set_variant(sobel4_handle h, int32_t variant);
 sobel4_status sobel4_check_magnitude(sobel4_handle h, int32_t s_begin, int32_t s_end,
                                      uint64_t *mismatches);
 
+/*
+ * Allocation-free batched run.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate GPU memory -- plugins inside
+ * a host framework that owns every device buffer, services held to a fixed
+ * memory budget, latency-critical threads that must not pay for cudaMalloc or
+ * cudaFree.  It runs the same persistent batched kernel as sobel4_run_batched
+ * on the CURRENT device, with no handle, and calls no cudaMalloc, cudaFree or
+ * other allocating routine.  Its scratch (image descriptors and the
+ * work-queue counter) lives in a static device array of
+ * SOBEL4_STATIC_SCRATCH_BYTES bytes inside the library, which every GPU that
+ * loads the library holds until the process exits.
+ *   h_images, n, border, fmt, stream: as for sobel4_run_batched, with
+ *   1 <= n <= SOBEL4_STATIC_MAX_IMAGES; a larger n returns UNSUPPORTED.
+ * The first call on a device looks up the array's device address and the SM
+ * count; make that first call before any stream capture.  The descriptors are
+ * copied from host stack memory as pageable copies, which return only after
+ * earlier work on `stream` has finished and the bytes are staged; the kernel
+ * itself runs asynchronously.  Every call shares the one array and resets its
+ * queue counter: calls that overlap on the GPU race, so serialise them (for
+ * example on one stream).  The call uses about 52 KB of the calling thread's
+ * stack.  Results equal sobel4_run_batched's bit for bit.
+ * Errors: INVALID_ARG (nothing enqueued), UNSUPPORTED, CUDA.
+ */
+#define SOBEL4_STATIC_MAX_IMAGES 1024
+#define SOBEL4_STATIC_SCRATCH_BYTES (SOBEL4_STATIC_MAX_IMAGES * 64 + 256)
+sobel4_status sobel4_run_batched_static(const sobel4_image *h_images, int32_t n,
+                                        sobel4_border border, sobel4_format fmt,
+                                        cudaStream_t stream);
+
 /* Library version as "major.minor.patch" (static string). */
 const char *sobel4_version(void);
 

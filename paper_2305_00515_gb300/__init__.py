@@ -21,7 +21,7 @@ __all__ = [
     "library_path", "load", "sobel4_create", "sobel4_destroy", "sobel4_run",
     "sobel4_run_batched", "sobel4_run_host", "sobel4_status_string", "sobel4_last_cuda_error",
     "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
-    "EXPORTED_SYMBOLS",
+    "sobel4_run_batched_static", "EXPORTED_SYMBOLS",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -36,6 +36,7 @@ EXPORTED_SYMBOLS = (
     "sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_batched", "sobel4_run_host",
     "sobel4_status_string", "sobel4_last_cuda_error", "sobel4_launch_count",
     "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
+    "sobel4_run_batched_static",
 )
 
 
@@ -92,8 +93,10 @@ def load() -> ctypes.CDLL:
         lib.sobel4_set_variant.argtypes = [vp, i32]
         lib.sobel4_version.restype = ctypes.c_char_p
         lib.sobel4_check_magnitude.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_uint64)]
+        lib.sobel4_run_batched_static.argtypes = [ctypes.POINTER(Image), i32, i32, i32, vp]
         for name in ("sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_batched",
-                     "sobel4_run_host", "sobel4_set_variant", "sobel4_check_magnitude"):
+                     "sobel4_run_host", "sobel4_set_variant", "sobel4_check_magnitude",
+                     "sobel4_run_batched_static"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -121,6 +124,12 @@ def sobel4_run(h, d_src: int, src_pitch: int, d_dst: int, dst_pitch: int, height
 def sobel4_run_batched(h, images, border: int, fmt: int, stream: int) -> int:
     arr = images if isinstance(images, ctypes.Array) else (Image * len(images))(*images)
     return load().sobel4_run_batched(h, arr, len(arr), border, fmt, stream)
+
+
+def sobel4_run_batched_static(images, border: int, fmt: int, stream: int) -> int:
+    """Allocation-free batched run on the current device (no handle)."""
+    arr = images if isinstance(images, ctypes.Array) else (Image * len(images))(*images)
+    return load().sobel4_run_batched_static(arr, len(arr), border, fmt, stream)
 
 
 def sobel4_run_host(h, h_src: int, src_pitch: int, h_dst: int, dst_pitch: int, height: int,

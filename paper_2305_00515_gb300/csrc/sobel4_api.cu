@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -433,3 +434,125 @@ sobel4_status sobel4_check_magnitude(sobel4_handle h, int32_t s_begin, int32_t s
 
 }  // extern "C"
 
+// ---------------------------------------------------------------------------
+// Allocation-free batched entry point.
+//
+// Some callers cannot allocate GPU memory: plugins hosted by a framework that
+// owns every device buffer, services with a fixed memory budget, and
+// latency-critical threads that must not pay for cudaMalloc/cudaFree.  For
+// them, sobel4_run_batched_static runs the same persistent batched kernel
+// without a handle, with its scratch (the image descriptors and the work-queue
+// counter) in the file-scope device array below.  The caller still owns the
+// images.  The array is part of the library's device image, so every GPU that
+// loads the library holds it (about 64 KB) until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kStaticMaxImages = SOBEL4_STATIC_MAX_IMAGES;
+constexpr size_t kStaticDescBytes = sizeof(ImageDesc) * kStaticMaxImages;
+constexpr size_t kStaticScratchBytes = kStaticDescBytes + 256;  // descriptors + queue counter
+constexpr int kStaticChunk = 64;  // descriptors staged per host->device copy
+constexpr int kStaticMaxDevices = 64;
+
+static_assert(sizeof(ImageDesc) == 64, "descriptor size is part of SOBEL4_STATIC_SCRATCH_BYTES");
+static_assert(kStaticScratchBytes == SOBEL4_STATIC_SCRATCH_BYTES, "scratch size mismatch");
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+struct StaticDevice {
+  bool ready = false;
+  unsigned char *scratch = nullptr;  // device address of g_static_scratch on this device
+  int sm_count = 0;
+};
+StaticDevice g_static_dev[kStaticMaxDevices];
+std::mutex g_static_mu;
+
+// Once per device, with that device current: the array's device address (the
+// host-side symbol is only a stand-in and must never reach a kernel) and the
+// SM count.
+cudaError_t static_setup(int dev, StaticDevice **out) {
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  StaticDevice &d = g_static_dev[dev];
+  if (!d.ready) {
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    d.scratch = (unsigned char *)ptr;
+    d.sm_count = sms;
+    d.ready = true;
+  }
+  *out = &d;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" sobel4_status sobel4_run_batched_static(const sobel4_image *imgs, int32_t n,
+                                                   sobel4_border border, sobel4_format fmt,
+                                                   cudaStream_t stream) {
+  if (!imgs || n < 1 || !valid_enum(border, fmt)) return SOBEL4_ERR_INVALID_ARG;
+  if (n > kStaticMaxImages) return SOBEL4_ERR_UNSUPPORTED;
+  for (int32_t i = 0; i < n; ++i) {
+    const sobel4_image &m = imgs[i];
+    if (!m.src || !valid_dst_ptr(m.dst, fmt) ||
+        !valid_shape(m.src_pitch, m.dst_pitch, m.height, m.width, border, fmt))
+      return SOBEL4_ERR_INVALID_ARG;
+  }
+  // Overlap rule: sorted sweep over fixed-size stack arrays (no heap).
+  struct Iv {
+    uintptr_t b, e;
+    bool out;
+  };
+  Iv iv[2 * kStaticMaxImages];
+  for (int32_t i = 0; i < n; ++i) {
+    uintptr_t r[4];
+    ranges(imgs[i].src, imgs[i].src_pitch, imgs[i].dst, imgs[i].dst_pitch, imgs[i].height,
+           imgs[i].width, fmt, r);
+    iv[2 * i] = {r[0], r[1], false};
+    iv[2 * i + 1] = {r[2], r[3], true};
+  }
+  std::sort(iv, iv + 2 * n, [](const Iv &a, const Iv &b) { return a.b < b.b; });
+  uintptr_t end_out = 0, end_in = 0;
+  for (int32_t i = 0; i < 2 * n; ++i) {
+    const Iv &v = iv[i];
+    if (v.out ? (v.b < end_out || v.b < end_in) : (v.b < end_out)) return SOBEL4_ERR_INVALID_ARG;
+    if (v.out) end_out = std::max(end_out, v.e);
+    else end_in = std::max(end_in, v.e);
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices)
+    return SOBEL4_ERR_CUDA;
+  StaticDevice *sd = nullptr;
+  cudaError_t e = static_setup(dev, &sd);
+  if (e != cudaSuccess) return SOBEL4_ERR_CUDA;
+  ImageDesc *d_desc = (ImageDesc *)sd->scratch;
+  unsigned int *d_queue = (unsigned int *)(sd->scratch + kStaticDescBytes);
+  // Descriptors go through a small stack buffer; a copy from pageable memory
+  // returns once the bytes are staged, so the buffer can be reused at once.
+  const int R = kBatchR;
+  ImageDesc chunk[kStaticChunk];
+  int64_t total = 0;
+  for (int32_t i0 = 0; i0 < n; i0 += kStaticChunk) {
+    const int cnt = std::min<int32_t>(kStaticChunk, n - i0);
+    for (int j = 0; j < cnt; ++j) {
+      const sobel4_image &m = imgs[i0 + j];
+      ImageDesc d = make_desc(m.src, m.src_pitch, m.dst, m.dst_pitch, m.height, m.width, fmt, R);
+      d.item0 = total;
+      total += (int64_t)d.n_seg * d.n_band;
+      chunk[j] = d;
+    }
+    e = cudaMemcpyAsync(d_desc + i0, chunk, sizeof(ImageDesc) * cnt, cudaMemcpyHostToDevice,
+                        stream);
+    if (e != cudaSuccess) return SOBEL4_ERR_CUDA;
+  }
+  if (total >= (1ll << 31)) return SOBEL4_ERR_UNSUPPORTED;
+  e = cudaMemsetAsync(d_queue, 0, sizeof(unsigned int), stream);  // the queue starts at zero
+  if (e != cudaSuccess) return SOBEL4_ERR_CUDA;
+  const int64_t want = (total + kWarpsPerCta - 1) / kWarpsPerCta;
+  const int grid = (int)std::min<int64_t>(want, (int64_t)sd->sm_count * 4);
+  e = launch_rg_batched(d_desc, n, total, d_queue, border, fmt, R, std::max(grid, 1), stream);
+  return e == cudaSuccess ? SOBEL4_OK : SOBEL4_ERR_CUDA;
+}
