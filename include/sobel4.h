@@ -92,7 +92,7 @@ typedef struct {
   int32_t variant;               /* sobel4_variant; 0 = AUTO */
   int32_t rows_per_strip;        /* RG strip height R (rows per thread per strip); 0 = auto */
   int32_t persistent_ctas_per_sm;/* batched kernel CTAs per SM; 0 = auto */
-  int32_t reserved;              /* must be 0 */
+  int32_t columns_per_lane;      /* RG columns per thread: 2 or 4; 0 = default */
 } sobel4_options;
 
 /* One image of a batch (all pointers are device pointers). */

@@ -56,7 +56,7 @@ class Image(ctypes.Structure):
 class Options(ctypes.Structure):
     """``sobel4_options``."""
     _fields_ = [("variant", ctypes.c_int32), ("rows_per_strip", ctypes.c_int32),
-                ("persistent_ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("persistent_ctas_per_sm", ctypes.c_int32), ("columns_per_lane", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -104,9 +104,9 @@ def load() -> ctypes.CDLL:
 
 # -- one-to-one C ABI wrappers (raw pointers; return the status code) ----------
 def sobel4_create(device: int = 0, variant: int = 0, rows_per_strip: int = 0,
-                  persistent_ctas_per_sm: int = 0):
+                  persistent_ctas_per_sm: int = 0, columns_per_lane: int = 0):
     h = ctypes.c_void_p()
-    opt = Options(variant, rows_per_strip, persistent_ctas_per_sm, 0)
+    opt = Options(variant, rows_per_strip, persistent_ctas_per_sm, columns_per_lane)
     st = load().sobel4_create(ctypes.byref(h), device, ctypes.byref(opt))
     return st, h
 
@@ -175,8 +175,9 @@ class Sobel4:
     """A library handle bound to one CUDA device."""
 
     def __init__(self, device: int = 0, variant: str = "auto", rows_per_strip: int = 0,
-                 persistent_ctas_per_sm: int = 0):
-        st, h = sobel4_create(device, VARIANTS[variant], rows_per_strip, persistent_ctas_per_sm)
+                 persistent_ctas_per_sm: int = 0, columns_per_lane: int = 0):
+        st, h = sobel4_create(device, VARIANTS[variant], rows_per_strip, persistent_ctas_per_sm,
+                              columns_per_lane)
         _check(st, "sobel4_create")
         self.handle = h
         self.device = device

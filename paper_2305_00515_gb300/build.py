@@ -31,10 +31,11 @@ def _headers():
     return hs + [os.path.join(INCLUDE, "sobel4.h")]
 
 
-def _compile(src: str, verbose: bool, out_dir: str = BUILD, defines=(), csrc: str = CSRC) -> str:
+def _compile(src: str, verbose: bool, out_dir: str = BUILD, defines=(), csrc: str = CSRC,
+             extra=()) -> str:
     obj = os.path.join(out_dir, os.path.basename(src).replace(".cu", ".o"))
     cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-           "-I", INCLUDE, "-I", csrc, *[f"-D{d}" for d in defines], "-c", src, "-o", obj]
+           "-I", INCLUDE, "-I", csrc, *[f"-D{d}" for d in defines], *extra, "-c", src, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -53,18 +54,20 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, out_dir: str = None, defines=(),
-          src_dir: str = None) -> str:
+          src_dir: str = None, extra_flags=()) -> str:
     """Compile and link; `out_dir`, `defines` (kernel tuning macros such as
     SOBEL4_RG_MIN_CTAS=3) and `src_dir` build a separate copy for tuning sweeps."""
     csrc = src_dir or CSRC
     lib = LIB if out_dir is None else os.path.join(out_dir, "libsobel4.so")
     out_dir = BUILD if out_dir is None else out_dir
-    if not force and out_dir == BUILD and not defines and src_dir is None and up_to_date():
+    if (not force and out_dir == BUILD and not defines and src_dir is None and not extra_flags
+            and up_to_date()):
         return LIB
     os.makedirs(out_dir, exist_ok=True)
     srcs = _sources(csrc)
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose, out_dir, defines, csrc), srcs))
+        objs = list(ex.map(lambda s: _compile(s, verbose, out_dir, defines, csrc, extra_flags),
+                           srcs))
     tmp = lib + f".tmp{os.getpid()}"
     cmd = [NVCC, *ARCH, "-shared", "-Xcompiler", "-fPIC", *objs, "-o", tmp]
     r = subprocess.run(cmd, capture_output=True, text=True)

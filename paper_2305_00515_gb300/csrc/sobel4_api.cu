@@ -14,30 +14,31 @@
 #include "sobel4_launch.h"
 
 namespace sobel4 {
-cudaError_t launch_rg_single_f32(const ImageDesc &, int, int, cudaStream_t);
-cudaError_t launch_rg_single_u8(const ImageDesc &, int, int, cudaStream_t);
-cudaError_t launch_rg_single_s16(const ImageDesc &, int, int, cudaStream_t);
+cudaError_t launch_rg_single_f32(const ImageDesc &, int, int, int, cudaStream_t);
+cudaError_t launch_rg_single_u8(const ImageDesc &, int, int, int, cudaStream_t);
+cudaError_t launch_rg_single_s16(const ImageDesc &, int, int, int, cudaStream_t);
 cudaError_t launch_rg_batched_f32(const ImageDesc *, int, int64_t, unsigned int *, int, int, int,
-                                  cudaStream_t);
+                                  int, cudaStream_t);
 cudaError_t launch_rg_batched_u8(const ImageDesc *, int, int64_t, unsigned int *, int, int, int,
-                                 cudaStream_t);
+                                 int, cudaStream_t);
 cudaError_t launch_rg_batched_s16(const ImageDesc *, int, int64_t, unsigned int *, int, int, int,
-                                  cudaStream_t);
+                                  int, cudaStream_t);
 
-cudaError_t launch_rg_single(const ImageDesc &im, int border, int fmt, int R, cudaStream_t st) {
+cudaError_t launch_rg_single(const ImageDesc &im, int border, int fmt, int R, int nc,
+                             cudaStream_t st) {
   switch (fmt) {
-    case kF32: return launch_rg_single_f32(im, border, R, st);
-    case kU8: return launch_rg_single_u8(im, border, R, st);
-    default: return launch_rg_single_s16(im, border, R, st);
+    case kF32: return launch_rg_single_f32(im, border, R, nc, st);
+    case kU8: return launch_rg_single_u8(im, border, R, nc, st);
+    default: return launch_rg_single_s16(im, border, R, nc, st);
   }
 }
 
 cudaError_t launch_rg_batched(const ImageDesc *d, int n, int64_t total, unsigned int *q,
-                              int border, int fmt, int R, int grid, cudaStream_t st) {
+                              int border, int fmt, int R, int nc, int grid, cudaStream_t st) {
   switch (fmt) {
-    case kF32: return launch_rg_batched_f32(d, n, total, q, border, R, grid, st);
-    case kU8: return launch_rg_batched_u8(d, n, total, q, border, R, grid, st);
-    default: return launch_rg_batched_s16(d, n, total, q, border, R, grid, st);
+    case kF32: return launch_rg_batched_f32(d, n, total, q, border, R, nc, grid, st);
+    case kU8: return launch_rg_batched_u8(d, n, total, q, border, R, nc, grid, st);
+    default: return launch_rg_batched_s16(d, n, total, q, border, R, nc, grid, st);
   }
 }
 }  // namespace sobel4
@@ -46,7 +47,12 @@ using namespace sobel4;
 
 namespace {
 
+#ifndef SOBEL4_DEFAULT_NC
+#define SOBEL4_DEFAULT_NC 4
+#endif
+
 constexpr int kSlots = 4;           // batch descriptor slots in flight per handle
+constexpr int kDefaultNC = SOBEL4_DEFAULT_NC;  // RG columns per lane unless the handle says otherwise
 constexpr int kDefaultR = 32;       // RG strip height for large images
 constexpr int kBatchR = 16;         // RG strip height for batches
 constexpr int kMaxSide = 1 << 28;   // largest accepted height or width
@@ -87,6 +93,7 @@ struct sobel4_ctx {
   int variant = SOBEL4_VARIANT_AUTO;
   int rows_per_strip = 0;
   int ctas_per_sm = 4;
+  int nc = kDefaultNC;  // RG columns per lane (2 or 4)
   uint64_t launches = 0;
   int32_t last_err = 0;
   BatchSlot slots[kSlots];
@@ -141,17 +148,25 @@ void ranges(const uint8_t *src, size_t sp, const void *dst, size_t dp, int32_t H
 
 bool overlaps(uintptr_t a0, uintptr_t a1, uintptr_t b0, uintptr_t b1) { return a0 < b1 && b0 < a1; }
 
+int seg_cols(int nc) { return 32 * nc; }
+
 int pick_R(const sobel4_ctx *h, int32_t H, int32_t W) {
   if (h->rows_per_strip > 0) return h->rows_per_strip;
-  const int64_t n_seg = (W + kSegCols - 1) / kSegCols;
+  const int64_t n_seg = (W + seg_cols(h->nc) - 1) / seg_cols(h->nc);
   const int64_t target = 2ll * h->sm_count * h->ctas_per_sm * kWarpsPerCta;
   int R = kDefaultR;
   while (R > 4 && n_seg * ((H + 2 * R - 1) / (2 * R)) < target) R /= 2;
   return R;
 }
 
+int pow2_align(uintptr_t v) {
+  int a = 1;
+  while (a < 16 && v % (uintptr_t)(2 * a) == 0) a *= 2;
+  return a;
+}
+
 ImageDesc make_desc(const uint8_t *src, size_t sp, void *dst, size_t dp, int32_t H, int32_t W,
-                    int fmt, int R) {
+                    int R, int nc) {
   ImageDesc d;
   memset(&d, 0, sizeof(d));
   d.src = src;
@@ -160,13 +175,12 @@ ImageDesc make_desc(const uint8_t *src, size_t sp, void *dst, size_t dp, int32_t
   d.dp = dp;
   d.H = H;
   d.W = W;
-  d.n_seg = (W + kSegCols - 1) / kSegCols;
+  d.n_seg = (W + seg_cols(nc) - 1) / seg_cols(nc);
   d.n_band = (H + 2 * R - 1) / (2 * R);
   d.item0 = 0;
   d.src_aligned = ((uintptr_t)src % 16 == 0 && sp % 16 == 0) ? 16
                   : (((uintptr_t)src % 4 == 0 && sp % 4 == 0) ? 4 : 1);
-  const size_t vec = fmt == kF32 ? 16 : (fmt == kU8 ? 4 : 8);
-  d.dst_vec = ((uintptr_t)dst % vec == 0) && (dp % vec == 0);
+  d.dst_align = pow2_align((uintptr_t)dst | (uintptr_t)dp);
   return d;
 }
 
@@ -174,12 +188,12 @@ sobel4_status launch_one(sobel4_ctx *h, const uint8_t *src, size_t sp, void *dst
                          int32_t H, int32_t W, int border, int fmt, cudaStream_t stream) {
   cudaError_t e;
   if (h->variant == SOBEL4_VARIANT_DIRECT) {
-    const ImageDesc im = make_desc(src, sp, dst, dp, H, W, fmt, 1);
+    const ImageDesc im = make_desc(src, sp, dst, dp, H, W, 1, h->nc);
     e = launch_direct(im, border, fmt, stream);
   } else {
     const int R = pick_R(h, H, W);
-    const ImageDesc im = make_desc(src, sp, dst, dp, H, W, fmt, R);
-    e = launch_rg_single(im, border, fmt, R, stream);
+    const ImageDesc im = make_desc(src, sp, dst, dp, H, W, R, h->nc);
+    e = launch_rg_single(im, border, fmt, R, h->nc, stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e);
   h->launches += 1;
@@ -218,7 +232,9 @@ sobel4_status sobel4_create(sobel4_handle *out, int32_t device, const sobel4_opt
   *out = nullptr;
   if (opt && (opt->variant < 0 || opt->variant > SOBEL4_VARIANT_RG || opt->rows_per_strip < 0 ||
               opt->rows_per_strip > 4096 || opt->persistent_ctas_per_sm < 0 ||
-              opt->persistent_ctas_per_sm > 64 || opt->reserved != 0))
+              opt->persistent_ctas_per_sm > 64 ||
+              (opt->columns_per_lane != 0 && opt->columns_per_lane != 2 &&
+               opt->columns_per_lane != 4)))
     return SOBEL4_ERR_INVALID_ARG;
   int count = 0;
   cudaError_t e = cudaGetDeviceCount(&count);
@@ -240,6 +256,7 @@ sobel4_status sobel4_create(sobel4_handle *out, int32_t device, const sobel4_opt
     h->variant = opt->variant;
     h->rows_per_strip = opt->rows_per_strip;
     if (opt->persistent_ctas_per_sm > 0) h->ctas_per_sm = opt->persistent_ctas_per_sm;
+    if (opt->columns_per_lane != 0) h->nc = opt->columns_per_lane;
   }
   *out = h;
   return SOBEL4_OK;
@@ -345,7 +362,7 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
   int64_t total = 0;
   for (int32_t i = 0; i < n; ++i) {
     const sobel4_image &m = imgs[i];
-    ImageDesc d = make_desc(m.src, m.src_pitch, m.dst, m.dst_pitch, m.height, m.width, fmt, R);
+    ImageDesc d = make_desc(m.src, m.src_pitch, m.dst, m.dst_pitch, m.height, m.width, R, h->nc);
     d.item0 = total;
     total += (int64_t)d.n_seg * d.n_band;
     slot.h_desc[i] = d;
@@ -357,8 +374,8 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
   if (e != cudaSuccess) return cuda_fail(h, e);
   const int64_t want = (total + kWarpsPerCta - 1) / kWarpsPerCta;
   const int grid = (int)std::min<int64_t>(want, (int64_t)h->sm_count * h->ctas_per_sm);
-  e = launch_rg_batched(slot.d_desc, n, total, slot.d_queue, border, fmt, R, std::max(grid, 1),
-                        stream);
+  e = launch_rg_batched(slot.d_desc, n, total, slot.d_queue, border, fmt, R, h->nc,
+                        std::max(grid, 1), stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
   h->launches += 1;
   e = cudaEventRecord(slot.done, stream);
@@ -539,7 +556,8 @@ extern "C" sobel4_status sobel4_run_batched_static(const sobel4_image *imgs, int
     const int cnt = std::min<int32_t>(kStaticChunk, n - i0);
     for (int j = 0; j < cnt; ++j) {
       const sobel4_image &m = imgs[i0 + j];
-      ImageDesc d = make_desc(m.src, m.src_pitch, m.dst, m.dst_pitch, m.height, m.width, fmt, R);
+      ImageDesc d = make_desc(m.src, m.src_pitch, m.dst, m.dst_pitch, m.height, m.width, R,
+                              kDefaultNC);
       d.item0 = total;
       total += (int64_t)d.n_seg * d.n_band;
       chunk[j] = d;
@@ -553,6 +571,7 @@ extern "C" sobel4_status sobel4_run_batched_static(const sobel4_image *imgs, int
   if (e != cudaSuccess) return SOBEL4_ERR_CUDA;
   const int64_t want = (total + kWarpsPerCta - 1) / kWarpsPerCta;
   const int grid = (int)std::min<int64_t>(want, (int64_t)sd->sm_count * 4);
-  e = launch_rg_batched(d_desc, n, total, d_queue, border, fmt, R, std::max(grid, 1), stream);
+  e = launch_rg_batched(d_desc, n, total, d_queue, border, fmt, R, kDefaultNC, std::max(grid, 1),
+                        stream);
   return e == cudaSuccess ? SOBEL4_OK : SOBEL4_ERR_CUDA;
 }

@@ -8,14 +8,16 @@
 
 namespace sobel4 {
 
-// RG kernel over one image: ceil(items / 4) CTAs of 4 independent warps.
-cudaError_t launch_rg_single(const ImageDesc &im, int border, int fmt, int R, cudaStream_t st);
+// RG kernel over one image with nc (2 or 4) columns per lane: ceil(items / 4)
+// CTAs of 4 independent warps.  im.n_seg must be ceil(W / (32 * nc)).
+cudaError_t launch_rg_single(const ImageDesc &im, int border, int fmt, int R, int nc,
+                             cudaStream_t st);
 
 // Persistent RG kernel over a batch: `grid` CTAs pull warp items from the
 // device counter *d_queue (reset to 0 by the caller before the launch).
 cudaError_t launch_rg_batched(const ImageDesc *d_descs, int n_img, int64_t total_items,
-                              unsigned int *d_queue, int border, int fmt, int R, int grid,
-                              cudaStream_t st);
+                              unsigned int *d_queue, int border, int fmt, int R, int nc,
+                              int grid, cudaStream_t st);
 
 // DIRECT kernel (one thread per output pixel).
 cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, cudaStream_t st);

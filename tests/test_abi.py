@@ -55,7 +55,7 @@ def test_create_rejects_bad_options(lib):
     assert lib.sobel4_create(None, 0, None) == 1
     bad = pkg.Options(0, -1, 0, 0)
     assert lib.sobel4_create(ctypes.byref(h), 0, ctypes.byref(bad)) == 1
-    bad = pkg.Options(0, 0, 0, 5)
+    bad = pkg.Options(0, 0, 0, 3)
     assert lib.sobel4_create(ctypes.byref(h), 0, ctypes.byref(bad)) == 1
 
 
