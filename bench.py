@@ -53,6 +53,11 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rows-per-strip", type=int, default=0)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched, video and serving measurements")
+    ap.add_argument("--video-frames", type=int, default=2000)
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="length of the Poisson serving run (the full configuration is 60)")
     return ap.parse_args()
 
 
@@ -167,16 +172,201 @@ def kernel_source_hash() -> str:
 
 
 def recorded_traffic():
-    """DRAM bytes per launch of the RG kernel from the committed ncu summary,
-    only when that capture was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "rg_f32_8192_traffic.json")
+    """DRAM bytes per launch of the RG kernel from the committed ncu summary
+    (profiles/rg_f32_8192_full.md, lines "kernel_source_hash: ..." and
+    "dram_bytes_per_launch: ..."), only when that capture was taken on the
+    current kernel source; otherwise None."""
+    path = os.path.join(ROOT, "profiles", "rg_f32_8192_full.md")
     if not os.path.exists(path):
         return None
+    fields = {}
     with open(path) as f:
-        d = json.load(f)
-    if d.get("kernel_source_hash") != kernel_source_hash():
+        for line in f:
+            line = line.strip().lstrip("-* ").replace("`", "")
+            if ":" in line:
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip()
+    if fields.get("kernel_source_hash") != kernel_source_hash():
         return None
-    return d.get("dram_bytes_per_launch")
+    try:
+        return int(fields["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ----------------------------------------------------------------------------
+def _events(torch, n):
+    return [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(n)]
+
+
+def bench_batched(torch, pkg, synth, reps: int = 5):
+    """512 ragged images (sides U{37..2048}, seed 1) as ONE persistent launch
+    versus 512 single-image launches on one stream; F32, paper border rule."""
+    import numpy as np
+    imgs = synth.batch_images(512, 1)
+    px = sum(i.size for i in imgs)
+    srcs = [torch.from_numpy(i).cuda() for i in imgs]
+    outs_b = [torch.empty(i.shape, dtype=torch.float32, device="cuda") for i in imgs]
+    outs_s = [torch.empty(i.shape, dtype=torch.float32, device="cuda") for i in imgs]
+    st, h = pkg.sobel4_create(0)
+    assert st == 0
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    descs = (pkg.Image * len(imgs))(*[pkg.Image(s.data_ptr(), s.stride(0), o.data_ptr(),
+                                                 o.stride(0) * 4, *s.shape)
+                                      for s, o in zip(srcs, outs_b)])
+    tuned = pkg.sobel4_tune_batched(h, descs, 0, 0)[1]
+
+    def batched():
+        assert pkg.sobel4_run_batched(h, descs, 0, 0, sh) == 0
+
+    def singles():
+        for s_, o in zip(srcs, outs_s):
+            assert pkg.sobel4_run(h, s_.data_ptr(), s_.stride(0), o.data_ptr(), o.stride(0) * 4,
+                                  s_.shape[0], s_.shape[1], 0, 0, sh) == 0
+
+    res = {}
+    for name, fn in (("one_persistent_launch", batched), ("separate_launches", singles)):
+        for _ in range(2):
+            fn()
+        ev = _events(torch, reps)
+        with torch.cuda.stream(stream):
+            for a, b in ev:
+                a.record(stream)
+                fn()
+                b.record(stream)
+        stream.synchronize()
+        ms = sorted(a.elapsed_time(b) for a, b in ev)
+        res[name] = {"ms_median": ms[len(ms) // 2], "gpix_s": px / (ms[len(ms) // 2] * 1e-3) / 1e9}
+    torch.cuda.synchronize()
+    same = all(torch.equal(a, b) for a, b in zip(outs_b, outs_s))
+    import oracle
+    for k in (0, 100, 511):
+        assert np.array_equal(outs_b[k].cpu().numpy(),
+                              oracle.default().sobel4(imgs[k], "valid", "f32", threads=8))
+    pkg.sobel4_destroy(h)
+    return {"workload": "512 ragged uint8 images, sides U{37..2048} (seed 1), F32, VALID",
+            "pixels": px, **res, "speedup": res["separate_launches"]["ms_median"] /
+            res["one_persistent_launch"]["ms_median"], "tuned_us": tuned,
+            "batch_equals_single_runs": bool(same)}
+
+
+def bench_video(torch, pkg, synth, frames: int, slots: int = 4):
+    """3840x2160 frames through the graph-captured pipeline (H2D + kernel + D2H
+    per frame, `slots` frame slots); the slot buffers hold pre-generated frames
+    (frame k uses the frame of slot k mod slots)."""
+    import numpy as np
+    H, W = 2160, 3840
+    bg = synth.video_background(H, W, 3)
+    with pkg.Sobel4(0) as s:
+        pipe = pkg.Pipeline(s, H, W, "valid", "f32", slots=slots)
+        ring = [synth.video_frame(bg, k, H, W, 3) for k in range(slots)]
+        for k in range(slots):
+            pipe.inputs[k][:] = ring[k]
+        for k in range(slots):  # warm up
+            pipe.submit(k)
+        for k in range(slots):
+            pipe.wait(k)
+        t0 = time.perf_counter()
+        for k in range(frames):
+            slot = k % slots
+            pipe.wait(slot)
+            pipe.submit(slot)
+        for k in range(slots):
+            pipe.wait(k)
+        dt = time.perf_counter() - t0
+        import oracle
+        last = (frames - 1) % slots
+        ok = np.array_equal(pipe.outputs[last],
+                            oracle.default().sobel4(ring[last], "valid", "f32", threads=8))
+        pipe.close()
+    fps = frames / dt
+    bytes_per_frame = H * W * 5
+    return {"workload": f"{frames} frames of 3840x2160 u8 -> f32 through {slots} graph slots",
+            "frames_per_s": fps, "ms_per_frame": 1e3 / fps, "gpix_s": fps * H * W / 1e9,
+            "host_link_gb_s": fps * bytes_per_frame / 1e9, "last_frame_matches_oracle": bool(ok)}
+
+
+def bench_serving(torch, pkg, synth, seconds: float):
+    """Poisson arrivals (400 req/s) of the serving resolution mix through the
+    continuous-batching server, batched and plain (one launch per request);
+    p50/p99 latency from submit to result in host memory; then a saturation
+    burst (every request submitted at once) for throughput."""
+    import numpy as np
+    import threading
+    t_arr, shapes = synth.serving_trace(400.0, seconds, 4)
+    pool = {}
+    for (H, W, _) in synth.SERVING_MIX:
+        srcs = []
+        for k in range(4):
+            t = torch.empty((H, W), dtype=torch.uint8, pin_memory=True)
+            t.copy_(torch.from_numpy(synth.rects_noise(H, W, 70 + k)))
+            srcs.append(t)
+        outs = [torch.empty((H, W), dtype=torch.float32, pin_memory=True) for _ in range(48)]
+        pool[(H, W)] = (srcs, outs)
+
+    def run(plain: int, arrivals):
+        with pkg.Sobel4(0) as s:
+            st, srv = pkg.sobel4_server_create(s.handle, 8 << 30, 0, 0, 0, plain)
+            assert st == 0
+            tickets = []
+            counters = {k: 0 for k in pool}
+            free = {k: threading.Semaphore(len(v[1])) for k, v in pool.items()}
+            lat = []
+            done = threading.Event()
+
+            def collector():
+                i = 0
+                while i < len(arrivals):
+                    while i >= len(tickets):
+                        time.sleep(0.0002)
+                    t, key = tickets[i]
+                    rc, l = pkg.sobel4_server_wait(srv, t, -1)
+                    assert rc == 0
+                    lat.append(l)
+                    free[key].release()
+                    i += 1
+                done.set()
+
+            th = threading.Thread(target=collector, daemon=True)
+            th.start()
+            t0 = time.perf_counter()
+            for ta, (H, W) in zip(arrivals, shapes):
+                now = time.perf_counter() - t0
+                if ta > now:
+                    time.sleep(ta - now)
+                key = (H, W)
+                free[key].acquire()
+                srcs, outs = pool[key]
+                c = counters[key]
+                counters[key] += 1
+                src, out = srcs[c % len(srcs)], outs[c % len(outs)]
+                rc, t = pkg.sobel4_server_submit(srv, src.data_ptr(), W, out.data_ptr(), W * 4,
+                                                 H, W)
+                assert rc == 0
+                tickets.append((t, key))
+            done.wait()
+            span = time.perf_counter() - t0
+            stats = pkg.sobel4_server_stats(srv)[1]
+            pkg.sobel4_server_destroy(srv)
+        px = sum(h * w for h, w in shapes[:len(arrivals)])
+        lat = np.array(lat)
+        return {"p50_ms": float(np.percentile(lat, 50)) / 1e3,
+                "p99_ms": float(np.percentile(lat, 99)) / 1e3,
+                "mean_ms": float(lat.mean()) / 1e3, "gpix_s": px / span / 1e9,
+                "requests": len(arrivals), "batches": stats["batches"],
+                "max_batch": stats["max_batch_seen"], "span_s": span}
+
+    res = {}
+    for name, plain in (("batched", 0), ("plain_launch_per_request", 1)):
+        res[name] = run(plain, t_arr)
+    burst = np.zeros(min(len(t_arr), 2000))
+    for name, plain in (("burst_batched", 0), ("burst_plain", 1)):
+        res[name] = run(plain, burst)
+    return {"workload": f"Poisson 400 req/s for {seconds:.0f} s ({len(t_arr)} requests), "
+                        "640x480 40% / 1280x720 30% / 1920x1080 20% / 3840x2160 10%, F32, "
+                        "8 GiB admission budget; burst = 2000 requests at t=0", **res}
 
 
 # ----------------------------------------------------------------------------
@@ -336,6 +526,15 @@ def run_ours(args, world, rank, local):
                "ms_per_step": dt * 1e3 / args.e2e_steps, "steps": args.e2e_steps}
     pkg.sobel4_destroy(h)
 
+    extras = {}
+    if world == 1 and not args.no_extras:
+        del srcs, outs
+        torch.cuda.empty_cache()
+        extras["batched"] = bench_batched(torch, pkg, synth)
+        torch.cuda.empty_cache()
+        extras["video"] = bench_video(torch, pkg, synth, args.video_frames)
+        extras["serving"] = bench_serving(torch, pkg, synth, args.serve_seconds)
+
     if rank != 0:
         return
     cpu = None
@@ -360,6 +559,7 @@ def run_ours(args, world, rank, local):
         "cpu_baseline": cpu,
         "clocks": clocks.summary(),
         "gpu_launches": int(launches),
+        **extras,
     }
     print(json.dumps(line), flush=True)
 

@@ -212,6 +212,136 @@ sobel4_status sobel4_run_batched_static(const sobel4_image *h_images, int32_t n,
                                         sobel4_border border, sobel4_format fmt,
                                         cudaStream_t stream);
 
+/*
+ * Autotuner: the per-shape form of the paper's block-configuration study
+ * (Fig. 5, Section 5.2).  sobel4_tune times the register-window kernel for
+ * every candidate (2 or 4 columns per thread x strip height R in 8, 16, 32,
+ * 64; restricted by options that force either) on a height x width image in
+ * scratch device buffers it allocates and frees, and records the fastest in
+ * the handle's table under the bucket (ceil log2 height, ceil log2 width,
+ * fmt).  Later sobel4_run calls whose shape falls in that bucket use it.
+ * *best_us (may be NULL) receives the chosen candidate's median time in
+ * microseconds.  Synchronous.  Errors: INVALID_ARG, OOM, CUDA.
+ */
+sobel4_status sobel4_tune(sobel4_handle h, int32_t height, int32_t width, sobel4_border border,
+                          sobel4_format fmt, float *best_us);
+
+/*
+ * Autotune the batched kernel on a real batch (columns per thread 2/4 x strip
+ * height 8/16/32 x 2/4/6 CTAs per SM): runs sobel4_run_batched repeatedly on
+ * `h_images` (their outputs are written), keeps the fastest for batches of
+ * format `fmt`.  Synchronous.  Errors as sobel4_run_batched.
+ */
+sobel4_status sobel4_tune_batched(sobel4_handle h, const sobel4_image *h_images, int32_t n,
+                                  sobel4_border border, sobel4_format fmt, float *best_us);
+
+/* Number of entries in the handle's tuned table. */
+int32_t sobel4_tune_entries(sobel4_handle h);
+
+/*
+ * Write the tuned table to `path` as JSON (written to path.tmp, then renamed
+ * over path).  The file records the device name, SM count and library
+ * version.  Errors: INVALID_ARG (bad path or write failure).
+ */
+sobel4_status sobel4_tune_save(sobel4_handle h, const char *path);
+
+/*
+ * Merge a table written by sobel4_tune_save into the handle.  A file tuned on
+ * another device model returns UNSUPPORTED and changes nothing; a missing,
+ * malformed or out-of-range file returns INVALID_ARG and changes nothing.
+ * sobel4_create loads the file named by the SOBEL4_TUNE_CACHE environment
+ * variable, when set, the same way.
+ */
+sobel4_status sobel4_tune_load(sobel4_handle h, const char *path);
+
+/*
+ * Graph-captured video pipeline: the stream processing the paper proposes for
+ * its IO bottleneck (Section 5.2, Section 6).  A pipeline owns `slots` (2..64)
+ * frame slots for height x width frames of one border rule and format; each
+ * slot has pinned host input and output buffers, device buffers, its own
+ * stream and an instantiated CUDA graph of host->device copy, kernel and
+ * device->host copy.  While one slot's kernel runs, other slots' copies run.
+ * Usage per frame: wait(slot) (its previous frame is done and its output
+ * readable), write the frame into the slot's input buffer, submit(slot).
+ * Host buffers use the pitches reported by sobel4_pipeline_buffers; S16X4
+ * outputs hold 4 planes of `height` rows.  The handle must outlive the
+ * pipeline; its kernel configuration at creation time is frozen into the graphs.
+ */
+typedef struct sobel4_pipeline_ctx *sobel4_pipeline;
+
+/* Errors: INVALID_ARG, OOM, CUDA.  On error *out is NULL. */
+sobel4_status sobel4_pipeline_create(sobel4_handle h, int32_t height, int32_t width,
+                                     sobel4_border border, sobel4_format fmt, int32_t slots,
+                                     sobel4_pipeline *out);
+
+/* The slot's pinned buffers and their row pitches (any pointer may be NULL). */
+sobel4_status sobel4_pipeline_buffers(sobel4_pipeline p, int32_t slot, uint8_t **h_in,
+                                      void **h_out, size_t *in_pitch, size_t *out_pitch);
+
+/* Launch the slot's graph; INVALID_ARG if the slot's previous frame was not waited for. */
+sobel4_status sobel4_pipeline_submit(sobel4_pipeline p, int32_t slot);
+
+/* Block until the slot's last submitted frame is complete (OK if none is pending). */
+sobel4_status sobel4_pipeline_wait(sobel4_pipeline p, int32_t slot);
+
+/* Wait for all slots and release everything.  NULL is a no-op. */
+sobel4_status sobel4_pipeline_destroy(sobel4_pipeline p);
+
+/*
+ * Continuous-batching request server.  A scheduler thread admits submitted
+ * requests first-in first-out while a device-memory arena of
+ * `memory_budget` bytes (allocated once, at creation) has room for their
+ * input and output, uploads them on a copy stream, packs everything admitted
+ * into one persistent batched launch (sobel4_run_batched; at most two batches
+ * on the GPU at once, so requests arriving while a batch runs join the next),
+ * and downloads results on a third stream.  With plain = 1 each request is
+ * its own sobel4_run launch instead (the comparison point).  Host buffers
+ * passed to submit must stay valid until wait returns; pinned host memory
+ * keeps the copies asynchronous (pageable memory serialises them).  Every
+ * result equals sobel4_run's output for that image.
+ */
+typedef struct sobel4_server_ctx *sobel4_server;
+
+typedef struct {
+  int64_t memory_budget; /* device bytes for admitted requests; 0 = 8 GiB */
+  int32_t max_batch;     /* images per launch; 0 = 256 */
+  int32_t border;        /* sobel4_border of every request */
+  int32_t format;        /* sobel4_format of every request */
+  int32_t plain;         /* 1 = one launch per request, 0 = batched */
+} sobel4_server_options;
+
+typedef struct {
+  uint64_t submitted, completed, batches, max_batch_seen;
+  int64_t device_bytes_in_use, device_bytes_peak;
+} sobel4_server_counters;
+
+/* Start a server on the handle's device.  Errors: INVALID_ARG, OOM, CUDA. */
+sobel4_status sobel4_server_create(sobel4_handle h, const sobel4_server_options *opt,
+                                   sobel4_server *out);
+
+/*
+ * Queue one request (host image, host output in the server's format and
+ * border).  *ticket identifies it.  Errors: INVALID_ARG, UNSUPPORTED (larger
+ * than the whole budget), CUDA (the server has failed).
+ */
+sobel4_status sobel4_server_submit(sobel4_server s, const uint8_t *h_src, size_t src_pitch,
+                                   void *h_dst, size_t dst_pitch, int32_t height, int32_t width,
+                                   uint64_t *ticket);
+
+/*
+ * Wait for a request (timeout_us < 0: no limit).  On success the output is in
+ * h_dst, *latency_us (may be NULL) holds submit-to-completion time, and the
+ * ticket is retired.  TIMEOUT if it is still pending (the ticket stays valid).
+ */
+sobel4_status sobel4_server_wait(sobel4_server s, uint64_t ticket, int64_t timeout_us,
+                                 double *latency_us);
+
+/* Counters and the arena's current and peak use. */
+sobel4_status sobel4_server_stats(sobel4_server s, sobel4_server_counters *out);
+
+/* Finish every submitted request, stop the scheduler, release the arena. */
+sobel4_status sobel4_server_destroy(sobel4_server s);
+
 /* Library version as "major.minor.patch" (static string). */
 const char *sobel4_version(void);
 

@@ -21,7 +21,11 @@ __all__ = [
     "library_path", "load", "sobel4_create", "sobel4_destroy", "sobel4_run",
     "sobel4_run_batched", "sobel4_run_host", "sobel4_status_string", "sobel4_last_cuda_error",
     "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
-    "sobel4_run_batched_static", "EXPORTED_SYMBOLS",
+    "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched", "sobel4_tune_entries",
+    "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create", "sobel4_pipeline_buffers",
+    "sobel4_pipeline_submit", "sobel4_pipeline_wait", "sobel4_pipeline_destroy", "Pipeline",
+    "sobel4_server_create", "sobel4_server_submit", "sobel4_server_wait", "sobel4_server_stats",
+    "sobel4_server_destroy", "ServerOptions", "ServerStats", "EXPORTED_SYMBOLS",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -36,7 +40,11 @@ EXPORTED_SYMBOLS = (
     "sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_batched", "sobel4_run_host",
     "sobel4_status_string", "sobel4_last_cuda_error", "sobel4_launch_count",
     "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
-    "sobel4_run_batched_static",
+    "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched", "sobel4_tune_entries",
+    "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create", "sobel4_pipeline_buffers",
+    "sobel4_pipeline_submit", "sobel4_pipeline_wait", "sobel4_pipeline_destroy",
+    "sobel4_server_create", "sobel4_server_submit", "sobel4_server_wait", "sobel4_server_stats",
+    "sobel4_server_destroy",
 )
 
 
@@ -51,6 +59,19 @@ class Image(ctypes.Structure):
     _fields_ = [("src", ctypes.c_void_p), ("src_pitch", ctypes.c_size_t),
                 ("dst", ctypes.c_void_p), ("dst_pitch", ctypes.c_size_t),
                 ("height", ctypes.c_int32), ("width", ctypes.c_int32)]
+
+
+class ServerOptions(ctypes.Structure):
+    """``sobel4_server_options``."""
+    _fields_ = [("memory_budget", ctypes.c_int64), ("max_batch", ctypes.c_int32),
+                ("border", ctypes.c_int32), ("format", ctypes.c_int32), ("plain", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    """``sobel4_server_counters``."""
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("max_batch_seen", ctypes.c_uint64),
+                ("device_bytes_in_use", ctypes.c_int64), ("device_bytes_peak", ctypes.c_int64)]
 
 
 class Options(ctypes.Structure):
@@ -94,9 +115,33 @@ def load() -> ctypes.CDLL:
         lib.sobel4_version.restype = ctypes.c_char_p
         lib.sobel4_check_magnitude.argtypes = [vp, i32, i32, ctypes.POINTER(ctypes.c_uint64)]
         lib.sobel4_run_batched_static.argtypes = [ctypes.POINTER(Image), i32, i32, i32, vp]
+        fp = ctypes.POINTER(ctypes.c_float)
+        lib.sobel4_tune.argtypes = [vp, i32, i32, i32, i32, fp]
+        lib.sobel4_tune_batched.argtypes = [vp, ctypes.POINTER(Image), i32, i32, i32, fp]
+        lib.sobel4_tune_entries.argtypes = [vp]
+        lib.sobel4_tune_entries.restype = i32
+        lib.sobel4_tune_save.argtypes = [vp, ctypes.c_char_p]
+        lib.sobel4_tune_load.argtypes = [vp, ctypes.c_char_p]
+        lib.sobel4_pipeline_create.argtypes = [vp, i32, i32, i32, i32, i32, ctypes.POINTER(vp)]
+        lib.sobel4_pipeline_buffers.argtypes = [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                                ctypes.POINTER(sz), ctypes.POINTER(sz)]
+        lib.sobel4_pipeline_submit.argtypes = [vp, i32]
+        lib.sobel4_pipeline_wait.argtypes = [vp, i32]
+        lib.sobel4_pipeline_destroy.argtypes = [vp]
+        lib.sobel4_server_create.argtypes = [vp, ctypes.POINTER(ServerOptions), ctypes.POINTER(vp)]
+        lib.sobel4_server_submit.argtypes = [vp, vp, sz, vp, sz, i32, i32,
+                                             ctypes.POINTER(ctypes.c_uint64)]
+        lib.sobel4_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_int64,
+                                           ctypes.POINTER(ctypes.c_double)]
+        lib.sobel4_server_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+        lib.sobel4_server_destroy.argtypes = [vp]
         for name in ("sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_batched",
                      "sobel4_run_host", "sobel4_set_variant", "sobel4_check_magnitude",
-                     "sobel4_run_batched_static"):
+                     "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched",
+                     "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create",
+                     "sobel4_pipeline_buffers", "sobel4_pipeline_submit", "sobel4_pipeline_wait",
+                     "sobel4_pipeline_destroy", "sobel4_server_create", "sobel4_server_submit",
+                     "sobel4_server_wait", "sobel4_server_stats", "sobel4_server_destroy"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -159,6 +204,136 @@ def sobel4_check_magnitude(h, s_begin: int, s_end: int):
     n = ctypes.c_uint64()
     st = load().sobel4_check_magnitude(h, s_begin, s_end, ctypes.byref(n))
     return st, n.value
+
+
+def sobel4_tune(h, height: int, width: int, border: int, fmt: int):
+    """(status, best_us) of the per-shape autotuner."""
+    us = ctypes.c_float()
+    st = load().sobel4_tune(h, height, width, border, fmt, ctypes.byref(us))
+    return st, us.value
+
+
+def sobel4_tune_batched(h, images, border: int, fmt: int):
+    """(status, best_us) of the batch autotuner (runs the batch repeatedly)."""
+    arr = images if isinstance(images, ctypes.Array) else (Image * len(images))(*images)
+    us = ctypes.c_float()
+    st = load().sobel4_tune_batched(h, arr, len(arr), border, fmt, ctypes.byref(us))
+    return st, us.value
+
+
+def sobel4_tune_entries(h) -> int:
+    return load().sobel4_tune_entries(h)
+
+
+def sobel4_tune_save(h, path: str) -> int:
+    return load().sobel4_tune_save(h, path.encode())
+
+
+def sobel4_tune_load(h, path: str) -> int:
+    return load().sobel4_tune_load(h, path.encode())
+
+
+def sobel4_pipeline_create(h, height: int, width: int, border: int, fmt: int, slots: int):
+    p = ctypes.c_void_p()
+    st = load().sobel4_pipeline_create(h, height, width, border, fmt, slots, ctypes.byref(p))
+    return st, p
+
+
+def sobel4_pipeline_buffers(p, slot: int):
+    """(status, h_in, h_out, in_pitch, out_pitch) of one slot."""
+    a, b = ctypes.c_void_p(), ctypes.c_void_p()
+    ip, op = ctypes.c_size_t(), ctypes.c_size_t()
+    st = load().sobel4_pipeline_buffers(p, slot, ctypes.byref(a), ctypes.byref(b),
+                                        ctypes.byref(ip), ctypes.byref(op))
+    return st, a.value, b.value, ip.value, op.value
+
+
+def sobel4_pipeline_submit(p, slot: int) -> int:
+    return load().sobel4_pipeline_submit(p, slot)
+
+
+def sobel4_pipeline_wait(p, slot: int) -> int:
+    return load().sobel4_pipeline_wait(p, slot)
+
+
+def sobel4_pipeline_destroy(p) -> int:
+    return load().sobel4_pipeline_destroy(p)
+
+
+class Pipeline:
+    """numpy views over a graph-captured video pipeline's pinned slot buffers."""
+
+    def __init__(self, sobel: "Sobel4", height: int, width: int, border: str = "valid",
+                 fmt: str = "f32", slots: int = 2):
+        import numpy as np
+        st, p = sobel4_pipeline_create(sobel.handle, height, width, BORDERS[border],
+                                       FORMATS[fmt], slots)
+        _check(st, "sobel4_pipeline_create")
+        self.p, self.slots, self.H, self.W, self.fmt = p, slots, height, width, fmt
+        dtype = {"f32": np.float32, "u8": np.uint8, "s16x4": np.int16}[fmt]
+        planes = 4 if fmt == "s16x4" else 1
+        self.inputs, self.outputs = [], []
+        for k in range(slots):
+            st, a, b, ip, op = sobel4_pipeline_buffers(p, k)
+            _check(st, "sobel4_pipeline_buffers")
+            raw_in = (ctypes.c_uint8 * (ip * height)).from_address(a)
+            raw_out = (ctypes.c_uint8 * (op * height * planes)).from_address(b)
+            vin = np.frombuffer(raw_in, dtype=np.uint8).reshape(height, ip)[:, :width]
+            vout = np.frombuffer(raw_out, dtype=np.uint8).reshape(planes * height, op)
+            vout = vout[:, :width * ELEM_SIZE[fmt]].view(dtype)
+            self.inputs.append(vin)
+            self.outputs.append(vout.reshape(4, height, width) if planes == 4 else vout)
+
+    def submit(self, slot: int):
+        _check(sobel4_pipeline_submit(self.p, slot), "sobel4_pipeline_submit")
+
+    def wait(self, slot: int):
+        _check(sobel4_pipeline_wait(self.p, slot), "sobel4_pipeline_wait")
+
+    def close(self):
+        if getattr(self, "p", None):
+            sobel4_pipeline_destroy(self.p)
+            self.p = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sobel4_server_create(h, memory_budget: int = 0, max_batch: int = 0, border: int = 0,
+                         fmt: int = 0, plain: int = 0):
+    srv = ctypes.c_void_p()
+    opt = ServerOptions(memory_budget, max_batch, border, fmt, plain)
+    st = load().sobel4_server_create(h, ctypes.byref(opt), ctypes.byref(srv))
+    return st, srv
+
+
+def sobel4_server_submit(srv, h_src: int, src_pitch: int, h_dst: int, dst_pitch: int,
+                         height: int, width: int):
+    """(status, ticket)."""
+    t = ctypes.c_uint64()
+    st = load().sobel4_server_submit(srv, h_src, src_pitch, h_dst, dst_pitch, height, width,
+                                     ctypes.byref(t))
+    return st, t.value
+
+
+def sobel4_server_wait(srv, ticket: int, timeout_us: int = -1):
+    """(status, latency_us)."""
+    lat = ctypes.c_double()
+    st = load().sobel4_server_wait(srv, ticket, timeout_us, ctypes.byref(lat))
+    return st, lat.value
+
+
+def sobel4_server_stats(srv):
+    out = ServerStats()
+    st = load().sobel4_server_stats(srv, ctypes.byref(out))
+    return st, {f: getattr(out, f) for f, _ in ServerStats._fields_}
+
+
+def sobel4_server_destroy(srv) -> int:
+    return load().sobel4_server_destroy(srv)
 
 
 def sobel4_version() -> str:

@@ -5,9 +5,13 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <stdio.h>
+#include <stdlib.h>
+
 #include <algorithm>
 #include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "sobel4.h"
@@ -53,7 +57,7 @@ namespace {
 
 constexpr int kSlots = 4;           // batch descriptor slots in flight per handle
 constexpr int kDefaultNC = SOBEL4_DEFAULT_NC;  // RG columns per lane unless the handle says otherwise
-constexpr int kDefaultR = 32;       // RG strip height for large images
+constexpr int kDefaultR = 16;       // RG strip height for large images (measured best on 8192^2)
 constexpr int kBatchR = 16;         // RG strip height for batches
 constexpr int kMaxSide = 1 << 28;   // largest accepted height or width
 constexpr uint64_t kMaxPitch = (1ull << 31) - 1;
@@ -87,6 +91,14 @@ class DeviceGuard {
 
 }  // namespace
 
+// One autotuned configuration: kind 0 = single image bucket (hb, wb) =
+// (ceil log2 height, ceil log2 width); kind 1 = batches of format fmt.
+struct TuneEntry {
+  int kind, hb, wb, fmt;
+  int nc, R, ctas;
+  float us;
+};
+
 struct sobel4_ctx {
   int device = 0;
   int sm_count = 0;
@@ -94,6 +106,7 @@ struct sobel4_ctx {
   int rows_per_strip = 0;
   int ctas_per_sm = 4;
   int nc = kDefaultNC;  // RG columns per lane (2 or 4)
+  bool nc_forced = false;  // set by the creation options
   uint64_t launches = 0;
   int32_t last_err = 0;
   BatchSlot slots[kSlots];
@@ -103,7 +116,14 @@ struct sobel4_ctx {
   size_t d_in_bytes = 0;
   uint8_t *d_out = nullptr;
   size_t d_out_bytes = 0;
+  std::vector<TuneEntry> tuned;
+  char device_name[256] = {0};
 };
+
+namespace sobel4 {
+HandleInfo handle_info(sobel4_handle h) { return HandleInfo{h->device}; }
+void note_launches(sobel4_handle h, int64_t delta) { h->launches += (uint64_t)delta; }
+}  // namespace sobel4
 
 namespace {
 
@@ -152,11 +172,34 @@ int seg_cols(int nc) { return 32 * nc; }
 
 int pick_R(const sobel4_ctx *h, int32_t H, int32_t W) {
   if (h->rows_per_strip > 0) return h->rows_per_strip;
-  const int64_t n_seg = (W + seg_cols(h->nc) - 1) / seg_cols(h->nc);
+  const int64_t n_seg = (W + seg_cols(h->nc) - 1) / seg_cols(h->nc);  // heuristic at the default NC
   const int64_t target = 2ll * h->sm_count * h->ctas_per_sm * kWarpsPerCta;
   int R = kDefaultR;
   while (R > 4 && n_seg * ((H + 2 * R - 1) / (2 * R)) < target) R /= 2;
   return R;
+}
+
+int ceil_log2(int64_t v) {
+  int b = 0;
+  while ((int64_t(1) << b) < v) ++b;
+  return b;
+}
+
+const TuneEntry *find_tuned(const sobel4_ctx *h, int kind, int32_t H, int32_t W, int fmt) {
+  const int hb = kind == 0 ? ceil_log2(H) : 0, wb = kind == 0 ? ceil_log2(W) : 0;
+  for (const TuneEntry &t : h->tuned)
+    if (t.kind == kind && t.hb == hb && t.wb == wb && t.fmt == fmt) return &t;
+  return nullptr;
+}
+
+// The RG configuration (columns per lane, strip height) for one image:
+// explicit options first, then the tuned table, then the heuristic.
+void rg_config(const sobel4_ctx *h, int32_t H, int32_t W, int fmt, int *nc, int *R) {
+  const TuneEntry *t = find_tuned(h, 0, H, W, fmt);
+  *nc = h->nc_forced ? h->nc : (t ? t->nc : h->nc);
+  if (h->rows_per_strip > 0) *R = h->rows_per_strip;
+  else if (t) *R = t->R;
+  else *R = pick_R(h, H, W);
 }
 
 int pow2_align(uintptr_t v) {
@@ -191,9 +234,10 @@ sobel4_status launch_one(sobel4_ctx *h, const uint8_t *src, size_t sp, void *dst
     const ImageDesc im = make_desc(src, sp, dst, dp, H, W, 1, h->nc);
     e = launch_direct(im, border, fmt, stream);
   } else {
-    const int R = pick_R(h, H, W);
-    const ImageDesc im = make_desc(src, sp, dst, dp, H, W, R, h->nc);
-    e = launch_rg_single(im, border, fmt, R, h->nc, stream);
+    int nc, R;
+    rg_config(h, H, W, fmt, &nc, &R);
+    const ImageDesc im = make_desc(src, sp, dst, dp, H, W, R, nc);
+    e = launch_rg_single(im, border, fmt, R, nc, stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e);
   h->launches += 1;
@@ -245,6 +289,11 @@ sobel4_status sobel4_create(sobel4_handle *out, int32_t device, const sobel4_opt
   if (!h) return SOBEL4_ERR_OOM;
   h->device = device;
   e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) {
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, device);
+    if (e == cudaSuccess) snprintf(h->device_name, sizeof(h->device_name), "%s", prop.name);
+  }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
   for (int i = 0; i < kSlots && e == cudaSuccess; ++i)
     e = cudaEventCreateWithFlags(&h->slots[i].done, cudaEventDisableTiming);
@@ -256,8 +305,13 @@ sobel4_status sobel4_create(sobel4_handle *out, int32_t device, const sobel4_opt
     h->variant = opt->variant;
     h->rows_per_strip = opt->rows_per_strip;
     if (opt->persistent_ctas_per_sm > 0) h->ctas_per_sm = opt->persistent_ctas_per_sm;
-    if (opt->columns_per_lane != 0) h->nc = opt->columns_per_lane;
+    if (opt->columns_per_lane != 0) {
+      h->nc = opt->columns_per_lane;
+      h->nc_forced = true;
+    }
   }
+  const char *cache = getenv("SOBEL4_TUNE_CACHE");
+  if (cache && *cache) sobel4_tune_load(h, cache);  // a missing or foreign cache is ignored
   *out = h;
   return SOBEL4_OK;
 }
@@ -337,7 +391,10 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
     }
     return SOBEL4_OK;
   }
-  const int R = h->rows_per_strip > 0 ? h->rows_per_strip : kBatchR;
+  const TuneEntry *bt = find_tuned(h, 1, 0, 0, fmt);
+  const int R = h->rows_per_strip > 0 ? h->rows_per_strip : (bt ? bt->R : kBatchR);
+  const int bnc = h->nc_forced ? h->nc : (bt ? bt->nc : h->nc);
+  const int bctas = bt ? bt->ctas : h->ctas_per_sm;
   BatchSlot &slot = h->slots[h->next_slot];
   h->next_slot = (h->next_slot + 1) % kSlots;
   cudaError_t e = cudaSuccess;
@@ -362,7 +419,7 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
   int64_t total = 0;
   for (int32_t i = 0; i < n; ++i) {
     const sobel4_image &m = imgs[i];
-    ImageDesc d = make_desc(m.src, m.src_pitch, m.dst, m.dst_pitch, m.height, m.width, R, h->nc);
+    ImageDesc d = make_desc(m.src, m.src_pitch, m.dst, m.dst_pitch, m.height, m.width, R, bnc);
     d.item0 = total;
     total += (int64_t)d.n_seg * d.n_band;
     slot.h_desc[i] = d;
@@ -373,8 +430,8 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
   if (e == cudaSuccess) e = cudaMemsetAsync(slot.d_queue, 0, sizeof(unsigned int), stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
   const int64_t want = (total + kWarpsPerCta - 1) / kWarpsPerCta;
-  const int grid = (int)std::min<int64_t>(want, (int64_t)h->sm_count * h->ctas_per_sm);
-  e = launch_rg_batched(slot.d_desc, n, total, slot.d_queue, border, fmt, R, h->nc,
+  const int grid = (int)std::min<int64_t>(want, (int64_t)h->sm_count * bctas);
+  e = launch_rg_batched(slot.d_desc, n, total, slot.d_queue, border, fmt, R, bnc,
                         std::max(grid, 1), stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
   h->launches += 1;
@@ -574,4 +631,204 @@ extern "C" sobel4_status sobel4_run_batched_static(const sobel4_image *imgs, int
   e = launch_rg_batched(d_desc, n, total, d_queue, border, fmt, R, kDefaultNC, std::max(grid, 1),
                         stream);
   return e == cudaSuccess ? SOBEL4_OK : SOBEL4_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: the per-shape analogue of the paper's block-configuration study
+// (Fig. 5, Section 5.2).  Candidates are timed with CUDA events on the
+// handle's own stream; the fastest is recorded in the handle's table.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kTuneWarmup = 2;
+constexpr int kTuneReps = 7;
+
+template <class Launch>
+cudaError_t median_us(cudaStream_t st, Launch launch, float *us) {
+  cudaEvent_t ev[2 * kTuneReps];
+  for (int i = 0; i < 2 * kTuneReps; ++i) ev[i] = nullptr;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 2 * kTuneReps && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+  for (int i = 0; i < kTuneWarmup && e == cudaSuccess; ++i) e = launch();
+  for (int i = 0; i < kTuneReps && e == cudaSuccess; ++i) {
+    e = cudaEventRecord(ev[2 * i], st);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2 * i + 1], st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  float t[kTuneReps];
+  for (int i = 0; i < kTuneReps && e == cudaSuccess; ++i)
+    e = cudaEventElapsedTime(&t[i], ev[2 * i], ev[2 * i + 1]);
+  for (int i = 0; i < 2 * kTuneReps; ++i)
+    if (ev[i]) cudaEventDestroy(ev[i]);
+  if (e != cudaSuccess) return e;
+  std::sort(t, t + kTuneReps);
+  *us = 1000.0f * t[kTuneReps / 2];
+  return cudaSuccess;
+}
+
+void upsert(sobel4_ctx *h, const TuneEntry &t) {
+  for (TuneEntry &u : h->tuned)
+    if (u.kind == t.kind && u.hb == t.hb && u.wb == t.wb && u.fmt == t.fmt) {
+      u = t;
+      return;
+    }
+  h->tuned.push_back(t);
+}
+
+bool valid_entry(const TuneEntry &t) {
+  return (t.kind == 0 || t.kind == 1) && t.hb >= 0 && t.hb <= 31 && t.wb >= 0 && t.wb <= 31 &&
+         t.fmt >= 0 && t.fmt <= 2 && (t.nc == 2 || t.nc == 4) && t.R >= 1 && t.R <= 4096 &&
+         t.ctas >= 1 && t.ctas <= 64;
+}
+
+}  // namespace
+
+extern "C" sobel4_status sobel4_tune(sobel4_handle h, int32_t height, int32_t width,
+                                     sobel4_border border, sobel4_format fmt, float *best_us) {
+  if (!h) return SOBEL4_ERR_INVALID_ARG;
+  const size_t sp = ((size_t)width + 15) & ~(size_t)15;
+  const size_t dp = ((size_t)width * elem_size(fmt) + 15) & ~(size_t)15;
+  if (!valid_shape(sp, dp, height, width, border, fmt)) return SOBEL4_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  uint8_t *src = nullptr, *dst = nullptr;
+  cudaError_t e = cudaMalloc((void **)&src, sp * (size_t)height);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&dst, dp * (size_t)height * planes(fmt));
+  if (e == cudaSuccess) e = cudaMemsetAsync(src, 0x5A, sp * (size_t)height, h->own_stream);
+  TuneEntry best = {0, ceil_log2(height), ceil_log2(width), (int)fmt, h->nc, 0, h->ctas_per_sm, 0};
+  bool have = false;
+  const int ncs[2] = {2, 4};
+  const int Rs[4] = {8, 16, 32, 64};
+  for (int a = 0; a < 2 && e == cudaSuccess; ++a) {
+    if (h->nc_forced && ncs[a] != h->nc) continue;
+    for (int b = 0; b < 4 && e == cudaSuccess; ++b) {
+      if (h->rows_per_strip > 0 && Rs[b] != h->rows_per_strip) continue;
+      const ImageDesc im = make_desc(src, sp, dst, dp, height, width, Rs[b], ncs[a]);
+      float us = 0.f;
+      e = median_us(h->own_stream, [&]() {
+        h->launches += 1;
+        return launch_rg_single(im, border, fmt, Rs[b], ncs[a], h->own_stream);
+      }, &us);
+      if (e == cudaSuccess && (!have || us < best.us)) {
+        best.nc = ncs[a];
+        best.R = Rs[b];
+        best.us = us;
+        have = true;
+      }
+    }
+  }
+  if (src) cudaFree(src);
+  if (dst) cudaFree(dst);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  upsert(h, best);
+  if (best_us) *best_us = best.us;
+  return SOBEL4_OK;
+}
+
+extern "C" sobel4_status sobel4_tune_batched(sobel4_handle h, const sobel4_image *imgs, int32_t n,
+                                             sobel4_border border, sobel4_format fmt,
+                                             float *best_us) {
+  if (!h || !imgs || n < 1 || !valid_enum(border, fmt)) return SOBEL4_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  const std::vector<TuneEntry> saved = h->tuned;
+  TuneEntry best = {1, 0, 0, (int)fmt, h->nc, kBatchR, h->ctas_per_sm, 0};
+  bool have = false;
+  const int ncs[2] = {2, 4};
+  const int Rs[3] = {8, 16, 32};
+  const int ctas[3] = {2, 4, 6};
+  cudaError_t e = cudaSuccess;
+  sobel4_status st = SOBEL4_OK;
+  for (int a = 0; a < 2 && st == SOBEL4_OK; ++a) {
+    if (h->nc_forced && ncs[a] != h->nc) continue;
+    for (int b = 0; b < 3 && st == SOBEL4_OK; ++b) {
+      if (h->rows_per_strip > 0 && Rs[b] != h->rows_per_strip) continue;
+      for (int c = 0; c < 3 && st == SOBEL4_OK; ++c) {
+        const TuneEntry cand = {1, 0, 0, (int)fmt, ncs[a], Rs[b], ctas[c], 0};
+        h->tuned = saved;
+        upsert(h, cand);
+        float us = 0.f;
+        e = median_us(h->own_stream, [&]() {
+          st = sobel4_run_batched(h, imgs, n, border, fmt, h->own_stream);
+          return st == SOBEL4_OK ? cudaSuccess : cudaErrorUnknown;
+        }, &us);
+        if (st != SOBEL4_OK) break;
+        if (e != cudaSuccess) {
+          st = cuda_fail(h, e);
+          break;
+        }
+        if (!have || us < best.us) {
+          best = cand;
+          best.us = us;
+          have = true;
+        }
+      }
+    }
+  }
+  h->tuned = saved;
+  if (st != SOBEL4_OK) return st;
+  upsert(h, best);
+  if (best_us) *best_us = best.us;
+  return SOBEL4_OK;
+}
+
+extern "C" int32_t sobel4_tune_entries(sobel4_handle h) { return h ? (int32_t)h->tuned.size() : 0; }
+
+extern "C" sobel4_status sobel4_tune_save(sobel4_handle h, const char *path) {
+  if (!h || !path || !*path) return SOBEL4_ERR_INVALID_ARG;
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE *f = fopen(tmp.c_str(), "w");
+  if (!f) return SOBEL4_ERR_INVALID_ARG;
+  fprintf(f, "{\"sobel4_tune\": 1, \"version\": \"%s\", \"device\": \"%s\", \"sm_count\": %d,\n",
+          sobel4_version(), h->device_name, h->sm_count);
+  fprintf(f, " \"entries\": [\n");
+  for (size_t i = 0; i < h->tuned.size(); ++i) {
+    const TuneEntry &t = h->tuned[i];
+    fprintf(f,
+            "  {\"kind\": %d, \"hb\": %d, \"wb\": %d, \"fmt\": %d, \"nc\": %d, \"R\": %d, "
+            "\"ctas\": %d, \"us\": %.3f}%s\n",
+            t.kind, t.hb, t.wb, t.fmt, t.nc, t.R, t.ctas, t.us,
+            i + 1 < h->tuned.size() ? "," : "");
+  }
+  fprintf(f, " ]}\n");
+  const bool ok = fclose(f) == 0;
+  if (!ok || rename(tmp.c_str(), path) != 0) {
+    remove(tmp.c_str());
+    return SOBEL4_ERR_INVALID_ARG;
+  }
+  return SOBEL4_OK;
+}
+
+extern "C" sobel4_status sobel4_tune_load(sobel4_handle h, const char *path) {
+  if (!h || !path) return SOBEL4_ERR_INVALID_ARG;
+  FILE *f = fopen(path, "r");
+  if (!f) return SOBEL4_ERR_INVALID_ARG;
+  char line[512];
+  bool header_ok = false, device_ok = false;
+  std::vector<TuneEntry> got;
+  while (fgets(line, sizeof(line), f)) {
+    if (strstr(line, "\"sobel4_tune\": 1")) {
+      header_ok = true;
+      char want[320];
+      snprintf(want, sizeof(want), "\"device\": \"%s\", \"sm_count\": %d,", h->device_name,
+               h->sm_count);
+      device_ok = strstr(line, want) != nullptr;
+      continue;
+    }
+    TuneEntry t;
+    if (sscanf(line,
+               " {\"kind\": %d, \"hb\": %d, \"wb\": %d, \"fmt\": %d, \"nc\": %d, \"R\": %d, "
+               "\"ctas\": %d, \"us\": %f}",
+               &t.kind, &t.hb, &t.wb, &t.fmt, &t.nc, &t.R, &t.ctas, &t.us) == 8) {
+      if (!valid_entry(t)) {
+        fclose(f);
+        return SOBEL4_ERR_INVALID_ARG;
+      }
+      got.push_back(t);
+    }
+  }
+  fclose(f);
+  if (!header_ok) return SOBEL4_ERR_INVALID_ARG;
+  if (!device_ok) return SOBEL4_ERR_UNSUPPORTED;  // tuned on another device: keep the heuristic
+  for (const TuneEntry &t : got) upsert(h, t);
+  return SOBEL4_OK;
 }

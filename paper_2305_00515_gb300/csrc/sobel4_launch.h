@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "sobel4.h"
 #include "sobel4_device.cuh"
 
 namespace sobel4 {
@@ -25,5 +26,28 @@ cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, cudaStream_t
 // Self-check of the magnitude step over S in [s0, s1); mismatches added to *d_bad.
 cudaError_t launch_check_magnitude(int64_t s0, int64_t s1, unsigned long long *d_bad, int grid,
                                    cudaStream_t st);
+
+// Handle internals shared with the pipeline and server translation units.
+struct HandleInfo {
+  int device;
+};
+__attribute__((visibility("hidden"))) HandleInfo handle_info(sobel4_handle h);
+__attribute__((visibility("hidden"))) void note_launches(sobel4_handle h, int64_t delta);
+
+// Make `dev` current for the lifetime of the guard.
+class DeviceScope {
+ public:
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = -1;
+    if (prev_ != dev) cudaSetDevice(dev);
+  }
+  ~DeviceScope() {
+    int cur = -1;
+    if (prev_ >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev_) cudaSetDevice(prev_);
+  }
+
+ private:
+  int prev_ = -1;
+};
 
 }  // namespace sobel4

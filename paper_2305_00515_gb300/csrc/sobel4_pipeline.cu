@@ -1,0 +1,166 @@
+// sobel4_pipeline.cu — graph-captured video pipeline: per frame slot, one CUDA
+// graph of host->device copy, the RG kernel and device->host copy, launched
+// on the slot's own stream so the copies of one slot overlap the kernel of
+// another.  This is the stream processing that the paper proposes for its
+// IO bottleneck (Section 5.2, Section 6).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <new>
+#include <vector>
+
+#include "sobel4.h"
+#include "sobel4_launch.h"
+
+namespace {
+
+struct Slot {
+  uint8_t *h_in = nullptr;   // pinned
+  void *h_out = nullptr;     // pinned
+  uint8_t *d_in = nullptr;
+  uint8_t *d_out = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t done = nullptr;
+  bool pending = false;
+};
+
+size_t elem_bytes(int fmt) { return fmt == SOBEL4_OUT_F32 ? 4 : (fmt == SOBEL4_OUT_U8 ? 1 : 2); }
+
+}  // namespace
+
+struct sobel4_pipeline_ctx {
+  sobel4_handle h = nullptr;
+  int device = 0;
+  int32_t H = 0, W = 0;
+  int border = 0, fmt = 0;
+  size_t in_pitch = 0, out_pitch = 0, in_bytes = 0, out_bytes = 0;
+  std::vector<Slot> slots;
+};
+
+namespace {
+
+void release(sobel4_pipeline_ctx *p) {
+  for (Slot &s : p->slots) {
+    if (s.stream) cudaStreamSynchronize(s.stream);
+    if (s.exec) cudaGraphExecDestroy(s.exec);
+    if (s.done) cudaEventDestroy(s.done);
+    if (s.stream) cudaStreamDestroy(s.stream);
+    if (s.h_in) cudaFreeHost(s.h_in);
+    if (s.h_out) cudaFreeHost(s.h_out);
+    if (s.d_in) cudaFree(s.d_in);
+    if (s.d_out) cudaFree(s.d_out);
+  }
+  delete p;
+}
+
+}  // namespace
+
+extern "C" sobel4_status sobel4_pipeline_create(sobel4_handle h, int32_t height, int32_t width,
+                                                sobel4_border border, sobel4_format fmt,
+                                                int32_t slots, sobel4_pipeline *out) {
+  if (!out) return SOBEL4_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!h || slots < 2 || slots > 64 || height < 1 || width < 1) return SOBEL4_ERR_INVALID_ARG;
+  const int dev = sobel4::handle_info(h).device;
+  sobel4::DeviceScope scope(dev);
+  sobel4_pipeline_ctx *p = new (std::nothrow) sobel4_pipeline_ctx();
+  if (!p) return SOBEL4_ERR_OOM;
+  p->h = h;
+  p->device = dev;
+  p->H = height;
+  p->W = width;
+  p->border = border;
+  p->fmt = fmt;
+  p->in_pitch = ((size_t)width + 15) & ~(size_t)15;
+  p->out_pitch = ((size_t)width * elem_bytes(fmt) + 15) & ~(size_t)15;
+  const size_t planes = fmt == SOBEL4_OUT_S16X4 ? 4 : 1;
+  p->in_bytes = p->in_pitch * (size_t)height;
+  p->out_bytes = p->out_pitch * (size_t)height * planes;
+  p->slots.resize((size_t)slots);
+  cudaError_t e = cudaSuccess;
+  sobel4_status st = SOBEL4_OK;
+  const uint64_t launches0 = sobel4_launch_count(h);
+  for (Slot &s : p->slots) {
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&s.h_in, p->in_bytes, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc(&s.h_out, p->out_bytes, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s.d_in, p->in_bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s.d_out, p->out_bytes);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+    if (e != cudaSuccess) break;
+    // The input's pitch padding is never read; zero it once so the copies move defined bytes.
+    e = cudaMemsetAsync(s.d_in, 0, p->in_bytes, s.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s.stream);
+    if (e != cudaSuccess) break;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) break;
+    cudaError_t ce = cudaMemcpyAsync(s.d_in, s.h_in, p->in_bytes, cudaMemcpyHostToDevice, s.stream);
+    if (ce == cudaSuccess)
+      st = sobel4_run(h, s.d_in, p->in_pitch, s.d_out, p->out_pitch, height, width, border, fmt,
+                      s.stream);
+    if (ce == cudaSuccess && st == SOBEL4_OK)
+      ce = cudaMemcpyAsync(s.h_out, s.d_out, p->out_bytes, cudaMemcpyDeviceToHost, s.stream);
+    e = cudaStreamEndCapture(s.stream, &g);
+    if (e == cudaSuccess) e = ce;
+    if (st != SOBEL4_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      break;
+    }
+    e = cudaGraphInstantiate(&s.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) break;
+  }
+  if (st == SOBEL4_OK && e != cudaSuccess)
+    st = e == cudaErrorMemoryAllocation ? SOBEL4_ERR_OOM : SOBEL4_ERR_CUDA;
+  if (st != SOBEL4_OK) {
+    release(p);
+    return st;
+  }
+  // Capturing recorded the kernels into the graphs without launching them.
+  sobel4::note_launches(h, -(int64_t)(sobel4_launch_count(h) - launches0));
+  *out = p;
+  return SOBEL4_OK;
+}
+
+extern "C" sobel4_status sobel4_pipeline_buffers(sobel4_pipeline p, int32_t slot, uint8_t **h_in,
+                                                 void **h_out, size_t *in_pitch,
+                                                 size_t *out_pitch) {
+  if (!p || slot < 0 || slot >= (int32_t)p->slots.size()) return SOBEL4_ERR_INVALID_ARG;
+  if (h_in) *h_in = p->slots[slot].h_in;
+  if (h_out) *h_out = p->slots[slot].h_out;
+  if (in_pitch) *in_pitch = p->in_pitch;
+  if (out_pitch) *out_pitch = p->out_pitch;
+  return SOBEL4_OK;
+}
+
+extern "C" sobel4_status sobel4_pipeline_submit(sobel4_pipeline p, int32_t slot) {
+  if (!p || slot < 0 || slot >= (int32_t)p->slots.size()) return SOBEL4_ERR_INVALID_ARG;
+  Slot &s = p->slots[slot];
+  if (s.pending) return SOBEL4_ERR_INVALID_ARG;  // wait for the slot before refilling it
+  sobel4::DeviceScope scope(p->device);
+  cudaError_t e = cudaGraphLaunch(s.exec, s.stream);
+  if (e == cudaSuccess) e = cudaEventRecord(s.done, s.stream);
+  if (e != cudaSuccess) return SOBEL4_ERR_CUDA;
+  s.pending = true;
+  sobel4::note_launches(p->h, 1);
+  return SOBEL4_OK;
+}
+
+extern "C" sobel4_status sobel4_pipeline_wait(sobel4_pipeline p, int32_t slot) {
+  if (!p || slot < 0 || slot >= (int32_t)p->slots.size()) return SOBEL4_ERR_INVALID_ARG;
+  Slot &s = p->slots[slot];
+  if (!s.pending) return SOBEL4_OK;
+  sobel4::DeviceScope scope(p->device);
+  const cudaError_t e = cudaEventSynchronize(s.done);
+  s.pending = false;
+  return e == cudaSuccess ? SOBEL4_OK : SOBEL4_ERR_CUDA;
+}
+
+extern "C" sobel4_status sobel4_pipeline_destroy(sobel4_pipeline p) {
+  if (!p) return SOBEL4_OK;
+  sobel4::DeviceScope scope(p->device);
+  release(p);
+  return SOBEL4_OK;
+}

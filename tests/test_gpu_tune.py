@@ -1,0 +1,82 @@
+"""The autotuner: tuned configurations keep the output bit-exact, and the
+tuned table survives a save / load round trip and the SOBEL4_TUNE_CACHE
+variable."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2305_00515_gb300 as pkg
+import synth
+from gpu_util import Output, Placed, run_placed
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture
+def handle():
+    from paper_2305_00515_gb300 import build
+    build.build()
+    st, h = pkg.sobel4_create(0)
+    assert st == 0
+    yield h
+    pkg.sobel4_destroy(h)
+
+
+def test_tune_single_then_run(handle, tmp_path):
+    st, us = pkg.sobel4_tune(handle, 1000, 1500, 0, 0)
+    assert st == 0 and us > 0
+    assert pkg.sobel4_tune_entries(handle) == 1
+    img = synth.rects_noise(1000, 1500, 4)
+    got, guards = run_placed(torch, handle, img, "valid", "f32")
+    assert guards and np.array_equal(got, oracle.sobel4(img, "valid", "f32", threads=8))
+    path = str(tmp_path / "tune.json")
+    assert pkg.sobel4_tune_save(handle, path) == 0
+    st, h2 = pkg.sobel4_create(0)
+    try:
+        assert pkg.sobel4_tune_load(h2, path) == 0
+        assert pkg.sobel4_tune_entries(h2) == 1
+        got2, _ = run_placed(torch, h2, img, "valid", "f32")
+        assert np.array_equal(got2, got)
+    finally:
+        pkg.sobel4_destroy(h2)
+
+
+def test_tune_cache_rejections(handle, tmp_path, monkeypatch):
+    bad = tmp_path / "bad.json"
+    bad.write_text("not a tuning file\n")
+    assert pkg.sobel4_tune_load(handle, str(bad)) == 1
+    assert pkg.sobel4_tune_load(handle, str(tmp_path / "missing.json")) == 1
+    other = tmp_path / "other.json"
+    other.write_text('{"sobel4_tune": 1, "version": "0.1.0", "device": "Some Other GPU", '
+                     '"sm_count": 3,\n "entries": [\n  {"kind": 0, "hb": 5, "wb": 5, "fmt": 0, '
+                     '"nc": 4, "R": 8, "ctas": 4, "us": 1.000}\n ]}\n')
+    assert pkg.sobel4_tune_load(handle, str(other)) == 2
+    assert pkg.sobel4_tune_entries(handle) == 0
+    # a table saved here loads automatically through SOBEL4_TUNE_CACHE
+    assert pkg.sobel4_tune(handle, 300, 300, 1, 1)[0] == 0
+    path = str(tmp_path / "cache.json")
+    assert pkg.sobel4_tune_save(handle, path) == 0
+    monkeypatch.setenv("SOBEL4_TUNE_CACHE", path)
+    st, h2 = pkg.sobel4_create(0)
+    assert st == 0
+    assert pkg.sobel4_tune_entries(h2) == 1
+    pkg.sobel4_destroy(h2)
+
+
+def test_tune_batched_keeps_results_exact(handle):
+    imgs = [synth.rects_noise(h, w, 50 + i) for i, (h, w) in
+            enumerate(((37, 41), (300, 129), (131, 600), (64, 64), (500, 257)))]
+    srcs = [Placed(torch, im, im.shape[1], 0) for im in imgs]
+    outs = [Output(torch, im.shape[0], im.shape[1], "u8", im.shape[1], 0) for im in imgs]
+    descs = [pkg.Image(s.ptr, s.pitch, o.ptr, o.pitch, *im.shape)
+             for s, o, im in zip(srcs, outs, imgs)]
+    torch.cuda.synchronize()
+    st, us = pkg.sobel4_tune_batched(handle, descs, 2, 1)
+    assert st == 0 and us > 0
+    assert pkg.sobel4_tune_entries(handle) == 1
+    assert pkg.sobel4_run_batched(handle, descs, 2, 1, torch.cuda.current_stream().cuda_stream) == 0
+    torch.cuda.synchronize()
+    for im, o in zip(imgs, outs):
+        got, guards = o.read()
+        assert guards and np.array_equal(got, oracle.sobel4(im, "reflect101", "u8"))
