@@ -75,14 +75,20 @@ def dist_setup(gpus):
     return world, rank, local
 
 
-def max_over_ranks(value: float, world: int) -> float:
+def max_over_ranks(value: float, world: int, device: str = "cuda") -> float:
+    """The slowest rank's time (every rank calls this)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    t = torch.tensor([value], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def weak_scaling_value(px_per_rank: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job Gpixel/s: every rank's pixels over the slowest rank's time."""
+    return world * px_per_rank * steps / (max_ms * 1e-3) / 1e9
 
 
 def barrier(world: int):
@@ -501,7 +507,7 @@ def run_ours(args, world, rank, local):
     total_ms = t_start.elapsed_time(t_end)
     kern_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = max_over_ranks(total_ms, world)
-    value = world * px * args.steps / (total_ms * 1e-3) / 1e9
+    value = weak_scaling_value(px, args.steps, world, total_ms)
     mean_kernel_s = statistics.fmean(kern_ms) * 1e-3
     peak, peak_kind = measured_peaks()
     achieved = px * BYTES_PER_PX / mean_kernel_s / 1e9

@@ -129,6 +129,7 @@ namespace {
 
 sobel4_status cuda_fail(sobel4_ctx *h, cudaError_t e) {
   if (h) h->last_err = (int32_t)e;
+  (void)cudaGetLastError();  // a failed call must not be reported again by a later launch
   return e == cudaErrorMemoryAllocation ? SOBEL4_ERR_OOM : SOBEL4_ERR_CUDA;
 }
 

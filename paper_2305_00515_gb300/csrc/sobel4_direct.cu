@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(256) direct_kernel(ImageDesc im, int border) {
 cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, cudaStream_t st) {
   const dim3 block(32, 8);
   const dim3 grid((im.W + 31) / 32, (im.H + 7) / 8);
+  (void)cudaGetLastError();  // report this launch only, not an earlier failed call
   switch (fmt) {
     case kF32: direct_kernel<kF32><<<grid, block, 0, st>>>(im, border); break;
     case kU8: direct_kernel<kU8><<<grid, block, 0, st>>>(im, border); break;

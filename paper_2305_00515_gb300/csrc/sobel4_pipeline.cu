@@ -115,6 +115,7 @@ extern "C" sobel4_status sobel4_pipeline_create(sobel4_handle h, int32_t height,
   if (st == SOBEL4_OK && e != cudaSuccess)
     st = e == cudaErrorMemoryAllocation ? SOBEL4_ERR_OOM : SOBEL4_ERR_CUDA;
   if (st != SOBEL4_OK) {
+    (void)cudaGetLastError();  // the failure is reported here, not by a later call
     release(p);
     return st;
   }

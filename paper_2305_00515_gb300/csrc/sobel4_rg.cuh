@@ -61,6 +61,7 @@ cudaError_t launch_rg_single_fmt(const ImageDesc &im, int border, int R, int nc,
   const int64_t items = (int64_t)im.n_seg * im.n_band;
   if (items <= 0) return cudaSuccess;
   const int64_t grid = (items + kWarpsPerCta - 1) / kWarpsPerCta;
+  (void)cudaGetLastError();  // report this launch only, not an earlier failed call
   if (nc == 2)
     rg_single_kernel<2, FMT><<<(unsigned)grid, kWarpsPerCta * 32, 0, st>>>(im, border, R,
                                                                           (int)items);
@@ -74,6 +75,7 @@ template <int FMT>
 cudaError_t launch_rg_batched_fmt(const ImageDesc *d_descs, int n_img, int64_t total,
                                   unsigned int *d_queue, int border, int R, int nc, int grid,
                                   cudaStream_t st) {
+  (void)cudaGetLastError();  // report this launch only, not an earlier failed call
   if (nc == 2)
     rg_batched_kernel<2, FMT><<<grid, kWarpsPerCta * 32, 0, st>>>(d_descs, n_img, total,
                                                                  d_queue, border, R);

@@ -26,6 +26,7 @@ __global__ void check_magnitude_kernel(int64_t s0, int64_t s1, unsigned long lon
 
 cudaError_t launch_check_magnitude(int64_t s0, int64_t s1, unsigned long long *d_bad, int grid,
                                    cudaStream_t st) {
+  (void)cudaGetLastError();  // report this launch only, not an earlier failed call
   check_magnitude_kernel<<<grid, 256, 0, st>>>(s0, s1, d_bad);
   return cudaGetLastError();
 }

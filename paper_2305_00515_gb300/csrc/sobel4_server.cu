@@ -320,6 +320,7 @@ extern "C" sobel4_status sobel4_server_create(sobel4_handle h, const sobel4_serv
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->comp, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->down, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
+    (void)cudaGetLastError();  // the failure is reported here, not by a later call
     sobel4_server_destroy(s);
     return e == cudaErrorMemoryAllocation ? SOBEL4_ERR_OOM : SOBEL4_ERR_CUDA;
   }

@@ -115,3 +115,18 @@ def test_server_rejects_and_times_out():
         assert rc == 0
         assert np.array_equal(o2, oracle.sobel4(small))
         assert pkg.sobel4_server_destroy(srv) == 0
+
+
+def test_allocation_failures_surface_as_oom():
+    """Failure injection on the host: allocations no GPU can satisfy."""
+    with pkg.Sobel4(0) as s:
+        st, srv = pkg.sobel4_server_create(s.handle, 1 << 52, 0, 0, 0, 0)
+        assert st == 3 and not srv.value
+        st, _ = pkg.sobel4_tune(s.handle, 1 << 26, 1 << 26, 0, 0)
+        assert st == 3
+        assert s.launches == 0
+        # the handle still works afterwards
+        img = synth.uniform(40, 50, 3)
+        out = s.run(torch.from_numpy(img).cuda())
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), oracle.sobel4(img))
