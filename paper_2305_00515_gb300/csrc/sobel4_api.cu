@@ -18,31 +18,35 @@
 #include "sobel4_launch.h"
 
 namespace sobel4 {
-cudaError_t launch_rg_single_f32(const ImageDesc &, int, int, int, cudaStream_t);
-cudaError_t launch_rg_single_u8(const ImageDesc &, int, int, int, cudaStream_t);
-cudaError_t launch_rg_single_s16(const ImageDesc &, int, int, int, cudaStream_t);
+cudaError_t launch_rg_single_f32(const ImageDesc &, int, int, int, int, unsigned int *,
+                                 cudaStream_t);
+cudaError_t launch_rg_single_u8(const ImageDesc &, int, int, int, int, unsigned int *,
+                                cudaStream_t);
+cudaError_t launch_rg_single_s16(const ImageDesc &, int, int, int, int, unsigned int *,
+                                 cudaStream_t);
 cudaError_t launch_rg_batched_f32(const ImageDesc *, int, int64_t, unsigned int *, int, int, int,
-                                  int, cudaStream_t);
+                                  int, int, cudaStream_t);
 cudaError_t launch_rg_batched_u8(const ImageDesc *, int, int64_t, unsigned int *, int, int, int,
-                                 int, cudaStream_t);
+                                 int, int, cudaStream_t);
 cudaError_t launch_rg_batched_s16(const ImageDesc *, int, int64_t, unsigned int *, int, int, int,
-                                  int, cudaStream_t);
+                                  int, int, cudaStream_t);
 
 cudaError_t launch_rg_single(const ImageDesc &im, int border, int fmt, int R, int nc,
-                             cudaStream_t st) {
+                             int sm_count, unsigned int *pair, cudaStream_t st) {
   switch (fmt) {
-    case kF32: return launch_rg_single_f32(im, border, R, nc, st);
-    case kU8: return launch_rg_single_u8(im, border, R, nc, st);
-    default: return launch_rg_single_s16(im, border, R, nc, st);
+    case kF32: return launch_rg_single_f32(im, border, R, nc, sm_count, pair, st);
+    case kU8: return launch_rg_single_u8(im, border, R, nc, sm_count, pair, st);
+    default: return launch_rg_single_s16(im, border, R, nc, sm_count, pair, st);
   }
 }
 
 cudaError_t launch_rg_batched(const ImageDesc *d, int n, int64_t total, unsigned int *q,
-                              int border, int fmt, int R, int nc, int grid, cudaStream_t st) {
+                              int border, int fmt, int R, int nc, int grid, int sm_count,
+                              cudaStream_t st) {
   switch (fmt) {
-    case kF32: return launch_rg_batched_f32(d, n, total, q, border, R, nc, grid, st);
-    case kU8: return launch_rg_batched_u8(d, n, total, q, border, R, nc, grid, st);
-    default: return launch_rg_batched_s16(d, n, total, q, border, R, nc, grid, st);
+    case kF32: return launch_rg_batched_f32(d, n, total, q, border, R, nc, grid, sm_count, st);
+    case kU8: return launch_rg_batched_u8(d, n, total, q, border, R, nc, grid, sm_count, st);
+    default: return launch_rg_batched_s16(d, n, total, q, border, R, nc, grid, sm_count, st);
   }
 }
 }  // namespace sobel4
@@ -56,6 +60,7 @@ namespace {
 #endif
 
 constexpr int kSlots = 4;           // batch descriptor slots in flight per handle
+constexpr int kQueuePairs = 256;    // single-image work-queue counter pairs per handle
 constexpr int kDefaultNC = SOBEL4_DEFAULT_NC;  // RG columns per lane unless the handle says otherwise
 constexpr int kDefaultR = 16;       // RG strip height for large images (measured best on 8192^2)
 constexpr int kBatchR = 16;         // RG strip height for batches
@@ -111,6 +116,10 @@ struct sobel4_ctx {
   int32_t last_err = 0;
   BatchSlot slots[kSlots];
   int next_slot = 0;
+  // kQueuePairs zeroed counter pairs, handed to single-image launches in turn;
+  // each launch leaves its pair zero again when it completes.
+  unsigned int *d_pairs = nullptr;
+  uint32_t next_pair = 0;
   cudaStream_t own_stream = nullptr;
   uint8_t *d_in = nullptr;
   size_t d_in_bytes = 0;
@@ -228,8 +237,14 @@ ImageDesc make_desc(const uint8_t *src, size_t sp, void *dst, size_t dp, int32_t
   return d;
 }
 
+unsigned int *next_pair(sobel4_ctx *h) {
+  return h->d_pairs + 2 * (h->next_pair++ % (uint32_t)kQueuePairs);
+}
+
+// pair: the RG kernel's counter pair, or nullptr for the handle's next one.
 sobel4_status launch_one(sobel4_ctx *h, const uint8_t *src, size_t sp, void *dst, size_t dp,
-                         int32_t H, int32_t W, int border, int fmt, cudaStream_t stream) {
+                         int32_t H, int32_t W, int border, int fmt, cudaStream_t stream,
+                         unsigned int *pair = nullptr) {
   cudaError_t e;
   if (h->variant == SOBEL4_VARIANT_DIRECT) {
     const ImageDesc im = make_desc(src, sp, dst, dp, H, W, 1, h->nc);
@@ -238,7 +253,8 @@ sobel4_status launch_one(sobel4_ctx *h, const uint8_t *src, size_t sp, void *dst
     int nc, R;
     rg_config(h, H, W, fmt, &nc, &R);
     const ImageDesc im = make_desc(src, sp, dst, dp, H, W, R, nc);
-    e = launch_rg_single(im, border, fmt, R, nc, stream);
+    e = launch_rg_single(im, border, fmt, R, nc, h->sm_count, pair ? pair : next_pair(h),
+                         stream);
   }
   if (e != cudaSuccess) return cuda_fail(h, e);
   h->launches += 1;
@@ -296,6 +312,9 @@ sobel4_status sobel4_create(sobel4_handle *out, int32_t device, const sobel4_opt
     if (e == cudaSuccess) snprintf(h->device_name, sizeof(h->device_name), "%s", prop.name);
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess)
+    e = cudaMalloc((void **)&h->d_pairs, sizeof(unsigned int) * 2 * kQueuePairs);
+  if (e == cudaSuccess) e = cudaMemset(h->d_pairs, 0, sizeof(unsigned int) * 2 * kQueuePairs);
   for (int i = 0; i < kSlots && e == cudaSuccess; ++i)
     e = cudaEventCreateWithFlags(&h->slots[i].done, cudaEventDisableTiming);
   if (e != cudaSuccess) {
@@ -327,6 +346,7 @@ sobel4_status sobel4_destroy(sobel4_handle h) {
   }
   if (h->d_in) cudaFree(h->d_in);
   if (h->d_out) cudaFree(h->d_out);
+  if (h->d_pairs) cudaFree(h->d_pairs);
   delete h;
   return SOBEL4_OK;
 }
@@ -345,6 +365,18 @@ sobel4_status sobel4_set_variant(sobel4_handle h, int32_t variant) {
 sobel4_status sobel4_run(sobel4_handle h, const uint8_t *d_src, size_t src_pitch, void *d_dst,
                          size_t dst_pitch, int32_t height, int32_t width, sobel4_border border,
                          sobel4_format fmt, cudaStream_t stream) {
+  return sobel4::run_with_pair(h, d_src, src_pitch, d_dst, dst_pitch, height, width, border, fmt,
+                               stream, nullptr);
+}
+
+}  // extern "C"
+
+namespace sobel4 {
+// sobel4_run with a caller-owned counter pair (nullptr: the handle's next);
+// a captured graph owns its pair, since every replay reuses it.
+sobel4_status run_with_pair(sobel4_handle h, const uint8_t *d_src, size_t src_pitch, void *d_dst,
+                            size_t dst_pitch, int32_t height, int32_t width, int border, int fmt,
+                            cudaStream_t stream, unsigned int *pair) {
   if (!h || !d_src || !valid_dst_ptr(d_dst, fmt)) return SOBEL4_ERR_INVALID_ARG;
   if (!valid_shape(src_pitch, dst_pitch, height, width, border, fmt))
     return SOBEL4_ERR_INVALID_ARG;
@@ -352,8 +384,12 @@ sobel4_status sobel4_run(sobel4_handle h, const uint8_t *d_src, size_t src_pitch
   ranges(d_src, src_pitch, d_dst, dst_pitch, height, width, fmt, r);
   if (overlaps(r[0], r[1], r[2], r[3])) return SOBEL4_ERR_INVALID_ARG;
   DeviceGuard g(h->device);
-  return launch_one(h, d_src, src_pitch, d_dst, dst_pitch, height, width, border, fmt, stream);
+  return launch_one(h, d_src, src_pitch, d_dst, dst_pitch, height, width, border, fmt, stream,
+                    pair);
 }
+}  // namespace sobel4
+
+extern "C" {
 
 sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int32_t n,
                                  sobel4_border border, sobel4_format fmt, cudaStream_t stream) {
@@ -433,7 +469,7 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
   const int64_t want = (total + kWarpsPerCta - 1) / kWarpsPerCta;
   const int grid = (int)std::min<int64_t>(want, (int64_t)h->sm_count * bctas);
   e = launch_rg_batched(slot.d_desc, n, total, slot.d_queue, border, fmt, R, bnc,
-                        std::max(grid, 1), stream);
+                        std::max(grid, 1), h->sm_count, stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
   h->launches += 1;
   e = cudaEventRecord(slot.done, stream);
@@ -630,7 +666,7 @@ extern "C" sobel4_status sobel4_run_batched_static(const sobel4_image *imgs, int
   const int64_t want = (total + kWarpsPerCta - 1) / kWarpsPerCta;
   const int grid = (int)std::min<int64_t>(want, (int64_t)sd->sm_count * 4);
   e = launch_rg_batched(d_desc, n, total, d_queue, border, fmt, R, kDefaultNC, std::max(grid, 1),
-                        stream);
+                        sd->sm_count, stream);
   return e == cudaSuccess ? SOBEL4_OK : SOBEL4_ERR_CUDA;
 }
 
@@ -708,7 +744,8 @@ extern "C" sobel4_status sobel4_tune(sobel4_handle h, int32_t height, int32_t wi
       float us = 0.f;
       e = median_us(h->own_stream, [&]() {
         h->launches += 1;
-        return launch_rg_single(im, border, fmt, Rs[b], ncs[a], h->own_stream);
+        return launch_rg_single(im, border, fmt, Rs[b], ncs[a], h->sm_count, next_pair(h),
+                                h->own_stream);
       }, &us);
       if (e == cudaSuccess && (!have || us < best.us)) {
         best.nc = ncs[a];

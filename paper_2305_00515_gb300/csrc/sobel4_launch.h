@@ -9,16 +9,20 @@
 
 namespace sobel4 {
 
-// RG kernel over one image with nc (2 or 4) columns per lane: ceil(items / 4)
-// CTAs of 4 independent warps.  im.n_seg must be ceil(W / (32 * nc)).
+// RG kernel over one image with nc (2 or 4) columns per lane: CTAs of 4
+// independent warps, at most as many as are resident on sm_count SMs, pulling
+// items from the device counter pair `pair` (two zero words; the kernel leaves
+// them zero again).  No two launches in flight at once may share a pair.
+// im.n_seg must be ceil(W / (32 * nc)).
 cudaError_t launch_rg_single(const ImageDesc &im, int border, int fmt, int R, int nc,
-                             cudaStream_t st);
+                             int sm_count, unsigned int *pair, cudaStream_t st);
 
-// Persistent RG kernel over a batch: `grid` CTAs pull warp items from the
-// device counter *d_queue (reset to 0 by the caller before the launch).
+// Persistent RG kernel over a batch: min(grid, resident CTAs on sm_count SMs)
+// CTAs pull warp items from the device counter *d_queue (reset to 0 by the
+// caller before the launch).
 cudaError_t launch_rg_batched(const ImageDesc *d_descs, int n_img, int64_t total_items,
                               unsigned int *d_queue, int border, int fmt, int R, int nc,
-                              int grid, cudaStream_t st);
+                              int grid, int sm_count, cudaStream_t st);
 
 // DIRECT kernel (one thread per output pixel).
 cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, cudaStream_t st);
@@ -33,6 +37,12 @@ struct HandleInfo {
 };
 __attribute__((visibility("hidden"))) HandleInfo handle_info(sobel4_handle h);
 __attribute__((visibility("hidden"))) void note_launches(sobel4_handle h, int64_t delta);
+// sobel4_run with a caller-owned RG counter pair (two zeroed words in device
+// memory; nullptr takes the handle's next one).  A captured graph must own its
+// pair, because every replay of the graph reuses it.
+__attribute__((visibility("hidden"))) sobel4_status run_with_pair(
+    sobel4_handle h, const uint8_t *d_src, size_t src_pitch, void *d_dst, size_t dst_pitch,
+    int32_t height, int32_t width, int border, int fmt, cudaStream_t stream, unsigned int *pair);
 
 // Make `dev` current for the lifetime of the guard.
 class DeviceScope {

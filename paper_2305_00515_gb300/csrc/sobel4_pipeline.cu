@@ -19,6 +19,7 @@ struct Slot {
   void *h_out = nullptr;     // pinned
   uint8_t *d_in = nullptr;
   uint8_t *d_out = nullptr;
+  unsigned int *d_pair = nullptr;  // the captured kernel's own work-queue counter pair
   cudaStream_t stream = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t done = nullptr;
@@ -50,6 +51,7 @@ void release(sobel4_pipeline_ctx *p) {
     if (s.h_out) cudaFreeHost(s.h_out);
     if (s.d_in) cudaFree(s.d_in);
     if (s.d_out) cudaFree(s.d_out);
+    if (s.d_pair) cudaFree(s.d_pair);
   }
   delete p;
 }
@@ -86,6 +88,8 @@ extern "C" sobel4_status sobel4_pipeline_create(sobel4_handle h, int32_t height,
     if (e == cudaSuccess) e = cudaHostAlloc(&s.h_out, p->out_bytes, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaMalloc((void **)&s.d_in, p->in_bytes);
     if (e == cudaSuccess) e = cudaMalloc((void **)&s.d_out, p->out_bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s.d_pair, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(s.d_pair, 0, 2 * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
     if (e != cudaSuccess) break;
@@ -98,8 +102,8 @@ extern "C" sobel4_status sobel4_pipeline_create(sobel4_handle h, int32_t height,
     if (e != cudaSuccess) break;
     cudaError_t ce = cudaMemcpyAsync(s.d_in, s.h_in, p->in_bytes, cudaMemcpyHostToDevice, s.stream);
     if (ce == cudaSuccess)
-      st = sobel4_run(h, s.d_in, p->in_pitch, s.d_out, p->out_pitch, height, width, border, fmt,
-                      s.stream);
+      st = sobel4::run_with_pair(h, s.d_in, p->in_pitch, s.d_out, p->out_pitch, height, width,
+                                 border, fmt, s.stream, s.d_pair);
     if (ce == cudaSuccess && st == SOBEL4_OK)
       ce = cudaMemcpyAsync(s.h_out, s.d_out, p->out_bytes, cudaMemcpyDeviceToHost, s.stream);
     e = cudaStreamEndCapture(s.stream, &g);

@@ -7,11 +7,32 @@ a wrong border rule, ...), compiled into a temporary library.  The pins of
 the pins are strong enough to catch the mistakes they are meant to catch.
 """
 import os
+import subprocess
+import sys
 
 import pytest
 
 import oracle
-import oracle_checks as oc
+
+TESTS = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(TESTS)
+
+# Runs every pin on one mutant library and reports each failed pin on its own
+# line.  A mutant may read or write outside its buffers (a wrong plane stride,
+# an index past the last row), so it runs in a child process: its damage
+# cannot reach the test process.
+CHILD = """
+import sys
+sys.path[:0] = [{root!r}, {tests!r}]
+import oracle, oracle_checks as oc
+o = oracle.Oracle(sys.argv[1])
+for check in oc.ALL_CHECKS:
+    try:
+        check(o)
+    except (AssertionError, ValueError):
+        print("FAILED", check.__name__, flush=True)
+print("DONE", flush=True)
+"""
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "sobel4_oracle.c")
 
@@ -45,11 +66,9 @@ def test_mutant_is_caught(name, tmp_path):
     src = tmp_path / "mutant.c"
     src.write_text(text.replace(before, after))
     lib = oracle.build(str(src), str(tmp_path / "libmutant.so"), force=True)
-    o = oracle.Oracle(lib)
-    failed = []
-    for check in oc.ALL_CHECKS:
-        try:
-            check(o)
-        except (AssertionError, ValueError):
-            failed.append(check.__name__)
-    assert failed, f"no pin caught mutant {name}"
+    r = subprocess.run([sys.executable, "-c", CHILD.format(root=ROOT, tests=TESTS), lib],
+                       capture_output=True, text=True, timeout=600)
+    failed = [ln.split()[1] for ln in r.stdout.splitlines() if ln.startswith("FAILED ")]
+    # A pin must fail by assertion; a mutant that only crashes is not caught.
+    assert failed, (f"no pin caught mutant {name} (exit {r.returncode}):\n"
+                    f"{r.stdout[-2000:]}{r.stderr[-2000:]}")
