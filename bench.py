@@ -557,7 +557,7 @@ def run_ours(args, world, rank, local):
                          f"(> 2x L2) instead of a flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "rg_single_kernel<F32>", "peak_kind": peak_kind,
+                     "kernel": "tma_single_kernel<F32>", "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": px * BYTES_PER_PX,
                      "mean_kernel_us": mean_kernel_s * 1e6,
                      "p50_kernel_us": statistics.median(kern_ms) * 1e3},

@@ -83,9 +83,18 @@ typedef enum { SOBEL4_OUT_F32 = 0, SOBEL4_OUT_U8 = 1, SOBEL4_OUT_S16X4 = 2 } sob
  * global memory (the paper's "GM" kernel, Section 5.2).  RG is the
  * register-window kernel (Section 4.3): threads across columns, rows walked
  * sequentially, the x/y masks factored into 1x5 passes (Eq. 6-7), the
- * diagonals through K_d+ / K_d- (Eq. 10-19), next rows prefetched.
+ * diagonals through K_d+ / K_d- (Eq. 10-19), next rows prefetched.  When the
+ * source address and pitch are multiples of 16 bytes, RG stages rows with
+ * 2-D tensor copies (TMA) into a per-warp shared-memory ring; otherwise each
+ * lane copies 16-byte granules (cp.async).  RG_LANECOPY forces the second
+ * staging for every image (both give identical results).
  */
-typedef enum { SOBEL4_VARIANT_AUTO = 0, SOBEL4_VARIANT_DIRECT = 1, SOBEL4_VARIANT_RG = 2 } sobel4_variant;
+typedef enum {
+  SOBEL4_VARIANT_AUTO = 0,
+  SOBEL4_VARIANT_DIRECT = 1,
+  SOBEL4_VARIANT_RG = 2,
+  SOBEL4_VARIANT_RG_LANECOPY = 3
+} sobel4_variant;
 
 /* Creation options; pass NULL for defaults (all fields 0). */
 typedef struct {
@@ -165,6 +174,16 @@ const char *sobel4_status_string(sobel4_status s);
 
 /* The cudaError_t of the handle's most recent SOBEL4_ERR_CUDA (0 if none). */
 int32_t sobel4_last_cuda_error(sobel4_handle h);
+
+/*
+ * Result of the bounded waits inside this handle's kernels.  The TMA-staged
+ * kernel waits on shared-memory barriers for its row copies; a wait that runs
+ * out (2 s) makes the kernel stop early and set the handle's error word, and
+ * the outputs of that launch are then incomplete.  This call synchronises the
+ * handle's device, reads and clears the word, and returns TIMEOUT if any wait
+ * ran out since the previous call, OK otherwise (CUDA if the device faulted).
+ */
+sobel4_status sobel4_device_status(sobel4_handle h);
 
 /* Number of kernels this handle has launched so far (for launch accounting). */
 uint64_t sobel4_launch_count(sobel4_handle h);

@@ -20,6 +20,7 @@ __all__ = [
     "BORDERS", "FORMATS", "VARIANTS", "Sobel4", "Sobel4Error", "Image", "Options",
     "library_path", "load", "sobel4_create", "sobel4_destroy", "sobel4_run",
     "sobel4_run_batched", "sobel4_run_host", "sobel4_status_string", "sobel4_last_cuda_error",
+    "sobel4_device_status",
     "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
     "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched", "sobel4_tune_entries",
     "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create", "sobel4_pipeline_buffers",
@@ -31,15 +32,15 @@ __all__ = [
 _PKG = os.path.dirname(os.path.abspath(__file__))
 BORDERS = {"valid": 0, "replicate": 1, "reflect101": 2, "constant0": 3}
 FORMATS = {"f32": 0, "u8": 1, "s16x4": 2}
-VARIANTS = {"auto": 0, "direct": 1, "rg": 2}
+VARIANTS = {"auto": 0, "direct": 1, "rg": 2, "rg_lanecopy": 3}
 ELEM_SIZE = {"f32": 4, "u8": 1, "s16x4": 2}
 STATUS = {0: "SOBEL4_OK", 1: "SOBEL4_ERR_INVALID_ARG", 2: "SOBEL4_ERR_UNSUPPORTED",
           3: "SOBEL4_ERR_OOM", 4: "SOBEL4_ERR_CUDA", 5: "SOBEL4_ERR_TIMEOUT"}
 
 EXPORTED_SYMBOLS = (
     "sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_batched", "sobel4_run_host",
-    "sobel4_status_string", "sobel4_last_cuda_error", "sobel4_launch_count",
-    "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
+    "sobel4_status_string", "sobel4_last_cuda_error", "sobel4_device_status",
+    "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
     "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched", "sobel4_tune_entries",
     "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create", "sobel4_pipeline_buffers",
     "sobel4_pipeline_submit", "sobel4_pipeline_wait", "sobel4_pipeline_destroy",
@@ -109,6 +110,7 @@ def load() -> ctypes.CDLL:
         lib.sobel4_status_string.restype = ctypes.c_char_p
         lib.sobel4_last_cuda_error.argtypes = [vp]
         lib.sobel4_last_cuda_error.restype = i32
+        lib.sobel4_device_status.argtypes = [vp]
         lib.sobel4_launch_count.argtypes = [vp]
         lib.sobel4_launch_count.restype = ctypes.c_uint64
         lib.sobel4_set_variant.argtypes = [vp, i32]
@@ -137,6 +139,7 @@ def load() -> ctypes.CDLL:
         lib.sobel4_server_destroy.argtypes = [vp]
         for name in ("sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_batched",
                      "sobel4_run_host", "sobel4_set_variant", "sobel4_check_magnitude",
+                     "sobel4_device_status",
                      "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched",
                      "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create",
                      "sobel4_pipeline_buffers", "sobel4_pipeline_submit", "sobel4_pipeline_wait",
@@ -189,6 +192,10 @@ def sobel4_status_string(status: int) -> str:
 
 def sobel4_last_cuda_error(h) -> int:
     return load().sobel4_last_cuda_error(h)
+
+
+def sobel4_device_status(h) -> int:
+    return load().sobel4_device_status(h)
 
 
 def sobel4_launch_count(h) -> int:

@@ -102,6 +102,7 @@ struct TuneEntry {
   int kind, hb, wb, fmt;
   int nc, R, ctas;
   float us;
+  int kernel;  // single images: 0 = lane-copy staging, 1 = TMA staging
 };
 
 struct sobel4_ctx {
@@ -120,6 +121,7 @@ struct sobel4_ctx {
   // each launch leaves its pair zero again when it completes.
   unsigned int *d_pairs = nullptr;
   uint32_t next_pair = 0;
+  unsigned int *d_err = nullptr;  // bit 0: a bounded wait in a kernel ran out (inside d_pairs)
   cudaStream_t own_stream = nullptr;
   uint8_t *d_in = nullptr;
   size_t d_in_bytes = 0;
@@ -202,13 +204,25 @@ const TuneEntry *find_tuned(const sobel4_ctx *h, int kind, int32_t H, int32_t W,
   return nullptr;
 }
 
-// The RG configuration (columns per lane, strip height) for one image:
-// explicit options first, then the tuned table, then the heuristic.
-void rg_config(const sobel4_ctx *h, int32_t H, int32_t W, int fmt, int *nc, int *R) {
+// The RG configuration for one image: which staging (TMA needs a 16-byte
+// aligned source and pitch), columns per lane and strip height.  Explicit
+// options first, then the tuned table, then the heuristics.
+void rg_config(const sobel4_ctx *h, const uint8_t *src, size_t sp, int32_t H, int32_t W, int fmt,
+               bool *use_tma, int *nc, int *R) {
   const TuneEntry *t = find_tuned(h, 0, H, W, fmt);
-  *nc = h->nc_forced ? h->nc : (t ? t->nc : h->nc);
+  *use_tma = h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced && tma_eligible(src, sp) &&
+             !(t && t->kernel == 0);
+  if (*use_tma) {
+    *nc = 4;
+    if (h->rows_per_strip > 0) *R = tma_round_R(h->rows_per_strip);
+    else if (t && t->kernel == 1) *R = t->R;
+    else *R = tma_pick_R(fmt, h->sm_count, H, W);
+    return;
+  }
+  const bool lane_entry = t && t->kernel == 0;
+  *nc = h->nc_forced ? h->nc : (lane_entry ? t->nc : h->nc);
   if (h->rows_per_strip > 0) *R = h->rows_per_strip;
-  else if (t) *R = t->R;
+  else if (lane_entry) *R = t->R;
   else *R = pick_R(h, H, W);
 }
 
@@ -251,10 +265,16 @@ sobel4_status launch_one(sobel4_ctx *h, const uint8_t *src, size_t sp, void *dst
     e = launch_direct(im, border, fmt, stream);
   } else {
     int nc, R;
-    rg_config(h, H, W, fmt, &nc, &R);
-    const ImageDesc im = make_desc(src, sp, dst, dp, H, W, R, nc);
-    e = launch_rg_single(im, border, fmt, R, nc, h->sm_count, pair ? pair : next_pair(h),
-                         stream);
+    bool use_tma;
+    rg_config(h, src, sp, H, W, fmt, &use_tma, &nc, &R);
+    if (use_tma) {
+      e = launch_tma_single(src, sp, dst, dp, H, W, border, fmt, R, h->sm_count,
+                            pair ? pair : next_pair(h), h->d_err, stream);
+    } else {
+      const ImageDesc im = make_desc(src, sp, dst, dp, H, W, R, nc);
+      e = launch_rg_single(im, border, fmt, R, nc, h->sm_count, pair ? pair : next_pair(h),
+                           stream);
+    }
   }
   if (e != cudaSuccess) return cuda_fail(h, e);
   h->launches += 1;
@@ -291,7 +311,7 @@ const char *sobel4_status_string(sobel4_status s) {
 sobel4_status sobel4_create(sobel4_handle *out, int32_t device, const sobel4_options *opt) {
   if (!out) return SOBEL4_ERR_INVALID_ARG;
   *out = nullptr;
-  if (opt && (opt->variant < 0 || opt->variant > SOBEL4_VARIANT_RG || opt->rows_per_strip < 0 ||
+  if (opt && (opt->variant < 0 || opt->variant > SOBEL4_VARIANT_RG_LANECOPY || opt->rows_per_strip < 0 ||
               opt->rows_per_strip > 4096 || opt->persistent_ctas_per_sm < 0 ||
               opt->persistent_ctas_per_sm > 64 ||
               (opt->columns_per_lane != 0 && opt->columns_per_lane != 2 &&
@@ -312,9 +332,11 @@ sobel4_status sobel4_create(sobel4_handle *out, int32_t device, const sobel4_opt
     if (e == cudaSuccess) snprintf(h->device_name, sizeof(h->device_name), "%s", prop.name);
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess)
-    e = cudaMalloc((void **)&h->d_pairs, sizeof(unsigned int) * 2 * kQueuePairs);
-  if (e == cudaSuccess) e = cudaMemset(h->d_pairs, 0, sizeof(unsigned int) * 2 * kQueuePairs);
+  // kQueuePairs counter pairs, then the error word (own 256-byte line).
+  const size_t pair_bytes = sizeof(unsigned int) * 2 * kQueuePairs + 256;
+  if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_pairs, pair_bytes);
+  if (e == cudaSuccess) e = cudaMemset(h->d_pairs, 0, pair_bytes);
+  if (e == cudaSuccess) h->d_err = h->d_pairs + 2 * kQueuePairs;
   for (int i = 0; i < kSlots && e == cudaSuccess; ++i)
     e = cudaEventCreateWithFlags(&h->slots[i].done, cudaEventDisableTiming);
   if (e != cudaSuccess) {
@@ -353,10 +375,21 @@ sobel4_status sobel4_destroy(sobel4_handle h) {
 
 int32_t sobel4_last_cuda_error(sobel4_handle h) { return h ? h->last_err : 0; }
 
+sobel4_status sobel4_device_status(sobel4_handle h) {
+  if (!h) return SOBEL4_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  unsigned int word = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&word, h->d_err, sizeof(word), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && word) e = cudaMemset(h->d_err, 0, sizeof(word));
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  return word ? SOBEL4_ERR_TIMEOUT : SOBEL4_OK;
+}
+
 uint64_t sobel4_launch_count(sobel4_handle h) { return h ? h->launches : 0; }
 
 sobel4_status sobel4_set_variant(sobel4_handle h, int32_t variant) {
-  if (!h || variant < SOBEL4_VARIANT_AUTO || variant > SOBEL4_VARIANT_RG)
+  if (!h || variant < SOBEL4_VARIANT_AUTO || variant > SOBEL4_VARIANT_RG_LANECOPY)
     return SOBEL4_ERR_INVALID_ARG;
   h->variant = variant;
   return SOBEL4_OK;
@@ -715,8 +748,9 @@ void upsert(sobel4_ctx *h, const TuneEntry &t) {
 
 bool valid_entry(const TuneEntry &t) {
   return (t.kind == 0 || t.kind == 1) && t.hb >= 0 && t.hb <= 31 && t.wb >= 0 && t.wb <= 31 &&
-         t.fmt >= 0 && t.fmt <= 2 && (t.nc == 2 || t.nc == 4) && t.R >= 1 && t.R <= 4096 &&
-         t.ctas >= 1 && t.ctas <= 64;
+         t.fmt >= 0 && t.fmt <= 2 && (t.nc == 2 || t.nc == 4) && t.R >= 1 && t.R <= (1 << 20) &&
+         t.ctas >= 1 && t.ctas <= 64 && (t.kernel == 0 || (t.kernel == 1 && t.kind == 0 &&
+                                                           t.nc == 4 && t.R == tma_round_R(t.R)));
 }
 
 }  // namespace
@@ -732,8 +766,40 @@ extern "C" sobel4_status sobel4_tune(sobel4_handle h, int32_t height, int32_t wi
   cudaError_t e = cudaMalloc((void **)&src, sp * (size_t)height);
   if (e == cudaSuccess) e = cudaMalloc((void **)&dst, dp * (size_t)height * planes(fmt));
   if (e == cudaSuccess) e = cudaMemsetAsync(src, 0x5A, sp * (size_t)height, h->own_stream);
-  TuneEntry best = {0, ceil_log2(height), ceil_log2(width), (int)fmt, h->nc, 0, h->ctas_per_sm, 0};
+  TuneEntry best = {0, ceil_log2(height), ceil_log2(width), (int)fmt, h->nc, 0, h->ctas_per_sm, 0,
+                    0};
   bool have = false;
+  auto consider = [&](int kernel, int nc, int R, float us) {
+    if (!have || us < best.us) {
+      best.kernel = kernel;
+      best.nc = nc;
+      best.R = R;
+      best.us = us;
+      have = true;
+    }
+  };
+  // TMA-staged kernel: a few strip heights, including the one that gives every
+  // resident warp about one item.
+  if (h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced && tma_eligible(src, sp)) {
+    std::vector<int> cands;
+    if (h->rows_per_strip > 0) {
+      cands.push_back(tma_round_R(h->rows_per_strip));
+    } else {
+      const int r0 = tma_pick_R(fmt, h->sm_count, height, width);
+      for (int R : {8, 16, 32, tma_round_R(r0 * 2 / 3), r0, 2 * r0})
+        if (std::find(cands.begin(), cands.end(), R) == cands.end()) cands.push_back(R);
+    }
+    for (size_t b = 0; b < cands.size() && e == cudaSuccess; ++b) {
+      const int R = cands[b];
+      float us = 0.f;
+      e = median_us(h->own_stream, [&]() {
+        h->launches += 1;
+        return launch_tma_single(src, sp, dst, dp, height, width, border, fmt, R, h->sm_count,
+                                 next_pair(h), h->d_err, h->own_stream);
+      }, &us);
+      if (e == cudaSuccess) consider(1, 4, R, us);
+    }
+  }
   const int ncs[2] = {2, 4};
   const int Rs[4] = {8, 16, 32, 64};
   for (int a = 0; a < 2 && e == cudaSuccess; ++a) {
@@ -747,14 +813,10 @@ extern "C" sobel4_status sobel4_tune(sobel4_handle h, int32_t height, int32_t wi
         return launch_rg_single(im, border, fmt, Rs[b], ncs[a], h->sm_count, next_pair(h),
                                 h->own_stream);
       }, &us);
-      if (e == cudaSuccess && (!have || us < best.us)) {
-        best.nc = ncs[a];
-        best.R = Rs[b];
-        best.us = us;
-        have = true;
-      }
+      if (e == cudaSuccess) consider(0, ncs[a], Rs[b], us);
     }
   }
+  if (e == cudaSuccess && !have) e = cudaErrorInvalidValue;  // no candidate fits the options
   if (src) cudaFree(src);
   if (dst) cudaFree(dst);
   if (e != cudaSuccess) return cuda_fail(h, e);
@@ -769,7 +831,7 @@ extern "C" sobel4_status sobel4_tune_batched(sobel4_handle h, const sobel4_image
   if (!h || !imgs || n < 1 || !valid_enum(border, fmt)) return SOBEL4_ERR_INVALID_ARG;
   DeviceGuard g(h->device);
   const std::vector<TuneEntry> saved = h->tuned;
-  TuneEntry best = {1, 0, 0, (int)fmt, h->nc, kBatchR, h->ctas_per_sm, 0};
+  TuneEntry best = {1, 0, 0, (int)fmt, h->nc, kBatchR, h->ctas_per_sm, 0, 0};
   bool have = false;
   const int ncs[2] = {2, 4};
   const int Rs[3] = {8, 16, 32};
@@ -781,7 +843,7 @@ extern "C" sobel4_status sobel4_tune_batched(sobel4_handle h, const sobel4_image
     for (int b = 0; b < 3 && st == SOBEL4_OK; ++b) {
       if (h->rows_per_strip > 0 && Rs[b] != h->rows_per_strip) continue;
       for (int c = 0; c < 3 && st == SOBEL4_OK; ++c) {
-        const TuneEntry cand = {1, 0, 0, (int)fmt, ncs[a], Rs[b], ctas[c], 0};
+        const TuneEntry cand = {1, 0, 0, (int)fmt, ncs[a], Rs[b], ctas[c], 0, 0};
         h->tuned = saved;
         upsert(h, cand);
         float us = 0.f;
@@ -823,8 +885,8 @@ extern "C" sobel4_status sobel4_tune_save(sobel4_handle h, const char *path) {
     const TuneEntry &t = h->tuned[i];
     fprintf(f,
             "  {\"kind\": %d, \"hb\": %d, \"wb\": %d, \"fmt\": %d, \"nc\": %d, \"R\": %d, "
-            "\"ctas\": %d, \"us\": %.3f}%s\n",
-            t.kind, t.hb, t.wb, t.fmt, t.nc, t.R, t.ctas, t.us,
+            "\"ctas\": %d, \"kernel\": %d, \"us\": %.3f}%s\n",
+            t.kind, t.hb, t.wb, t.fmt, t.nc, t.R, t.ctas, t.kernel, t.us,
             i + 1 < h->tuned.size() ? "," : "");
   }
   fprintf(f, " ]}\n");
@@ -855,8 +917,8 @@ extern "C" sobel4_status sobel4_tune_load(sobel4_handle h, const char *path) {
     TuneEntry t;
     if (sscanf(line,
                " {\"kind\": %d, \"hb\": %d, \"wb\": %d, \"fmt\": %d, \"nc\": %d, \"R\": %d, "
-               "\"ctas\": %d, \"us\": %f}",
-               &t.kind, &t.hb, &t.wb, &t.fmt, &t.nc, &t.R, &t.ctas, &t.us) == 8) {
+               "\"ctas\": %d, \"kernel\": %d, \"us\": %f}",
+               &t.kind, &t.hb, &t.wb, &t.fmt, &t.nc, &t.R, &t.ctas, &t.kernel, &t.us) == 9) {
       if (!valid_entry(t)) {
         fclose(f);
         return SOBEL4_ERR_INVALID_ARG;

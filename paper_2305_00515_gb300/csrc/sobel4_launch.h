@@ -24,6 +24,18 @@ cudaError_t launch_rg_batched(const ImageDesc *d_descs, int n_img, int64_t total
                               unsigned int *d_queue, int border, int fmt, int R, int nc,
                               int grid, int sm_count, cudaStream_t st);
 
+// TMA-staged RG kernel (sobel4_tma.cuh) over one image whose source address
+// and pitch are multiples of 16 bytes (tma_eligible).  R must equal
+// tma_round_R(R) (a multiple of the kernel's row-step unroll).  Same
+// counter-pair contract as launch_rg_single; a stage wait that runs out sets
+// bit 0 of *err and the kernel returns early.
+bool tma_eligible(const uint8_t *src, size_t sp);
+int tma_pick_R(int fmt, int sm_count, int32_t H, int32_t W);
+int tma_round_R(int R);
+cudaError_t launch_tma_single(const uint8_t *src, size_t sp, void *dst, size_t dp, int32_t H,
+                              int32_t W, int border, int fmt, int R, int sm_count,
+                              unsigned int *pair, unsigned int *err, cudaStream_t st);
+
 // DIRECT kernel (one thread per output pixel).
 cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, cudaStream_t st);
 

@@ -1,10 +1,21 @@
 // sobel4_selftest.cu — on-device self-check of the magnitude step: the
-// library's F32 magnitude against CUDA's IEEE sqrtf((float)S), and its U8
-// magnitude against the exact rule min(255, round(sqrt(S))), for every S in
-// a range (the operator's whole domain is 0 .. 599,270,400).
+// library's F32 magnitudes (the scalar one of the lane-copy and direct
+// kernels, the packed-pair one of the TMA kernel) against CUDA's IEEE
+// sqrtf((float)S), and its U8 magnitudes against the exact rule
+// min(255, round(sqrt(S))), for every S in a range (the operator's whole
+// domain is 0 .. 599,270,400).
 #include "sobel4_launch.h"
+#include "sobel4_tma.cuh"
 
 namespace sobel4 {
+
+// exact rule: u = round(sqrt(S)) <=> (2u-1)^2 <= 4S < (2u+1)^2, saturated at 255
+__device__ __forceinline__ bool u8_ok(uint32_t u, int32_t s) {
+  const int64_t q = 4 * (int64_t)s;
+  return u == 255u ? q >= 509ll * 509ll
+                   : ((u == 0u || (int64_t)(2 * u - 1) * (2 * u - 1) <= q) &&
+                      q < (int64_t)(2 * u + 1) * (2 * u + 1));
+}
 
 __global__ void check_magnitude_kernel(int64_t s0, int64_t s1, unsigned long long *bad) {
   unsigned long long nb = 0;
@@ -13,13 +24,16 @@ __global__ void check_magnitude_kernel(int64_t s0, int64_t s1, unsigned long lon
     const int32_t s = (int32_t)i;
     const float want = sqrtf((float)s);
     if (__float_as_uint(magnitude_f32(s)) != __float_as_uint(want)) ++nb;
-    // exact rule: u = round(sqrt(S)) <=> (2u-1)^2 <= 4S < (2u+1)^2, saturated at 255
-    const uint32_t u = magnitude_u8(s);
-    const int64_t q = 4 * (int64_t)s;
-    const bool ok = u == 255u ? q >= 509ll * 509ll
-                              : ((u == 0u || (int64_t)(2 * u - 1) * (2 * u - 1) <= q) &&
-                                 q < (int64_t)(2 * u + 1) * (2 * u + 1));
-    if (!ok) ++nb;
+    if (!u8_ok(magnitude_u8(s), s)) ++nb;
+    // packed pair: s in the low lane, its mirror s1 - 1 - (s - s0) in the high lane
+    const int32_t m = (int32_t)(s1 - 1 - (i - s0));
+    float ga, gb;
+    tma::magnitude_f32x2(s, m, ga, gb);
+    if (__float_as_uint(ga) != __float_as_uint(want)) ++nb;
+    if (__float_as_uint(gb) != __float_as_uint(sqrtf((float)m))) ++nb;
+    uint32_t ua, ub;
+    tma::magnitude_u8x2(s, m, ua, ub);
+    if (!u8_ok(ua, s) || !u8_ok(ub, m)) ++nb;
   }
   if (nb) atomicAdd(bad, nb);
 }

@@ -1,0 +1,815 @@
+// sobel4_tma.cuh — TMA-staged register-window kernel for single images whose
+// rows start on 16-byte boundaries (sm_103a).
+//
+// The operator is that of sobel4_device.cuh (Section 3.1, Eq. 3 and Eq. 4);
+// the schedule is the paper's register-window design (Section 4.3) rebuilt
+// around the Blackwell memory path:
+//
+//  * Work item = one warp: a 128-column segment and a band of 2R rows, split
+//    into two strips of R rows that travel together in the two 16-bit halves
+//    of every register (v = lo + 65536 * hi, lo = strip a, hi = strip b).  The
+//    host sizes R so that the items fill every resident warp about once, which
+//    keeps the 4-row window fill of each strip (Section 4.3.2) near 3 % of
+//    the rows.
+//  * Staging: lane 0 of each warp issues 2-D tensor copies (cp.async.bulk.tensor,
+//    TMA) of 8 rows x 160 bytes per strip into a 3-slot shared-memory ring,
+//    completing on one mbarrier per slot; rows and columns outside the image
+//    arrive as zeros from the copy engine, which is the CONSTANT0 rule and
+//    harmless under VALID.  Under REPLICATE / REFLECT101 the lanes whose
+//    columns cross the left or right edge read their bytes from the staged row
+//    at the mapped columns, and rows outside the image are gathered from the
+//    mapped rows in global memory.  This is the prefetch of Section 4.3.4, two
+//    stages (16 rows) ahead.
+//  * Per new row each column does the 1x5 horizontal passes (Eq. 6, the K_y
+//    smoothing row, the K_d+ rows of Eq. 12 and the K_d- rows of Eq. 18 with
+//    D = p3 - p1) and transposed 5-tap vertical filters (Eq. 7, Eq. 15,
+//    Eq. 19), on packed pairs.  Scaled terms are split between shift-adds
+//    (integer ALU pipe) and multiply-adds (FMA pipe) so that neither pipe
+//    limits the issue rate.
+//  * The four packed responses leave the vertical pass with the low half
+//    biased by 2^15, which makes both halves' squares one mad.hi each:
+//    with v = (lo + 2^15) + 2^16 hi, (v << 16) + 2^31 = lo * 2^16 and
+//    v & 0xffff0000 = hi * 2^16 exactly (Eq. 4 and Eq. 11: R_d = P' + M',
+//    R_dt = P' - M').  The square root runs on packed fp32 pairs.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sobel4_device.cuh"
+
+namespace sobel4 {
+namespace tma {
+
+constexpr int kNC = 4;                        // columns per lane
+constexpr int kCols = 32 * kNC;               // columns per warp segment
+constexpr int kBoxW = 160;                    // staged bytes per row: columns x0-16 .. x0+143
+constexpr int kStageRows = 8;                 // rows per stage and strip
+constexpr int kSlots = 3;                     // ring slots per warp
+constexpr int kStripBytes = kStageRows * kBoxW;     // 1280
+constexpr int kSlotBytes = 2 * kStripBytes;         // 2560 (strip a, then strip b)
+constexpr int kWarps = 4;                     // warps per CTA
+constexpr uint32_t kBias = 0x8000u;           // low-half bias of the tail values
+#ifndef SOBEL4_TMA_UNROLL
+#define SOBEL4_TMA_UNROLL 4
+#endif
+constexpr int kUnroll = SOBEL4_TMA_UNROLL;    // row steps per main-loop trip (2 or 4)
+static_assert(kUnroll == 2 || kUnroll == 4, "the stage length must be a multiple of the unroll");
+
+#ifndef SOBEL4_TMA_MIN_CTAS
+#define SOBEL4_TMA_MIN_CTAS 4
+#endif
+constexpr int kMinCtas = SOBEL4_TMA_MIN_CTAS;
+
+#ifndef SOBEL4_TMA_SQ
+#define SOBEL4_TMA_SQ 1  // squares: 0 = high-word multiply-adds, 1 = unpacked halves + multiply-adds
+#endif
+#ifndef SOBEL4_TMA_I2F
+#define SOBEL4_TMA_I2F 0  // S -> float: 0 = conversion instruction, 1 = exponent-field splice
+#endif
+#ifndef SOBEL4_TMA_FP2
+#define SOBEL4_TMA_FP2 0  // square root: 1 = packed fp32 pairs, 0 = scalar
+#endif
+#ifndef SOBEL4_TMA_LIN
+#define SOBEL4_TMA_LIN 0  // scaled terms: 0 = mixed, 1 = all multiply-adds, 2 = all shift-adds
+#endif
+#ifndef SOBEL4_TMA_SHF
+#define SOBEL4_TMA_SHF 1  // shift-add terms: 0 = shifts, 1 = funnel shifts (integer ALU only)
+#endif
+
+// Upper bound on one mbarrier wait (globaltimer nanoseconds) before the
+// kernel gives up, records the failure and leaves.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+struct __align__(128) WarpRing {
+  uint8_t slot[kSlots][kSlotBytes];
+  uint64_t bar[kSlots];
+};
+
+// One image as the TMA kernel sees it (the source is staged through the
+// tensor map; src/sp serve only the edge-rule gathers).
+struct TmaImage {
+  const uint8_t *src;  // read directly only for rows outside the image (edge rules)
+  uint64_t sp;
+  void *dst;
+  uint64_t dp;
+  int32_t H, W;
+  int32_t n_seg, n_band;
+  int32_t dst_align;  // largest power of two (<= 16) dividing dst and dp
+};
+
+// ---------------------------------------------------------------------------
+// PTX wrappers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Orders this thread's earlier shared-memory accesses (generic proxy) before
+// later copies into shared memory by the copy engine (async proxy).
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 2-D tile load: box at element coordinates (x, y) of `map` into shared
+// memory at `dst`, completing `bar` with the box's byte count.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t lds_u16(uint32_t a) {
+  uint16_t v;
+  asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint32_t lds_u8(uint32_t a) {
+  uint16_t v;
+  asm volatile("ld.shared.u8 %0, [%1];" : "=h"(v) : "r"(a));
+  return v;
+}
+
+// x << k for the shift-add terms.
+template <int K>
+__device__ __forceinline__ uint32_t shl(uint32_t x) {
+#if SOBEL4_TMA_SHF
+  return __funnelshift_l(0u, x, K);
+#else
+  return x << K;
+#endif
+}
+
+// Integer multiply-add with a constant multiplier (FMA-pipe form).
+template <uint32_t K>
+__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "n"(K), "r"(b));
+  return d;
+}
+
+// k*a + b for the scaled terms of the passes (k in {2, 3, 4, 6, 8}); the
+// form (multiply-add or shift-adds) is chosen per term class below.
+template <uint32_t K, int MODE>
+__device__ __forceinline__ uint32_t scaled(uint32_t a, uint32_t b) {
+  if (MODE == 1) return imad<K>(a, b);
+  if constexpr (K == 2) return shl<1>(a) + b;
+  else if constexpr (K == 4) return shl<2>(a) + b;
+  else if constexpr (K == 8) return shl<3>(a) + b;
+  else if constexpr (K == 3) return shl<1>(a) + a + b;
+  else return shl<1>(shl<1>(a) + a) + b;  // K == 6
+}
+
+__device__ __forceinline__ int32_t mulhi(int32_t a, int32_t b) {
+  int32_t d;
+  asm("mul.hi.s32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+__device__ __forceinline__ int32_t madhi(int32_t a, int32_t b, int32_t c) {
+  int32_t d;
+  asm("mad.hi.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
+// Packed fp32 pairs (register pair: low word = strip a, high word = strip b).
+__device__ __forceinline__ uint64_t pk(float a, float b) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk(uint64_t v, float &a, float &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// sqrtf((float)s) for two values of S (0 <= s <= 599,270,400) at once:
+// y ~ 1/sqrt(x) from the hardware approximation, g = x*y, then one Newton
+// correction whose residual g*g - x is formed exactly by a fused multiply-add
+// (Markstein, "Computation of elementary functions on the IBM RISC
+// System/6000", 1990): G = g - (y/2)(g*g - x).  x + 2^-126 feeds the
+// approximation so that x = 0 gives y finite and G = +0; for x >= 1 the sum
+// is x.  Checked exhaustively on the device against IEEE sqrtf over the whole
+// domain (sobel4_check_magnitude).
+__device__ __forceinline__ float magnitude_f32_tiny(int32_t s) {
+  const float x = (float)s;
+  const float y = rsqrt_approx(x + 0x1p-126f);
+  const float g = x * y;
+  const float hn = y * -0.5f;
+  return fmaf(fmaf(g, g, -x), hn, g);
+}
+
+__device__ __forceinline__ void magnitude_f32x2(int32_t sa, int32_t sb, float &ga, float &gb) {
+#if !SOBEL4_TMA_FP2
+  ga = magnitude_f32_tiny(sa);
+  gb = magnitude_f32_tiny(sb);
+  return;
+#endif
+  constexpr uint64_t kTiny = 0x0080000000800000ull;     // (2^-126, 2^-126)
+  constexpr uint64_t kNegHalf = 0xBF000000BF000000ull;  // (-0.5, -0.5)
+#if SOBEL4_TMA_I2F
+  // float(s) = RN(hi * 128 + lo), hi = s >> 7 < 2^23 and lo = s & 127 both exact
+  // as floats (spliced into the mantissa of 2^23); one fused multiply-add rounds.
+  constexpr uint64_t kTwo23 = 0x4B0000004B000000ull;   // (2^23, 2^23)
+  constexpr uint64_t k128 = 0x4300000043000000ull;     // (128, 128)
+  const uint64_t hb = pk(__int_as_float(0x4B000000 | (uint32_t)(sa >> 7)),
+                         __int_as_float(0x4B000000 | (uint32_t)(sb >> 7)));
+  const uint64_t lb = pk(__int_as_float(0x4B000000 | (uint32_t)(sa & 127)),
+                         __int_as_float(0x4B000000 | (uint32_t)(sb & 127)));
+  const uint64_t x = fma2(sub2(hb, kTwo23), k128, sub2(lb, kTwo23));
+#else
+  const uint64_t x = pk((float)sa, (float)sb);
+#endif
+  float ta, tb;
+  upk(add2(x, kTiny), ta, tb);
+  const uint64_t y = pk(rsqrt_approx(ta), rsqrt_approx(tb));
+  const uint64_t g = mul2(x, y);
+  const uint64_t hn = mul2(y, kNegHalf);
+  const uint64_t xn = sub2(0ull, x);
+  const uint64_t r = fma2(g, g, xn);
+  upk(fma2(r, hn, g), ga, gb);
+}
+
+// min(255, round(sqrt(S))) from the F32 magnitude (see magnitude_u8).
+__device__ __forceinline__ void magnitude_u8x2(int32_t sa, int32_t sb, uint32_t &ua,
+                                               uint32_t &ub) {
+  float ga, gb;
+  magnitude_f32x2(sa, sb, ga, gb);
+  ua = min(__float2uint_rn(ga), 255u);
+  ub = min(__float2uint_rn(gb), 255u);
+}
+
+// ---------------------------------------------------------------------------
+// One column, one new row.
+// ---------------------------------------------------------------------------
+struct Col {
+  uint32_t X1, X2, X3, hdp;   // R_x : vertical [1 4 6 4 1] over hd (transposed form)
+  uint32_t Y3, Y2n, Y1n, hsp; // R_y : vertical [-1 -2 0 2 1] over hs
+  uint32_t P3, P2n, P1n, q0p; // P'  : rows -q0', -q1', 0, q1', q0'
+  uint32_t M1, M2, M3, r0p;   // M'  : rows r0', 3hd, r2', 3hd, r0'
+};
+
+// p0..p4: packed pixels of columns x-2..x+2.  With TAIL the four packed
+// responses centred two rows above the new row are returned biased
+// (low half + 2^15): vx = R_x, vy = R_y, vd = R_d = P' + M', vt = R_dt = P' - M'.
+template <bool TAIL>
+__device__ __forceinline__ void column_step(uint32_t p0, uint32_t p1, uint32_t p2, uint32_t p3,
+                                            uint32_t p4, Col &c, uint32_t &vx, uint32_t &vy,
+                                            uint32_t &vd, uint32_t &vt) {
+  // Horizontal 1x5 passes (A = p0+p4, B = p1+p3, C = p2, E = p4-p0, D = p3-p1).
+  const uint32_t A = p0 + p4, B = p1 + p3, E = p4 - p0, D = p3 - p1;
+  // MA: terms written as multiply-adds in the mixed form; SA: as shift-adds.
+  constexpr int MA = SOBEL4_TMA_LIN == 2 ? 2 : 1;
+  constexpr int SA = SOBEL4_TMA_LIN == 1 ? 1 : 2;
+  const uint32_t hd = E + D + D;                            // [-1 -2 0 2 1]  (Eq. 6, K_x row)
+  const uint32_t hs = scaled<6, MA>(p2, scaled<4, SA>(B, A));  // [ 1  4 6 4 1]  (K_y row)
+  const uint32_t q1 = scaled<2, SA>(B + p2, hs);            // [ 1  6 8 6 1] = -K_d+ row 1 / 2 (Eq. 12)
+  const uint32_t q0 = scaled<3, MA>(A + B, p2);             // [ 3  3 1 3 3] = -K_d+ row 0 / 2
+  const uint32_t r0 = scaled<3, MA>(E, D);                  // [-3 -1 0 1 3] =  K_d- row 0 / 2 (Eq. 18)
+  const uint32_t r2 = scaled<8, SA>(D, E);                  // [-1 -8 0 8 1] =  K_d- row 2 / 2
+  // Vertical passes, transposed form.
+  if (TAIL) {
+    vx = c.X3 + hd + kBias;                       // [1 4 6 4 1] over hd (Eq. 7)
+    vy = c.Y3 + hs + kBias;                       // [-1 -2 0 2 1] over hs
+    const uint32_t pp = c.P3 + q0;                // P' (Eq. 15)
+    const uint32_t mm = c.M3 + r0;                // M' (Eq. 19)
+    vd = pp + mm + kBias;                         // R_d  (Eq. 11)
+    vt = pp - mm + kBias;                         // R_dt
+  }
+  c.X3 = scaled<4, SA>(hd, c.X2);
+  c.X2 = scaled<6, MA>(hd, c.X1);
+  c.X1 = scaled<4, SA>(hd, c.hdp);
+  c.hdp = hd;
+  c.Y3 = hs + hs - c.Y2n;
+  c.Y2n = c.Y1n;
+  c.Y1n = c.hsp + hs + hs;
+  c.hsp = hs;
+  c.P3 = q1 - c.P2n;
+  c.P2n = c.P1n;
+  c.P1n = c.q0p + q1;
+  c.q0p = q0;
+  c.M3 = scaled<3, MA>(hd, c.M2);
+  c.M2 = c.M1 + r2;
+  c.M1 = scaled<3, MA>(hd, c.r0p);
+  c.r0p = r0;
+}
+
+// Unbiased low and high halves of a biased packed value (S16X4 format).
+__device__ __forceinline__ int32_t lo_of(uint32_t v) { return (int32_t)(v & 0xFFFFu) - 0x8000; }
+__device__ __forceinline__ int32_t hi_of(uint32_t v) { return (int32_t)v >> 16; }
+
+// S of both strips from one column's biased packed responses (Eq. 4).
+__device__ __forceinline__ void squares(uint32_t vx, uint32_t vy, uint32_t vd, uint32_t vt,
+                                        int32_t &sa, int32_t &sb) {
+#if SOBEL4_TMA_SQ
+  const int32_t ax = lo_of(vx), ay = lo_of(vy), ad = lo_of(vd), at = lo_of(vt);
+  const int32_t bx = hi_of(vx), by = hi_of(vy), bd = hi_of(vd), bt = hi_of(vt);
+  sa = ax * ax + ay * ay + ad * ad + at * at;
+  sb = bx * bx + by * by + bd * bd + bt * bt;
+#else
+  const int32_t wx = (int32_t)imad<0x10000u>(vx, 0x80000000u);
+  const int32_t wy = (int32_t)imad<0x10000u>(vy, 0x80000000u);
+  const int32_t wd = (int32_t)imad<0x10000u>(vd, 0x80000000u);
+  const int32_t wt = (int32_t)imad<0x10000u>(vt, 0x80000000u);
+  sa = madhi(wx, wx, madhi(wy, wy, madhi(wd, wd, mulhi(wt, wt))));
+  const int32_t tx = (int32_t)(vx & 0xFFFF0000u), ty = (int32_t)(vy & 0xFFFF0000u);
+  const int32_t td = (int32_t)(vd & 0xFFFF0000u), tt = (int32_t)(vt & 0xFFFF0000u);
+  sb = madhi(tx, tx, madhi(ty, ty, madhi(td, td, mulhi(tt, tt))));
+#endif
+}
+
+// Packed columns c[0..7] (columns x-2 .. x+5 of both strips) from the staged
+// rows: column x-2 of strip a at shared address `a`, of strip b at a + kStripBytes.
+__device__ __forceinline__ void read_cols(uint32_t a, uint32_t c[8]) {
+  const uint32_t b = a + kStripBytes;
+  const uint32_t a0 = lds_u16(a), a1 = lds_u32(a + 2), a2 = lds_u16(a + 6);
+  const uint32_t b0 = lds_u16(b), b1 = lds_u32(b + 2), b2 = lds_u16(b + 6);
+  c[0] = __byte_perm(a0, b0, 0x6420);
+  c[1] = __byte_perm(a0, b0, 0x7531);
+  const uint32_t t1 = __byte_perm(a1, b1, 0x5140);
+  const uint32_t t2 = __byte_perm(a1, b1, 0x7362);
+  c[2] = __byte_perm(t1, 0u, 0x4140);
+  c[3] = __byte_perm(t1, 0u, 0x4342);
+  c[4] = __byte_perm(t2, 0u, 0x4140);
+  c[5] = __byte_perm(t2, 0u, 0x4342);
+  c[6] = __byte_perm(a2, b2, 0x6420);
+  c[7] = __byte_perm(a2, b2, 0x7531);
+}
+
+// Edge lanes under REPLICATE / REFLECT101: column j comes from staged byte
+// offset off[j] of the row (the mapped column).
+__device__ __forceinline__ void read_cols_mapped(uint32_t row_a, const uint32_t off[8],
+                                                 uint32_t c[8]) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    c[j] = lds_u8(row_a + off[j]) | (lds_u8(row_a + kStripBytes + off[j]) << 16);
+}
+
+// Rows outside the image under REPLICATE / REFLECT101: the strip's bytes come
+// from the mapped row (and mapped columns) in global memory; the other strip
+// reads its staged row.
+__device__ __forceinline__ void gather_cols(const TmaImage &im, uint32_t row_a,
+                                            const uint32_t off[8], int x, int ra, int rb,
+                                            bool out_a, bool out_b, int border, uint32_t c[8]) {
+  bool z;
+  const uint8_t *ga = im.src + (uint64_t)(uint32_t)map_index(ra, im.H, border, &z) * im.sp;
+  const uint8_t *gb = im.src + (uint64_t)(uint32_t)map_index(rb, im.H, border, &z) * im.sp;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int col = map_index(x - 2 + j, im.W, border, &z);
+    const uint32_t va = out_a ? (uint32_t)__ldg(ga + col) : lds_u8(row_a + off[j]);
+    const uint32_t vb = out_b ? (uint32_t)__ldg(gb + col) : lds_u8(row_a + kStripBytes + off[j]);
+    c[j] = va | (vb << 16);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stores of one output row pair (strip a row, strip b row) for columns
+// x..x+3.  GEN: per-column and per-row masks (edge items); otherwise four
+// columns of both rows, vector stores.
+// ---------------------------------------------------------------------------
+template <int FMT, bool GEN>
+__device__ __forceinline__ void store_rows(const TmaImage &im, uint8_t *row_a, uint8_t *row_b,
+                                           int x, const uint32_t vx[4], const uint32_t vy[4],
+                                           const uint32_t vd[4], const uint32_t vt[4],
+                                           bool st_a, bool st_b, bool zero_a, bool zero_b,
+                                           uint32_t colmask, uint32_t framemask, bool vec) {
+  if constexpr (FMT == kS16x4) {
+    const uint64_t plane = (uint64_t)(uint32_t)im.H * im.dp;
+    const uint32_t *vals[4] = {vx, vy, vd, vt};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t *v = vals[q];
+      int16_t *pa = (int16_t *)(row_a + q * plane) + x;
+      int16_t *pb = (int16_t *)(row_b + q * plane) + x;
+      if (!GEN) {
+        const uint2 la = make_uint2(__byte_perm(v[0], v[1], 0x5410) ^ 0x80008000u,
+                                    __byte_perm(v[2], v[3], 0x5410) ^ 0x80008000u);
+        const uint2 lb = make_uint2(__byte_perm(v[0], v[1], 0x7632),
+                                    __byte_perm(v[2], v[3], 0x7632));
+        if (st_a) *(uint2 *)pa = la;
+        if (st_b) *(uint2 *)pb = lb;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (!((colmask >> k) & 1u)) continue;
+          const bool fk = (framemask >> k) & 1u;
+          if (st_a) pa[k] = (int16_t)((zero_a || fk) ? 0 : lo_of(v[k]));
+          if (st_b) pb[k] = (int16_t)((zero_b || fk) ? 0 : hi_of(v[k]));
+        }
+      }
+    }
+  } else {
+  int32_t sa[4], sb[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) squares(vx[k], vy[k], vd[k], vt[k], sa[k], sb[k]);
+  if constexpr (FMT == kF32) {
+    float ga[4], gb[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) magnitude_f32x2(sa[k], sb[k], ga[k], gb[k]);
+    float *pa = (float *)row_a + x, *pb = (float *)row_b + x;
+    if (!GEN) {
+      if (st_a) *(float4 *)pa = make_float4(ga[0], ga[1], ga[2], ga[3]);
+      if (st_b) *(float4 *)pb = make_float4(gb[0], gb[1], gb[2], gb[3]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const bool fk = (framemask >> k) & 1u;
+        if (zero_a || fk) ga[k] = 0.0f;
+        if (zero_b || fk) gb[k] = 0.0f;
+      }
+      if (vec && colmask == 0xFu) {
+        if (st_a) *(float4 *)pa = make_float4(ga[0], ga[1], ga[2], ga[3]);
+        if (st_b) *(float4 *)pb = make_float4(gb[0], gb[1], gb[2], gb[3]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (!((colmask >> k) & 1u)) continue;
+          if (st_a) pa[k] = ga[k];
+          if (st_b) pb[k] = gb[k];
+        }
+      }
+    }
+  } else {
+    uint32_t ua[4], ub[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) magnitude_u8x2(sa[k], sb[k], ua[k], ub[k]);
+    uint8_t *pa = row_a + x, *pb = row_b + x;
+    if (GEN) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const bool fk = (framemask >> k) & 1u;
+        if (zero_a || fk) ua[k] = 0u;
+        if (zero_b || fk) ub[k] = 0u;
+      }
+    }
+    const uint32_t wa = ua[0] | (ua[1] << 8) | (ua[2] << 16) | (ua[3] << 24);
+    const uint32_t wb = ub[0] | (ub[1] << 8) | (ub[2] << 16) | (ub[3] << 24);
+    if (!GEN) {
+      if (st_a) *(uint32_t *)pa = wa;
+      if (st_b) *(uint32_t *)pb = wb;
+    } else if (vec && colmask == 0xFu) {
+      if (st_a) *(uint32_t *)pa = wa;
+      if (st_b) *(uint32_t *)pb = wb;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (!((colmask >> k) & 1u)) continue;
+        if (st_a) pa[k] = (uint8_t)ua[k];
+        if (st_b) pb[k] = (uint8_t)ub[k];
+      }
+    }
+  }
+  }
+}
+
+// Zero output element (y, x) in every plane of the format.
+template <int FMT>
+__device__ __forceinline__ void zero_px(const TmaImage &im, int y, int x) {
+  uint8_t *row = (uint8_t *)im.dst + (uint64_t)(uint32_t)y * im.dp;
+  if constexpr (FMT == kF32) {
+    ((float *)row)[x] = 0.0f;
+  } else if constexpr (FMT == kU8) {
+    row[x] = 0;
+  } else {
+    const uint64_t plane = (uint64_t)(uint32_t)im.H * im.dp;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) ((int16_t *)(row + q * plane))[x] = 0;
+  }
+}
+
+// Zero output elements (y, x..x+3) with vector stores (the destination is
+// vector-aligned on the fast path).
+template <int FMT>
+__device__ __forceinline__ void zero_row4(const TmaImage &im, int y, int x) {
+  uint8_t *row = (uint8_t *)im.dst + (uint64_t)(uint32_t)y * im.dp;
+  if constexpr (FMT == kF32) {
+    *(float4 *)((float *)row + x) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  } else if constexpr (FMT == kU8) {
+    *(uint32_t *)(row + x) = 0u;
+  } else {
+    const uint64_t plane = (uint64_t)(uint32_t)im.H * im.dp;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) *(uint2 *)((int16_t *)(row + q * plane) + x) = make_uint2(0u, 0u);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One warp item.  Returns false when a stage wait ran out (recorded in *err).
+// ---------------------------------------------------------------------------
+struct ItemCtx {
+  const CUtensorMap *map;   // source image, box 160 x 8
+  uint32_t ring;            // shared address of this warp's ring
+  uint32_t gstage;          // stages this warp has used so far (slot / parity counter)
+};
+
+// Waits until stage counter g has landed (all lanes agree on the outcome).
+__device__ __forceinline__ bool wait_stage(const ItemCtx &cx, uint32_t g, unsigned int *err) {
+  const uint32_t bar = cx.ring + (uint32_t)(kSlots * kSlotBytes + 8 * (g % kSlots));
+  const uint32_t parity = (g / kSlots) & 1u;
+  if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+    if (__any_sync(0xffffffffu, global_ns() - t0 > kWaitLimitNs)) {
+      if ((threadIdx.x & 31) == 0) atomicOr(err, 1u);
+      return false;
+    }
+  }
+}
+
+// After a failed wait: let the copies this warp still has in flight land
+// (bounded), so that none writes into shared memory after the CTA is gone.
+__device__ __forceinline__ void drain_stages(const ItemCtx &cx, uint32_t g_from, uint32_t g_to) {
+  for (uint32_t g = g_from; g < g_to; ++g) {
+    const uint32_t bar = cx.ring + (uint32_t)(kSlots * kSlotBytes + 8 * (g % kSlots));
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, (g / kSlots) & 1u) && global_ns() - t0 < kWaitLimitNs) {
+    }
+  }
+}
+
+// FULL: every output row of both strips lies inside the image (no row checks).
+template <int FMT, bool GEN, bool FULL>
+__device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg, int band,
+                                         int R, int lane, ItemCtx &cx, unsigned int *err) {
+  const int H = im.H, W = im.W;
+  const int x0 = seg * kCols;
+  const int x = x0 + kNC * lane;
+  const int ya = band * 2 * R;
+  const int yb = ya + R;
+  const int steps = R + 4;
+  const int n_stages = (steps + kStageRows - 1) / kStageRows;
+  const uint32_t g0 = cx.gstage;
+  const bool map_rows = GEN && (border == kReplicate || border == kReflect101);
+
+  // Producer: lane 0 copies stage j (rows 8j .. 8j+7 of both strips).
+  auto issue = [&](int j) {
+    const uint32_t g = g0 + (uint32_t)j;
+    const uint32_t slot = cx.ring + (uint32_t)(kSlotBytes * (g % kSlots));
+    const uint32_t bar = cx.ring + (uint32_t)(kSlots * kSlotBytes + 8 * (g % kSlots));
+    mbar_expect_tx(bar, (uint32_t)kSlotBytes);
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+      tma_load_2d(slot + (uint32_t)(s * kStripBytes), cx.map, x0 - 16,
+                  (s ? yb : ya) - 2 + kStageRows * j, bar);
+  };
+
+  __syncwarp();  // every lane is done with the ring slots about to be refilled
+  if (lane == 0) {
+    fence_proxy_async();
+    for (int j = 0; j < kSlots && j < n_stages; ++j) issue(j);
+  }
+
+  // Edge-item bookkeeping.
+  uint32_t colmask = 0xFu, framemask = 0u;
+  bool mapped_lane = false;
+  uint32_t off[8];
+  const int na = min(R, H - ya);           // output rows of strip a inside the image
+  const int nb = max(0, min(R, H - yb));   // ... of strip b
+  bool vec = true;
+  if (GEN) {
+    colmask = 0u;
+#pragma unroll
+    for (int k = 0; k < kNC; ++k) {
+      if (x + k < W) colmask |= 1u << k;
+      if (border == kValid && (x + k < 2 || x + k > W - 3)) framemask |= 1u << k;
+    }
+    mapped_lane = (border == kReplicate || border == kReflect101) && (x - 2 < 0 || x + 5 >= W);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      bool z;
+      const int m = map_index(x - 2 + j, W, border, &z);
+      const int o = m - (x0 - 16);
+      off[j] = (uint32_t)(o < 0 ? 0 : (o > kBoxW - 1 ? kBoxW - 1 : o));
+    }
+    const int vec_need = FMT == kF32 ? 16 : (FMT == kU8 ? 4 : 8);
+    vec = im.dst_align >= vec_need;
+  }
+
+  Col st[kNC];
+#pragma unroll
+  for (int k = 0; k < kNC; ++k) st[k] = Col{0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u,
+                                             0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+  uint8_t *row_a = (uint8_t *)im.dst + (uint64_t)(uint32_t)ya * im.dp;
+  uint8_t *row_b = (uint8_t *)im.dst + (uint64_t)(uint32_t)min(yb, H - 1) * im.dp;
+  const uint32_t lane_off = (uint32_t)(14 + kNC * lane);  // column x-2 in a staged row
+
+  auto step = [&](uint32_t rd, int s, bool tail) {
+    const int i = s - 4;  // output row of this step within each strip
+    uint32_t c[8];
+    if (GEN) {
+      const int ra = ya - 2 + s, rb = yb - 2 + s;  // input rows of this step
+      const bool out_a = map_rows && (ra < 0 || ra >= H);
+      const bool out_b = map_rows && (rb < 0 || rb >= H);
+      if (out_a || out_b) gather_cols(im, rd - lane_off, off, x, ra, rb, out_a, out_b, border, c);
+      else if (mapped_lane) read_cols_mapped(rd - lane_off, off, c);
+      else read_cols(rd, c);
+    } else {
+      read_cols(rd, c);
+    }
+    uint32_t vx[kNC], vy[kNC], vd[kNC], vt[kNC];
+    if (tail) {
+#pragma unroll
+      for (int k = 0; k < kNC; ++k)
+        column_step<true>(c[k], c[k + 1], c[k + 2], c[k + 3], c[k + 4], st[k], vx[k], vy[k],
+                          vd[k], vt[k]);
+      const bool st_a = FULL || i < na, st_b = FULL || i < nb;
+      bool zero_a = false, zero_b = false;
+      if (GEN) {
+        if (border == kValid) {
+          zero_a = ya + i < 2 || ya + i > H - 3;
+          zero_b = yb + i < 2 || yb + i > H - 3;
+        }
+      }
+      store_rows<FMT, GEN>(im, row_a, row_b, x, vx, vy, vd, vt, st_a, st_b, zero_a, zero_b,
+                           colmask, framemask, vec);
+      row_a += im.dp;
+      row_b += im.dp;
+    } else {
+#pragma unroll
+      for (int k = 0; k < kNC; ++k)
+        column_step<false>(c[k], c[k + 1], c[k + 2], c[k + 3], c[k + 4], st[k], vx[k], vy[k],
+                           vd[k], vt[k]);
+    }
+  };
+
+  if (!wait_stage(cx, g0, err)) {
+    drain_stages(cx, g0 + 1, g0 + (uint32_t)min(kSlots, n_stages));
+    return false;
+  }
+  uint32_t rd = cx.ring + (uint32_t)(kSlotBytes * (g0 % kSlots)) + lane_off;
+#pragma unroll
+  for (int s = 0; s < 4; ++s)  // rows 0..3 only fill the window
+    step(rd + (uint32_t)(s * kBoxW), s, false);
+  rd += 4 * kBoxW;
+  // Main loop: kUnroll row steps per trip (R is a multiple of kUnroll, so the
+  // trips tile the steps and the stage boundaries fall on trip boundaries).
+#pragma unroll 1
+  for (int s = 4; s < steps; s += kUnroll) {
+    if ((s & (kStageRows - 1)) == 0) {
+      const int j = s / kStageRows;
+      __syncwarp();  // stage j-1 has been read by every lane
+      if (lane == 0 && j - 1 + kSlots < n_stages) {
+        fence_proxy_async();
+        issue(j - 1 + kSlots);
+      }
+      if (!wait_stage(cx, g0 + (uint32_t)j, err)) {
+        drain_stages(cx, g0 + (uint32_t)j + 1, g0 + (uint32_t)min(j - 1 + kSlots + 1, n_stages));
+        return false;
+      }
+      rd = cx.ring + (uint32_t)(kSlotBytes * ((g0 + (uint32_t)j) % kSlots)) + lane_off;
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) step(rd + (uint32_t)(u * kBoxW), s + u, true);
+    rd += kUnroll * kBoxW;
+  }
+  cx.gstage = g0 + (uint32_t)n_stages;
+  if (!GEN && border == kValid) {
+    // The paper's rule leaves the 2-pixel frame at 0.  The fast path computed
+    // it from zero-filled halos; the lane that stored each frame element now
+    // overwrites it (same thread, later store).
+    const int yr[2] = {ya, yb}, nr[2] = {na, nb};
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int f[4] = {0, 1, H - 2, H - 1};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (f[q] >= yr[t] && f[q] < yr[t] + nr[t] && (q < 2 || f[q] > 1)) zero_row4<FMT>(im, f[q], x);
+    }
+    // Frame columns {0, 1, W-2, W-1} inside the segment: all lanes share the
+    // rows; the barrier orders the stores of the lanes that computed them.
+    if (x0 < 2 || x0 + kCols > W - 2) {
+      __syncwarp();
+      const int fc[4] = {0, 1, W - 2, W - 1};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = fc[q];
+        if (c < x0 || c >= x0 + kCols || (q >= 2 && c < 2)) continue;
+        for (int r = lane; r < na + nb; r += 32) zero_px<FMT>(im, r < na ? ya + r : yb + r - na, c);
+      }
+    }
+  }
+  return true;
+}
+
+// An item for the fast path: every lane's four columns inside the image, a
+// destination that takes one vector store per lane and row, and either a
+// border rule the copy engine's zero fill serves (CONSTANT0; VALID with the
+// frame zeroed afterwards) or every input row and column inside the image.
+__device__ __forceinline__ bool fast_item(const TmaImage &im, int border, int seg, int band,
+                                          int R, int fmt) {
+  const int x0 = seg * kCols;
+  const int ya = band * 2 * R;
+  const int vec_need = fmt == kF32 ? 16 : (fmt == kU8 ? 4 : 8);
+  if (im.dst_align < vec_need || x0 + kCols > im.W) return false;
+  if (border == kValid || border == kConstant0) return true;
+  return x0 >= 2 && x0 + kCols + 2 <= im.W && ya >= 2 && ya + 2 * R + 2 <= im.H;
+}
+
+// The single-image kernel: persistent CTAs of 4 warps; each warp pulls items
+// (band-major) from the counter pair[0]; the last warp out resets the pair.
+template <int FMT>
+__global__ void __launch_bounds__(kWarps * 32, kMinCtas)
+    tma_single_kernel(const __grid_constant__ CUtensorMap map, TmaImage im, int border, int R,
+                      int n_items, unsigned int *pair, unsigned int *err) {
+  __shared__ WarpRing rings[kWarps];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  ItemCtx cx;
+  cx.map = &map;
+  cx.ring = smem_addr(&rings[warp]);
+  cx.gstage = 0;
+  if (lane == 0) {
+    for (int i = 0; i < kSlots; ++i)
+      mbar_init(cx.ring + (uint32_t)(kSlots * kSlotBytes + 8 * i), 1u);
+    mbar_init_fence();
+  }
+  __syncwarp();
+  for (;;) {
+    unsigned int got = 0;
+    if (lane == 0) got = atomicAdd(&pair[0], 1u);
+    got = __shfl_sync(0xffffffffu, got, 0);
+    if (got >= (unsigned int)n_items) break;
+    const int item = (int)got;
+    const int band = item / im.n_seg;
+    const int seg = item - band * im.n_seg;
+    const bool full = band * 2 * R + 2 * R <= im.H;
+    const bool ok = !fast_item(im, border, seg, band, R, FMT)
+                        ? tma_item<FMT, true, false>(im, border, seg, band, R, lane, cx, err)
+                        : (full ? tma_item<FMT, false, true>(im, border, seg, band, R, lane, cx, err)
+                                : tma_item<FMT, false, false>(im, border, seg, band, R, lane, cx,
+                                                              err));
+    if (!ok) break;
+  }
+  if (lane == 0) {
+    __threadfence();  // this warp's last fetch is performed before it counts out
+    const unsigned int warps = gridDim.x * kWarps;
+    if (atomicAdd(&pair[1], 1u) == warps - 1u) {
+      atomicExch(&pair[0], 0u);
+      atomicExch(&pair[1], 0u);
+    }
+  }
+}
+
+}  // namespace tma
+}  // namespace sobel4
