@@ -1,11 +1,10 @@
 // sobel4_selftest.cu — on-device self-check of the magnitude step: the
-// library's F32 magnitudes (the scalar one of the lane-copy and direct
-// kernels, the packed-pair one of the TMA kernel) against CUDA's IEEE
+// library's F32 magnitudes (the one of the direct kernel, and the two-strip
+// one of the register-window kernels) against CUDA's IEEE
 // sqrtf((float)S), and its U8 magnitudes against the exact rule
 // min(255, round(sqrt(S))), for every S in a range (the operator's whole
 // domain is 0 .. 599,270,400).
 #include "sobel4_launch.h"
-#include "sobel4_tma.cuh"
 
 namespace sobel4 {
 
@@ -28,11 +27,11 @@ __global__ void check_magnitude_kernel(int64_t s0, int64_t s1, unsigned long lon
     // packed pair: s in the low lane, its mirror s1 - 1 - (s - s0) in the high lane
     const int32_t m = (int32_t)(s1 - 1 - (i - s0));
     float ga, gb;
-    tma::magnitude_f32x2(s, m, ga, gb);
+    magnitude_f32x2(s, m, ga, gb);
     if (__float_as_uint(ga) != __float_as_uint(want)) ++nb;
     if (__float_as_uint(gb) != __float_as_uint(sqrtf((float)m))) ++nb;
     uint32_t ua, ub;
-    tma::magnitude_u8x2(s, m, ua, ub);
+    magnitude_u8x2(s, m, ua, ub);
     if (!u8_ok(ua, s) || !u8_ok(ub, m)) ++nb;
   }
   if (nb) atomicAdd(bad, nb);

@@ -20,23 +20,19 @@
 //    at the mapped columns, and rows outside the image are gathered from the
 //    mapped rows in global memory.  This is the prefetch of Section 4.3.4, two
 //    stages (16 rows) ahead.
-//  * Per new row each column does the 1x5 horizontal passes (Eq. 6, the K_y
-//    smoothing row, the K_d+ rows of Eq. 12 and the K_d- rows of Eq. 18 with
-//    D = p3 - p1) and transposed 5-tap vertical filters (Eq. 7, Eq. 15,
-//    Eq. 19), on packed pairs.  Scaled terms are split between shift-adds
-//    (integer ALU pipe) and multiply-adds (FMA pipe) so that neither pipe
-//    limits the issue rate.
-//  * The four packed responses leave the vertical pass with the low half
-//    biased by 2^15, which makes both halves' squares one mad.hi each:
-//    with v = (lo + 2^15) + 2^16 hi, (v << 16) + 2^31 = lo * 2^16 and
-//    v & 0xffff0000 = hi * 2^16 exactly (Eq. 4 and Eq. 11: R_d = P' + M',
-//    R_dt = P' - M').  The square root runs on packed fp32 pairs.
+//  * Per new row each column runs the packed passes of sobel4_arith.cuh
+//    (Eq. 6-19), then the squares (Eq. 4) and the square root, and each lane
+//    stores four results per strip row with one vector store.
+//  * Border rules on the fast path: the copy engine's zero fill is the
+//    CONSTANT0 rule; under VALID the lane that stored a frame element
+//    overwrites it with 0 after the row loop.
 #pragma once
 
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "sobel4_arith.cuh"
 #include "sobel4_device.cuh"
 
 namespace sobel4 {
@@ -50,7 +46,6 @@ constexpr int kSlots = 3;                     // ring slots per warp
 constexpr int kStripBytes = kStageRows * kBoxW;     // 1280
 constexpr int kSlotBytes = 2 * kStripBytes;         // 2560 (strip a, then strip b)
 constexpr int kWarps = 4;                     // warps per CTA
-constexpr uint32_t kBias = 0x8000u;           // low-half bias of the tail values
 #ifndef SOBEL4_TMA_UNROLL
 #define SOBEL4_TMA_UNROLL 4
 #endif
@@ -61,22 +56,6 @@ static_assert(kUnroll == 2 || kUnroll == 4, "the stage length must be a multiple
 #define SOBEL4_TMA_MIN_CTAS 4
 #endif
 constexpr int kMinCtas = SOBEL4_TMA_MIN_CTAS;
-
-#ifndef SOBEL4_TMA_SQ
-#define SOBEL4_TMA_SQ 1  // squares: 0 = high-word multiply-adds, 1 = unpacked halves + multiply-adds
-#endif
-#ifndef SOBEL4_TMA_I2F
-#define SOBEL4_TMA_I2F 0  // S -> float: 0 = conversion instruction, 1 = exponent-field splice
-#endif
-#ifndef SOBEL4_TMA_FP2
-#define SOBEL4_TMA_FP2 0  // square root: 1 = packed fp32 pairs, 0 = scalar
-#endif
-#ifndef SOBEL4_TMA_LIN
-#define SOBEL4_TMA_LIN 0  // scaled terms: 0 = mixed, 1 = all multiply-adds, 2 = all shift-adds
-#endif
-#ifndef SOBEL4_TMA_SHF
-#define SOBEL4_TMA_SHF 1  // shift-add terms: 0 = shifts, 1 = funnel shifts (integer ALU only)
-#endif
 
 // Upper bound on one mbarrier wait (globaltimer nanoseconds) before the
 // kernel gives up, records the failure and leaves.
@@ -164,217 +143,6 @@ __device__ __forceinline__ uint32_t lds_u8(uint32_t a) {
   uint16_t v;
   asm volatile("ld.shared.u8 %0, [%1];" : "=h"(v) : "r"(a));
   return v;
-}
-
-// x << k for the shift-add terms.
-template <int K>
-__device__ __forceinline__ uint32_t shl(uint32_t x) {
-#if SOBEL4_TMA_SHF
-  return __funnelshift_l(0u, x, K);
-#else
-  return x << K;
-#endif
-}
-
-// Integer multiply-add with a constant multiplier (FMA-pipe form).
-template <uint32_t K>
-__device__ __forceinline__ uint32_t imad(uint32_t a, uint32_t b) {
-  uint32_t d;
-  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "n"(K), "r"(b));
-  return d;
-}
-
-// k*a + b for the scaled terms of the passes (k in {2, 3, 4, 6, 8}); the
-// form (multiply-add or shift-adds) is chosen per term class below.
-template <uint32_t K, int MODE>
-__device__ __forceinline__ uint32_t scaled(uint32_t a, uint32_t b) {
-  if (MODE == 1) return imad<K>(a, b);
-  if constexpr (K == 2) return shl<1>(a) + b;
-  else if constexpr (K == 4) return shl<2>(a) + b;
-  else if constexpr (K == 8) return shl<3>(a) + b;
-  else if constexpr (K == 3) return shl<1>(a) + a + b;
-  else return shl<1>(shl<1>(a) + a) + b;  // K == 6
-}
-
-__device__ __forceinline__ int32_t mulhi(int32_t a, int32_t b) {
-  int32_t d;
-  asm("mul.hi.s32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
-  return d;
-}
-__device__ __forceinline__ int32_t madhi(int32_t a, int32_t b, int32_t c) {
-  int32_t d;
-  asm("mad.hi.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-  return d;
-}
-
-// Packed fp32 pairs (register pair: low word = strip a, high word = strip b).
-__device__ __forceinline__ uint64_t pk(float a, float b) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void upk(uint64_t v, float &a, float &b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ float rsqrt_approx(float x) {
-  float y;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-// sqrtf((float)s) for two values of S (0 <= s <= 599,270,400) at once:
-// y ~ 1/sqrt(x) from the hardware approximation, g = x*y, then one Newton
-// correction whose residual g*g - x is formed exactly by a fused multiply-add
-// (Markstein, "Computation of elementary functions on the IBM RISC
-// System/6000", 1990): G = g - (y/2)(g*g - x).  x + 2^-126 feeds the
-// approximation so that x = 0 gives y finite and G = +0; for x >= 1 the sum
-// is x.  Checked exhaustively on the device against IEEE sqrtf over the whole
-// domain (sobel4_check_magnitude).
-__device__ __forceinline__ float magnitude_f32_tiny(int32_t s) {
-  const float x = (float)s;
-  const float y = rsqrt_approx(x + 0x1p-126f);
-  const float g = x * y;
-  const float hn = y * -0.5f;
-  return fmaf(fmaf(g, g, -x), hn, g);
-}
-
-__device__ __forceinline__ void magnitude_f32x2(int32_t sa, int32_t sb, float &ga, float &gb) {
-#if !SOBEL4_TMA_FP2
-  ga = magnitude_f32_tiny(sa);
-  gb = magnitude_f32_tiny(sb);
-  return;
-#endif
-  constexpr uint64_t kTiny = 0x0080000000800000ull;     // (2^-126, 2^-126)
-  constexpr uint64_t kNegHalf = 0xBF000000BF000000ull;  // (-0.5, -0.5)
-#if SOBEL4_TMA_I2F
-  // float(s) = RN(hi * 128 + lo), hi = s >> 7 < 2^23 and lo = s & 127 both exact
-  // as floats (spliced into the mantissa of 2^23); one fused multiply-add rounds.
-  constexpr uint64_t kTwo23 = 0x4B0000004B000000ull;   // (2^23, 2^23)
-  constexpr uint64_t k128 = 0x4300000043000000ull;     // (128, 128)
-  const uint64_t hb = pk(__int_as_float(0x4B000000 | (uint32_t)(sa >> 7)),
-                         __int_as_float(0x4B000000 | (uint32_t)(sb >> 7)));
-  const uint64_t lb = pk(__int_as_float(0x4B000000 | (uint32_t)(sa & 127)),
-                         __int_as_float(0x4B000000 | (uint32_t)(sb & 127)));
-  const uint64_t x = fma2(sub2(hb, kTwo23), k128, sub2(lb, kTwo23));
-#else
-  const uint64_t x = pk((float)sa, (float)sb);
-#endif
-  float ta, tb;
-  upk(add2(x, kTiny), ta, tb);
-  const uint64_t y = pk(rsqrt_approx(ta), rsqrt_approx(tb));
-  const uint64_t g = mul2(x, y);
-  const uint64_t hn = mul2(y, kNegHalf);
-  const uint64_t xn = sub2(0ull, x);
-  const uint64_t r = fma2(g, g, xn);
-  upk(fma2(r, hn, g), ga, gb);
-}
-
-// min(255, round(sqrt(S))) from the F32 magnitude (see magnitude_u8).
-__device__ __forceinline__ void magnitude_u8x2(int32_t sa, int32_t sb, uint32_t &ua,
-                                               uint32_t &ub) {
-  float ga, gb;
-  magnitude_f32x2(sa, sb, ga, gb);
-  ua = min(__float2uint_rn(ga), 255u);
-  ub = min(__float2uint_rn(gb), 255u);
-}
-
-// ---------------------------------------------------------------------------
-// One column, one new row.
-// ---------------------------------------------------------------------------
-struct Col {
-  uint32_t X1, X2, X3, hdp;   // R_x : vertical [1 4 6 4 1] over hd (transposed form)
-  uint32_t Y3, Y2n, Y1n, hsp; // R_y : vertical [-1 -2 0 2 1] over hs
-  uint32_t P3, P2n, P1n, q0p; // P'  : rows -q0', -q1', 0, q1', q0'
-  uint32_t M1, M2, M3, r0p;   // M'  : rows r0', 3hd, r2', 3hd, r0'
-};
-
-// p0..p4: packed pixels of columns x-2..x+2.  With TAIL the four packed
-// responses centred two rows above the new row are returned biased
-// (low half + 2^15): vx = R_x, vy = R_y, vd = R_d = P' + M', vt = R_dt = P' - M'.
-template <bool TAIL>
-__device__ __forceinline__ void column_step(uint32_t p0, uint32_t p1, uint32_t p2, uint32_t p3,
-                                            uint32_t p4, Col &c, uint32_t &vx, uint32_t &vy,
-                                            uint32_t &vd, uint32_t &vt) {
-  // Horizontal 1x5 passes (A = p0+p4, B = p1+p3, C = p2, E = p4-p0, D = p3-p1).
-  const uint32_t A = p0 + p4, B = p1 + p3, E = p4 - p0, D = p3 - p1;
-  // MA: terms written as multiply-adds in the mixed form; SA: as shift-adds.
-  constexpr int MA = SOBEL4_TMA_LIN == 2 ? 2 : 1;
-  constexpr int SA = SOBEL4_TMA_LIN == 1 ? 1 : 2;
-  const uint32_t hd = E + D + D;                            // [-1 -2 0 2 1]  (Eq. 6, K_x row)
-  const uint32_t hs = scaled<6, MA>(p2, scaled<4, SA>(B, A));  // [ 1  4 6 4 1]  (K_y row)
-  const uint32_t q1 = scaled<2, SA>(B + p2, hs);            // [ 1  6 8 6 1] = -K_d+ row 1 / 2 (Eq. 12)
-  const uint32_t q0 = scaled<3, MA>(A + B, p2);             // [ 3  3 1 3 3] = -K_d+ row 0 / 2
-  const uint32_t r0 = scaled<3, MA>(E, D);                  // [-3 -1 0 1 3] =  K_d- row 0 / 2 (Eq. 18)
-  const uint32_t r2 = scaled<8, SA>(D, E);                  // [-1 -8 0 8 1] =  K_d- row 2 / 2
-  // Vertical passes, transposed form.
-  if (TAIL) {
-    vx = c.X3 + hd + kBias;                       // [1 4 6 4 1] over hd (Eq. 7)
-    vy = c.Y3 + hs + kBias;                       // [-1 -2 0 2 1] over hs
-    const uint32_t pp = c.P3 + q0;                // P' (Eq. 15)
-    const uint32_t mm = c.M3 + r0;                // M' (Eq. 19)
-    vd = pp + mm + kBias;                         // R_d  (Eq. 11)
-    vt = pp - mm + kBias;                         // R_dt
-  }
-  c.X3 = scaled<4, SA>(hd, c.X2);
-  c.X2 = scaled<6, MA>(hd, c.X1);
-  c.X1 = scaled<4, SA>(hd, c.hdp);
-  c.hdp = hd;
-  c.Y3 = hs + hs - c.Y2n;
-  c.Y2n = c.Y1n;
-  c.Y1n = c.hsp + hs + hs;
-  c.hsp = hs;
-  c.P3 = q1 - c.P2n;
-  c.P2n = c.P1n;
-  c.P1n = c.q0p + q1;
-  c.q0p = q0;
-  c.M3 = scaled<3, MA>(hd, c.M2);
-  c.M2 = c.M1 + r2;
-  c.M1 = scaled<3, MA>(hd, c.r0p);
-  c.r0p = r0;
-}
-
-// Unbiased low and high halves of a biased packed value (S16X4 format).
-__device__ __forceinline__ int32_t lo_of(uint32_t v) { return (int32_t)(v & 0xFFFFu) - 0x8000; }
-__device__ __forceinline__ int32_t hi_of(uint32_t v) { return (int32_t)v >> 16; }
-
-// S of both strips from one column's biased packed responses (Eq. 4).
-__device__ __forceinline__ void squares(uint32_t vx, uint32_t vy, uint32_t vd, uint32_t vt,
-                                        int32_t &sa, int32_t &sb) {
-#if SOBEL4_TMA_SQ
-  const int32_t ax = lo_of(vx), ay = lo_of(vy), ad = lo_of(vd), at = lo_of(vt);
-  const int32_t bx = hi_of(vx), by = hi_of(vy), bd = hi_of(vd), bt = hi_of(vt);
-  sa = ax * ax + ay * ay + ad * ad + at * at;
-  sb = bx * bx + by * by + bd * bd + bt * bt;
-#else
-  const int32_t wx = (int32_t)imad<0x10000u>(vx, 0x80000000u);
-  const int32_t wy = (int32_t)imad<0x10000u>(vy, 0x80000000u);
-  const int32_t wd = (int32_t)imad<0x10000u>(vd, 0x80000000u);
-  const int32_t wt = (int32_t)imad<0x10000u>(vt, 0x80000000u);
-  sa = madhi(wx, wx, madhi(wy, wy, madhi(wd, wd, mulhi(wt, wt))));
-  const int32_t tx = (int32_t)(vx & 0xFFFF0000u), ty = (int32_t)(vy & 0xFFFF0000u);
-  const int32_t td = (int32_t)(vd & 0xFFFF0000u), tt = (int32_t)(vt & 0xFFFF0000u);
-  sb = madhi(tx, tx, madhi(ty, ty, madhi(td, td, mulhi(tt, tt))));
-#endif
 }
 
 // Packed columns c[0..7] (columns x-2 .. x+5 of both strips) from the staged
@@ -648,8 +416,7 @@ __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg
 
   Col st[kNC];
 #pragma unroll
-  for (int k = 0; k < kNC; ++k) st[k] = Col{0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u,
-                                             0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+  for (int k = 0; k < kNC; ++k) st[k] = col_zero();
   uint8_t *row_a = (uint8_t *)im.dst + (uint64_t)(uint32_t)ya * im.dp;
   uint8_t *row_b = (uint8_t *)im.dst + (uint64_t)(uint32_t)min(yb, H - 1) * im.dp;
   const uint32_t lane_off = (uint32_t)(14 + kNC * lane);  // column x-2 in a staged row
