@@ -68,9 +68,11 @@ constexpr int kMaxSide = 1 << 28;   // largest accepted height or width
 constexpr uint64_t kMaxPitch = (1ull << 31) - 1;
 
 struct BatchSlot {
-  ImageDesc *h_desc = nullptr;      // pinned host staging
+  ImageDesc *h_desc = nullptr;      // pinned host staging (lane-copy images)
   ImageDesc *d_desc = nullptr;
-  unsigned int *d_queue = nullptr;  // work-queue head of the persistent kernel
+  unsigned char *h_tma = nullptr;   // pinned host staging (TMA descriptors)
+  unsigned char *d_tma = nullptr;
+  unsigned int *d_queue = nullptr;  // work-queue heads: word 0 lane-copy, word 32 TMA
   int cap = 0;
   cudaEvent_t done = nullptr;
   bool pending = false;
@@ -285,6 +287,8 @@ void free_slot(BatchSlot &s) {
   if (s.done && s.pending) cudaEventSynchronize(s.done);
   if (s.h_desc) cudaFreeHost(s.h_desc);
   if (s.d_desc) cudaFree(s.d_desc);
+  if (s.h_tma) cudaFreeHost(s.h_tma);
+  if (s.d_tma) cudaFree(s.d_tma);
   if (s.d_queue) cudaFree(s.d_queue);
   if (s.done) cudaEventDestroy(s.done);
   s = BatchSlot();
@@ -477,34 +481,79 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
     int cap = std::max(n, 2 * slot.cap);
     if (slot.h_desc) cudaFreeHost(slot.h_desc);
     if (slot.d_desc) cudaFree(slot.d_desc);
+    if (slot.h_tma) cudaFreeHost(slot.h_tma);
+    if (slot.d_tma) cudaFree(slot.d_tma);
     slot.h_desc = nullptr;
     slot.d_desc = nullptr;
+    slot.h_tma = nullptr;
+    slot.d_tma = nullptr;
     slot.cap = 0;
+    const size_t tb = tma_batch_desc_bytes() * cap;
     e = cudaHostAlloc((void **)&slot.h_desc, sizeof(ImageDesc) * cap, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaMalloc((void **)&slot.d_desc, sizeof(ImageDesc) * cap);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&slot.h_tma, tb, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&slot.d_tma, tb);
     if (e == cudaSuccess && !slot.d_queue) e = cudaMalloc((void **)&slot.d_queue, 256);
     if (e != cudaSuccess) return cuda_fail(h, e);
     slot.cap = cap;
   }
-  int64_t total = 0;
+  // Images whose rows start on 16-byte boundaries go to the TMA-staged
+  // batched kernel, the others to the lane-copy one (two launches at most).
+  const bool tma_ok = h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced;
+  // TMA strip height: explicit option, else about two items per resident warp
+  // over the batch's TMA-eligible images (8 .. 256 rows).
+  int Rt = tma_round_R(R);
+  if (tma_ok && h->rows_per_strip <= 0) {
+    int64_t seg_rows = 0;
+    for (int32_t i = 0; i < n; ++i)
+      if (tma_eligible(imgs[i].src, imgs[i].src_pitch))
+        seg_rows += (int64_t)((imgs[i].width + 127) / 128) * imgs[i].height;
+    const int64_t warps = (int64_t)h->sm_count * 4 * kWarpsPerCta;
+    Rt = tma_round_R((int)std::min<int64_t>(256, std::max<int64_t>(8, seg_rows / (4 * warps))));
+  }
+  int n_lane = 0, n_tma = 0;
+  int64_t total = 0, total_tma = 0;
   for (int32_t i = 0; i < n; ++i) {
     const sobel4_image &m = imgs[i];
-    ImageDesc d = make_desc(m.src, m.src_pitch, m.dst, m.dst_pitch, m.height, m.width, R, bnc);
-    d.item0 = total;
-    total += (int64_t)d.n_seg * d.n_band;
-    slot.h_desc[i] = d;
+    if (tma_ok && tma_eligible(m.src, m.src_pitch)) {
+      int64_t items = 0;
+      e = tma_fill_batch_desc(slot.h_tma + tma_batch_desc_bytes() * n_tma, m.src, m.src_pitch,
+                              m.dst, m.dst_pitch, m.height, m.width, Rt, total_tma, &items);
+      if (e != cudaSuccess) return cuda_fail(h, e);
+      total_tma += items;
+      ++n_tma;
+    } else {
+      ImageDesc d = make_desc(m.src, m.src_pitch, m.dst, m.dst_pitch, m.height, m.width, R, bnc);
+      d.item0 = total;
+      total += (int64_t)d.n_seg * d.n_band;
+      slot.h_desc[n_lane++] = d;
+    }
   }
-  if (total >= (1ll << 31)) return SOBEL4_ERR_UNSUPPORTED;
-  e = cudaMemcpyAsync(slot.d_desc, slot.h_desc, sizeof(ImageDesc) * n, cudaMemcpyHostToDevice,
-                      stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(slot.d_queue, 0, sizeof(unsigned int), stream);
+  if (total >= (1ll << 31) || total_tma >= (1ll << 31)) return SOBEL4_ERR_UNSUPPORTED;
+  e = cudaMemsetAsync(slot.d_queue, 0, 256, stream);
+  if (e == cudaSuccess && n_lane)
+    e = cudaMemcpyAsync(slot.d_desc, slot.h_desc, sizeof(ImageDesc) * n_lane,
+                        cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess && n_tma)
+    e = cudaMemcpyAsync(slot.d_tma, slot.h_tma, tma_batch_desc_bytes() * n_tma,
+                        cudaMemcpyHostToDevice, stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
-  const int64_t want = (total + kWarpsPerCta - 1) / kWarpsPerCta;
-  const int grid = (int)std::min<int64_t>(want, (int64_t)h->sm_count * bctas);
-  e = launch_rg_batched(slot.d_desc, n, total, slot.d_queue, border, fmt, R, bnc,
-                        std::max(grid, 1), h->sm_count, stream);
-  if (e != cudaSuccess) return cuda_fail(h, e);
-  h->launches += 1;
+  if (n_tma) {
+    const int64_t want = (total_tma + kWarpsPerCta - 1) / kWarpsPerCta;
+    const int grid = (int)std::min<int64_t>(want, (int64_t)h->sm_count * bctas);
+    e = launch_tma_batched(slot.d_tma, n_tma, total_tma, slot.d_queue + 32, border, fmt, Rt,
+                           std::max(grid, 1), h->sm_count, h->d_err, stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    h->launches += 1;
+  }
+  if (n_lane) {
+    const int64_t want = (total + kWarpsPerCta - 1) / kWarpsPerCta;
+    const int grid = (int)std::min<int64_t>(want, (int64_t)h->sm_count * bctas);
+    e = launch_rg_batched(slot.d_desc, n_lane, total, slot.d_queue, border, fmt, R, bnc,
+                          std::max(grid, 1), h->sm_count, stream);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    h->launches += 1;
+  }
   e = cudaEventRecord(slot.done, stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
   slot.pending = true;

@@ -36,6 +36,17 @@ cudaError_t launch_tma_single(const uint8_t *src, size_t sp, void *dst, size_t d
                               int32_t W, int border, int fmt, int R, int sm_count,
                               unsigned int *pair, unsigned int *err, cudaStream_t st);
 
+// TMA-staged batches: the host fills one descriptor (tma_batch_desc_bytes
+// bytes, 64-byte aligned) per image, copies them to the device and launches
+// min(grid, resident CTAs) CTAs that pull items from *d_queue (zeroed before
+// the launch).  Every image must be tma_eligible; R as for launch_tma_single.
+size_t tma_batch_desc_bytes();
+cudaError_t tma_fill_batch_desc(void *out, const uint8_t *src, size_t sp, void *dst, size_t dp,
+                                int32_t H, int32_t W, int R, int64_t item0, int64_t *items);
+cudaError_t launch_tma_batched(const void *d_descs, int n_img, int64_t total,
+                               unsigned int *d_queue, int border, int fmt, int R, int grid,
+                               int sm_count, unsigned int *err, cudaStream_t st);
+
 // DIRECT kernel (one thread per output pixel).
 cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, cudaStream_t st);
 

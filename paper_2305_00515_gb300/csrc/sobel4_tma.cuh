@@ -78,6 +78,14 @@ struct TmaImage {
   int32_t dst_align;  // largest power of two (<= 16) dividing dst and dp
 };
 
+// One image of a TMA-staged batch: its tensor map (written by the host before
+// the launch), its geometry and its first work item in the batch.
+struct __align__(64) TmaBatchDesc {
+  CUtensorMap map;
+  TmaImage im;
+  int64_t item0;
+};
+
 // ---------------------------------------------------------------------------
 // PTX wrappers.
 // ---------------------------------------------------------------------------
@@ -110,6 +118,12 @@ __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
+}
+
+// Acquire a tensor map in global memory for the copy engine (tensor-map
+// proxy) before its first use by this thread.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap *map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
 }
 
 // Orders this thread's earlier shared-memory accesses (generic proxy) before
@@ -575,6 +589,59 @@ __global__ void __launch_bounds__(kWarps * 32, kMinCtas)
       atomicExch(&pair[0], 0u);
       atomicExch(&pair[1], 0u);
     }
+  }
+}
+
+
+// The batched kernel: persistent CTAs of 4 warps pull items (image by image,
+// band-major) from *queue (zeroed by the host before the launch); a warp
+// finds an item's image by binary search over the descriptors' first items.
+template <int FMT>
+__global__ void __launch_bounds__(kWarps * 32, kMinCtas)
+    tma_batched_kernel(const TmaBatchDesc *__restrict__ descs, int n_img, int total,
+                       unsigned int *queue, int border, int R, unsigned int *err) {
+  __shared__ WarpRing rings[kWarps];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  ItemCtx cx;
+  cx.ring = smem_addr(&rings[warp]);
+  cx.gstage = 0;
+  if (lane == 0) {
+    for (int i = 0; i < kSlots; ++i)
+      mbar_init(cx.ring + (uint32_t)(kSlots * kSlotBytes + 8 * i), 1u);
+    mbar_init_fence();
+  }
+  __syncwarp();
+  int cur = -1;
+  for (;;) {
+    unsigned int got = 0;
+    if (lane == 0) got = atomicAdd(queue, 1u);
+    got = __shfl_sync(0xffffffffu, got, 0);
+    if (got >= (unsigned int)total) break;
+    const int64_t item = (int64_t)got;
+    int lo = 0, hi = n_img - 1;  // largest image whose first item is <= item
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(&descs[mid].item0) <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    const TmaBatchDesc *d = descs + lo;
+    if (lo != cur) {
+      if (lane == 0) tensormap_acquire(&d->map);
+      cur = lo;
+    }
+    cx.map = &d->map;
+    const TmaImage im = d->im;
+    const int local = (int)(item - d->item0);
+    const int band = local / im.n_seg;
+    const int seg = local - band * im.n_seg;
+    const bool full = band * 2 * R + 2 * R <= im.H;
+    const bool ok = !fast_item(im, border, seg, band, R, FMT)
+                        ? tma_item<FMT, true, false>(im, border, seg, band, R, lane, cx, err)
+                        : (full ? tma_item<FMT, false, true>(im, border, seg, band, R, lane, cx, err)
+                                : tma_item<FMT, false, false>(im, border, seg, band, R, lane, cx,
+                                                              err));
+    if (!ok) break;
   }
 }
 

@@ -98,3 +98,34 @@ def test_back_to_back_batches_reuse_slots(h):
     for img, o in outs:
         got, guards = o.read()
         assert guards and np.array_equal(got, oracle.sobel4(img))
+
+
+def test_mixed_staging_batch_all_modes(h):
+    """Images with 16-byte aligned rows (TMA-staged batch kernel) and tight rows
+    (lane-copy batch kernel) in one call: every border rule and format."""
+    rng = np.random.default_rng(11)
+    shapes = [(int(a), int(b)) for a, b in rng.integers(3, 300, size=(14, 2))]
+    shapes += [(700, 1300), (129, 257), (37, 128), (300, 640)]
+    imgs = [synth.rects_noise(a, b, 40 + i) for i, (a, b) in enumerate(shapes)]
+    layout = []
+    for i, (H, W) in enumerate(shapes):
+        if i % 2 == 0:
+            layout.append(((-W) % 16, 0, (-W) % 4, 0))          # aligned source and output rows
+        else:
+            layout.append((int(rng.integers(0, 5)), int(rng.integers(0, 3)), 1, 4))
+    for border in ("valid", "replicate", "reflect101", "constant0"):
+        for fmt in ("f32", "u8", "s16x4"):
+            res = run_batch(h, imgs, border, fmt, layout)
+            for img, (got, guards) in zip(imgs, res):
+                assert guards, (img.shape, border, fmt)
+                assert np.array_equal(got, oracle.sobel4(img, border, fmt)), (img.shape, border, fmt)
+
+
+def test_aligned_frames_batch_like_serving(h):
+    """A batch of serving-sized frames (all rows 16-byte aligned) against the oracle."""
+    sizes = [(480, 640), (720, 1280), (1080, 1920), (480, 640), (2160, 3840), (720, 1280)]
+    imgs = [synth.rects_noise(a, b, 60 + i) for i, (a, b) in enumerate(sizes)]
+    res = run_batch(h, imgs, "valid", "f32")
+    for img, (got, guards) in zip(imgs, res):
+        assert guards
+        assert np.array_equal(got, oracle.sobel4(img, "valid", "f32", threads=NCPU)), img.shape
