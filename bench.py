@@ -179,10 +179,10 @@ def kernel_source_hash() -> str:
 
 def recorded_traffic():
     """DRAM bytes per launch of the RG kernel from the committed ncu summary
-    (profiles/rg_f32_8192_full.md, lines "kernel_source_hash: ..." and
+    (profiles/tma_f32_8192_full.md, lines "kernel_source_hash: ..." and
     "dram_bytes_per_launch: ..."), only when that capture was taken on the
     current kernel source; otherwise None."""
-    path = os.path.join(ROOT, "profiles", "rg_f32_8192_full.md")
+    path = os.path.join(ROOT, "profiles", "tma_f32_8192_full.md")
     if not os.path.exists(path):
         return None
     fields = {}

@@ -185,6 +185,17 @@ int32_t sobel4_last_cuda_error(sobel4_handle h);
  */
 sobel4_status sobel4_device_status(sobel4_handle h);
 
+/*
+ * Failure injection for tests of the bounded waits: the next single-image
+ * launch on this handle that uses TMA staging withholds the row copies of
+ * stage `stage` (0-based, 8 rows) of its first work item, so that the warp
+ * holding that item waits until its limit (2 s), records the failure and
+ * stops; sobel4_device_status then returns TIMEOUT.  The launch's output is
+ * incomplete.  No GPU fault is involved and the context stays usable.
+ * Errors: INVALID_ARG (h == NULL, stage < 0).
+ */
+sobel4_status sobel4_inject_stage_loss(sobel4_handle h, int32_t stage);
+
 /* Number of kernels this handle has launched so far (for launch accounting). */
 uint64_t sobel4_launch_count(sobel4_handle h);
 

@@ -20,8 +20,7 @@ __all__ = [
     "BORDERS", "FORMATS", "VARIANTS", "Sobel4", "Sobel4Error", "Image", "Options",
     "library_path", "load", "sobel4_create", "sobel4_destroy", "sobel4_run",
     "sobel4_run_batched", "sobel4_run_host", "sobel4_status_string", "sobel4_last_cuda_error",
-    "sobel4_device_status",
-    "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
+    "sobel4_device_status", "sobel4_inject_stage_loss", "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
     "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched", "sobel4_tune_entries",
     "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create", "sobel4_pipeline_buffers",
     "sobel4_pipeline_submit", "sobel4_pipeline_wait", "sobel4_pipeline_destroy", "Pipeline",
@@ -40,6 +39,7 @@ STATUS = {0: "SOBEL4_OK", 1: "SOBEL4_ERR_INVALID_ARG", 2: "SOBEL4_ERR_UNSUPPORTE
 EXPORTED_SYMBOLS = (
     "sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_batched", "sobel4_run_host",
     "sobel4_status_string", "sobel4_last_cuda_error", "sobel4_device_status",
+    "sobel4_inject_stage_loss",
     "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
     "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched", "sobel4_tune_entries",
     "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create", "sobel4_pipeline_buffers",
@@ -111,6 +111,7 @@ def load() -> ctypes.CDLL:
         lib.sobel4_last_cuda_error.argtypes = [vp]
         lib.sobel4_last_cuda_error.restype = i32
         lib.sobel4_device_status.argtypes = [vp]
+        lib.sobel4_inject_stage_loss.argtypes = [vp, i32]
         lib.sobel4_launch_count.argtypes = [vp]
         lib.sobel4_launch_count.restype = ctypes.c_uint64
         lib.sobel4_set_variant.argtypes = [vp, i32]
@@ -139,7 +140,7 @@ def load() -> ctypes.CDLL:
         lib.sobel4_server_destroy.argtypes = [vp]
         for name in ("sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_batched",
                      "sobel4_run_host", "sobel4_set_variant", "sobel4_check_magnitude",
-                     "sobel4_device_status",
+                     "sobel4_device_status", "sobel4_inject_stage_loss",
                      "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched",
                      "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create",
                      "sobel4_pipeline_buffers", "sobel4_pipeline_submit", "sobel4_pipeline_wait",
@@ -196,6 +197,10 @@ def sobel4_last_cuda_error(h) -> int:
 
 def sobel4_device_status(h) -> int:
     return load().sobel4_device_status(h)
+
+
+def sobel4_inject_stage_loss(h, stage: int) -> int:
+    return load().sobel4_inject_stage_loss(h, stage)
 
 
 def sobel4_launch_count(h) -> int:

@@ -124,6 +124,7 @@ struct sobel4_ctx {
   unsigned int *d_pairs = nullptr;
   uint32_t next_pair = 0;
   unsigned int *d_err = nullptr;  // bit 0: a bounded wait in a kernel ran out (inside d_pairs)
+  int lose_stage = -1;            // failure injection for the next TMA-staged launch
   cudaStream_t own_stream = nullptr;
   uint8_t *d_in = nullptr;
   size_t d_in_bytes = 0;
@@ -271,7 +272,8 @@ sobel4_status launch_one(sobel4_ctx *h, const uint8_t *src, size_t sp, void *dst
     rg_config(h, src, sp, H, W, fmt, &use_tma, &nc, &R);
     if (use_tma) {
       e = launch_tma_single(src, sp, dst, dp, H, W, border, fmt, R, h->sm_count,
-                            pair ? pair : next_pair(h), h->d_err, stream);
+                            pair ? pair : next_pair(h), h->d_err, stream, h->lose_stage);
+      h->lose_stage = -1;
     } else {
       const ImageDesc im = make_desc(src, sp, dst, dp, H, W, R, nc);
       e = launch_rg_single(im, border, fmt, R, nc, h->sm_count, pair ? pair : next_pair(h),
@@ -378,6 +380,12 @@ sobel4_status sobel4_destroy(sobel4_handle h) {
 }
 
 int32_t sobel4_last_cuda_error(sobel4_handle h) { return h ? h->last_err : 0; }
+
+sobel4_status sobel4_inject_stage_loss(sobel4_handle h, int32_t stage) {
+  if (!h || stage < 0) return SOBEL4_ERR_INVALID_ARG;
+  h->lose_stage = stage;
+  return SOBEL4_OK;
+}
 
 sobel4_status sobel4_device_status(sobel4_handle h) {
   if (!h) return SOBEL4_ERR_INVALID_ARG;

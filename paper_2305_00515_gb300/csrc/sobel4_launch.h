@@ -32,9 +32,12 @@ cudaError_t launch_rg_batched(const ImageDesc *d_descs, int n_img, int64_t total
 bool tma_eligible(const uint8_t *src, size_t sp);
 int tma_pick_R(int fmt, int sm_count, int32_t H, int32_t W);
 int tma_round_R(int R);
+// lose_stage >= 0 (failure injection for tests) withholds that stage's copy
+// for the first item, so that one warp's bounded wait runs out.
 cudaError_t launch_tma_single(const uint8_t *src, size_t sp, void *dst, size_t dp, int32_t H,
                               int32_t W, int border, int fmt, int R, int sm_count,
-                              unsigned int *pair, unsigned int *err, cudaStream_t st);
+                              unsigned int *pair, unsigned int *err, cudaStream_t st,
+                              int lose_stage = -1);
 
 // TMA-staged batches: the host fills one descriptor (tma_batch_desc_bytes
 // bytes, 64-byte aligned) per image, copies them to the device and launches

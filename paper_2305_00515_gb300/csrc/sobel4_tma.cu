@@ -109,6 +109,7 @@ tma::TmaImage make_image(const uint8_t *src, size_t sp, void *dst, size_t dp, in
   int a = 1;
   while (a < 16 && (((uintptr_t)dst | (uintptr_t)dp) % (uintptr_t)(2 * a)) == 0) a *= 2;
   im.dst_align = a;
+  im.lose_stage = -1;
   return im;
 }
 
@@ -116,12 +117,14 @@ tma::TmaImage make_image(const uint8_t *src, size_t sp, void *dst, size_t dp, in
 
 cudaError_t launch_tma_single(const uint8_t *src, size_t sp, void *dst, size_t dp, int32_t H,
                               int32_t W, int border, int fmt, int R, int sm_count,
-                              unsigned int *pair, unsigned int *err, cudaStream_t st) {
+                              unsigned int *pair, unsigned int *err, cudaStream_t st,
+                              int lose_stage) {
   if (R < tma::kUnroll || R % tma::kUnroll) return cudaErrorInvalidValue;
   CUtensorMap map;
   cudaError_t e = encode_map(&map, src, sp, H, W);
   if (e != cudaSuccess) return e;
-  const tma::TmaImage im = make_image(src, sp, dst, dp, H, W, R);
+  tma::TmaImage im = make_image(src, sp, dst, dp, H, W, R);
+  im.lose_stage = lose_stage;
   const int64_t items = (int64_t)im.n_seg * im.n_band;
   if (items >= (1ll << 31)) return cudaErrorInvalidValue;
   const int64_t cap = (int64_t)sm_count * resident_for(fmt);

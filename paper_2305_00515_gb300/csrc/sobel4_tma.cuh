@@ -76,6 +76,7 @@ struct TmaImage {
   int32_t H, W;
   int32_t n_seg, n_band;
   int32_t dst_align;  // largest power of two (<= 16) dividing dst and dp
+  int32_t lose_stage; // failure injection (tests): stage of item 0 never copied; -1 = off
 };
 
 // One image of a TMA-staged batch: its tensor map (written by the host before
@@ -340,6 +341,7 @@ __device__ __forceinline__ void zero_row4(const TmaImage &im, int y, int x) {
 // ---------------------------------------------------------------------------
 struct ItemCtx {
   const CUtensorMap *map;   // source image, box 160 x 8
+  int lose_stage;           // stage of this item whose copy is withheld (-1: none)
   uint32_t ring;            // shared address of this warp's ring
   uint32_t gstage;          // stages this warp has used so far (slot / parity counter)
 };
@@ -386,6 +388,7 @@ __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg
 
   // Producer: lane 0 copies stage j (rows 8j .. 8j+7 of both strips).
   auto issue = [&](int j) {
+    if (j == cx.lose_stage) return;  // injected loss: this stage's wait must run out
     const uint32_t g = g0 + (uint32_t)j;
     const uint32_t slot = cx.ring + (uint32_t)(kSlotBytes * (g % kSlots));
     const uint32_t bar = cx.ring + (uint32_t)(kSlots * kSlotBytes + 8 * (g % kSlots));
@@ -574,6 +577,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinCtas)
     const int item = (int)got;
     const int band = item / im.n_seg;
     const int seg = item - band * im.n_seg;
+    cx.lose_stage = item == 0 ? im.lose_stage : -1;
     const bool full = band * 2 * R + 2 * R <= im.H;
     const bool ok = !fast_item(im, border, seg, band, R, FMT)
                         ? tma_item<FMT, true, false>(im, border, seg, band, R, lane, cx, err)
@@ -631,6 +635,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinCtas)
       cur = lo;
     }
     cx.map = &d->map;
+    cx.lose_stage = -1;
     const TmaImage im = d->im;
     const int local = (int)(item - d->item0);
     const int band = local / im.n_seg;
