@@ -269,6 +269,17 @@ sobel4_status sobel4_tune_batched(sobel4_handle h, const sobel4_image *h_images,
 int32_t sobel4_tune_entries(sobel4_handle h);
 
 /*
+ * The configuration this handle uses for single images of height x width in
+ * format fmt whose rows are 16-byte aligned: *kernel = 1 for the TMA-staged
+ * kernel, 0 for the lane-copy one; its columns per lane and strip height
+ * (tuned if sobel4_tune or a loaded cache covers the shape, else the
+ * built-in rule).  Errors: INVALID_ARG.
+ */
+sobel4_status sobel4_tune_config(sobel4_handle h, int32_t height, int32_t width,
+                                 sobel4_format fmt, int32_t *kernel, int32_t *columns_per_lane,
+                                 int32_t *rows_per_strip);
+
+/*
  * Write the tuned table to `path` as JSON (written to path.tmp, then renamed
  * over path).  The file records the device name, SM count and library
  * version.  Errors: INVALID_ARG (bad path or write failure).

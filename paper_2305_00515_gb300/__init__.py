@@ -22,8 +22,9 @@ __all__ = [
     "sobel4_run_batched", "sobel4_run_host", "sobel4_status_string", "sobel4_last_cuda_error",
     "sobel4_device_status", "sobel4_inject_stage_loss", "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
     "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched", "sobel4_tune_entries",
-    "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create", "sobel4_pipeline_buffers",
-    "sobel4_pipeline_submit", "sobel4_pipeline_wait", "sobel4_pipeline_destroy", "Pipeline",
+    "sobel4_tune_config", "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create",
+    "sobel4_pipeline_buffers", "sobel4_pipeline_submit", "sobel4_pipeline_wait",
+    "sobel4_pipeline_destroy", "Pipeline",
     "sobel4_server_create", "sobel4_server_submit", "sobel4_server_wait", "sobel4_server_stats",
     "sobel4_server_destroy", "ServerOptions", "ServerStats", "EXPORTED_SYMBOLS",
 ]
@@ -42,9 +43,9 @@ EXPORTED_SYMBOLS = (
     "sobel4_inject_stage_loss",
     "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
     "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched", "sobel4_tune_entries",
-    "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create", "sobel4_pipeline_buffers",
-    "sobel4_pipeline_submit", "sobel4_pipeline_wait", "sobel4_pipeline_destroy",
-    "sobel4_server_create", "sobel4_server_submit", "sobel4_server_wait", "sobel4_server_stats",
+    "sobel4_tune_config", "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create",
+    "sobel4_pipeline_buffers", "sobel4_pipeline_submit", "sobel4_pipeline_wait",
+    "sobel4_pipeline_destroy", "sobel4_server_create", "sobel4_server_submit", "sobel4_server_wait", "sobel4_server_stats",
     "sobel4_server_destroy",
 )
 
@@ -123,6 +124,8 @@ def load() -> ctypes.CDLL:
         lib.sobel4_tune_batched.argtypes = [vp, ctypes.POINTER(Image), i32, i32, i32, fp]
         lib.sobel4_tune_entries.argtypes = [vp]
         lib.sobel4_tune_entries.restype = i32
+        ip = ctypes.POINTER(i32)
+        lib.sobel4_tune_config.argtypes = [vp, i32, i32, i32, ip, ip, ip]
         lib.sobel4_tune_save.argtypes = [vp, ctypes.c_char_p]
         lib.sobel4_tune_load.argtypes = [vp, ctypes.c_char_p]
         lib.sobel4_pipeline_create.argtypes = [vp, i32, i32, i32, i32, i32, ctypes.POINTER(vp)]
@@ -140,7 +143,7 @@ def load() -> ctypes.CDLL:
         lib.sobel4_server_destroy.argtypes = [vp]
         for name in ("sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_batched",
                      "sobel4_run_host", "sobel4_set_variant", "sobel4_check_magnitude",
-                     "sobel4_device_status", "sobel4_inject_stage_loss",
+                     "sobel4_device_status", "sobel4_inject_stage_loss", "sobel4_tune_config",
                      "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched",
                      "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create",
                      "sobel4_pipeline_buffers", "sobel4_pipeline_submit", "sobel4_pipeline_wait",
@@ -235,6 +238,14 @@ def sobel4_tune_batched(h, images, border: int, fmt: int):
 
 def sobel4_tune_entries(h) -> int:
     return load().sobel4_tune_entries(h)
+
+
+def sobel4_tune_config(h, height: int, width: int, fmt: int):
+    """(status, kernel, columns_per_lane, rows_per_strip) used for aligned images of the shape."""
+    k, nc, r = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    st = load().sobel4_tune_config(h, height, width, fmt, ctypes.byref(k), ctypes.byref(nc),
+                                   ctypes.byref(r))
+    return st, k.value, nc.value, r.value
 
 
 def sobel4_tune_save(h, path: str) -> int:

@@ -768,7 +768,7 @@ extern "C" sobel4_status sobel4_run_batched_static(const sobel4_image *imgs, int
 namespace {
 
 constexpr int kTuneWarmup = 2;
-constexpr int kTuneReps = 7;
+constexpr int kTuneReps = 9;
 
 template <class Launch>
 cudaError_t median_us(cudaStream_t st, Launch launch, float *us) {
@@ -842,9 +842,12 @@ extern "C" sobel4_status sobel4_tune(sobel4_handle h, int32_t height, int32_t wi
     if (h->rows_per_strip > 0) {
       cands.push_back(tma_round_R(h->rows_per_strip));
     } else {
+      // 8, 16, 24, ... 128 rows per strip (no taller than the image needs),
+      // plus the heuristic's choice.
+      const int top = tma_round_R(std::max(8, (height + 1) / 2));
+      for (int R = 8; R <= 128 && R <= top; R += 8) cands.push_back(R);
       const int r0 = tma_pick_R(fmt, h->sm_count, height, width);
-      for (int R : {8, 16, 32, tma_round_R(r0 * 2 / 3), r0, 2 * r0})
-        if (std::find(cands.begin(), cands.end(), R) == cands.end()) cands.push_back(R);
+      if (std::find(cands.begin(), cands.end(), r0) == cands.end()) cands.push_back(r0);
     }
     for (size_t b = 0; b < cands.size() && e == cudaSuccess; ++b) {
       const int R = cands[b];
@@ -929,6 +932,24 @@ extern "C" sobel4_status sobel4_tune_batched(sobel4_handle h, const sobel4_image
 }
 
 extern "C" int32_t sobel4_tune_entries(sobel4_handle h) { return h ? (int32_t)h->tuned.size() : 0; }
+
+extern "C" sobel4_status sobel4_tune_config(sobel4_handle h, int32_t height, int32_t width,
+                                            sobel4_format fmt, int32_t *kernel,
+                                            int32_t *columns_per_lane, int32_t *rows_per_strip) {
+  if (!h || !kernel || !columns_per_lane || !rows_per_strip || height < 1 || width < 1 ||
+      fmt < SOBEL4_OUT_F32 || fmt > SOBEL4_OUT_S16X4)
+    return SOBEL4_ERR_INVALID_ARG;
+  // The configuration a launch with 16-byte aligned rows would use.
+  static const uint8_t kAligned[16] __attribute__((aligned(16))) = {0};
+  bool use_tma = false;
+  int nc = 0, R = 0;
+  DeviceGuard g(h->device);
+  rg_config(h, kAligned, ((size_t)width + 15) & ~(size_t)15, height, width, fmt, &use_tma, &nc, &R);
+  *kernel = use_tma ? 1 : 0;
+  *columns_per_lane = nc;
+  *rows_per_strip = R;
+  return SOBEL4_OK;
+}
 
 extern "C" sobel4_status sobel4_tune_save(sobel4_handle h, const char *path) {
   if (!h || !path || !*path) return SOBEL4_ERR_INVALID_ARG;

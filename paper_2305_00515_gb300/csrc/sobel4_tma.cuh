@@ -52,6 +52,10 @@ constexpr int kWarps = 4;                     // warps per CTA
 constexpr int kUnroll = SOBEL4_TMA_UNROLL;    // row steps per main-loop trip (2 or 4)
 static_assert(kUnroll == 2 || kUnroll == 4, "the stage length must be a multiple of the unroll");
 
+#ifndef SOBEL4_TMA_CLD
+#define SOBEL4_TMA_CLD 1  // ring reads on the fast path: 1 = plain loads, 0 = volatile asm loads
+#endif
+
 #ifndef SOBEL4_TMA_MIN_CTAS
 #define SOBEL4_TMA_MIN_CTAS 4
 #endif
@@ -166,6 +170,26 @@ __device__ __forceinline__ void read_cols(uint32_t a, uint32_t c[8]) {
   const uint32_t b = a + kStripBytes;
   const uint32_t a0 = lds_u16(a), a1 = lds_u32(a + 2), a2 = lds_u16(a + 6);
   const uint32_t b0 = lds_u16(b), b1 = lds_u32(b + 2), b2 = lds_u16(b + 6);
+  c[0] = __byte_perm(a0, b0, 0x6420);
+  c[1] = __byte_perm(a0, b0, 0x7531);
+  const uint32_t t1 = __byte_perm(a1, b1, 0x5140);
+  const uint32_t t2 = __byte_perm(a1, b1, 0x7362);
+  c[2] = __byte_perm(t1, 0u, 0x4140);
+  c[3] = __byte_perm(t1, 0u, 0x4342);
+  c[4] = __byte_perm(t2, 0u, 0x4140);
+  c[5] = __byte_perm(t2, 0u, 0x4342);
+  c[6] = __byte_perm(a2, b2, 0x6420);
+  c[7] = __byte_perm(a2, b2, 0x7531);
+}
+
+// The same through a generic pointer into the ring (plain loads the compiler
+// may schedule freely after the stage's barrier wait).
+__device__ __forceinline__ void read_cols_p(const uint8_t *a, uint32_t c[8]) {
+  const uint8_t *b = a + kStripBytes;
+  const uint32_t a0 = *(const uint16_t *)a, a1 = *(const uint32_t *)(a + 2);
+  const uint32_t a2 = *(const uint16_t *)(a + 6);
+  const uint32_t b0 = *(const uint16_t *)b, b1 = *(const uint32_t *)(b + 2);
+  const uint32_t b2 = *(const uint16_t *)(b + 6);
   c[0] = __byte_perm(a0, b0, 0x6420);
   c[1] = __byte_perm(a0, b0, 0x7531);
   const uint32_t t1 = __byte_perm(a1, b1, 0x5140);
@@ -341,6 +365,7 @@ __device__ __forceinline__ void zero_row4(const TmaImage &im, int y, int x) {
 // ---------------------------------------------------------------------------
 struct ItemCtx {
   const CUtensorMap *map;   // source image, box 160 x 8
+  const uint8_t *ringp;     // the same ring as a generic pointer
   int lose_stage;           // stage of this item whose copy is withheld (-1: none)
   uint32_t ring;            // shared address of this warp's ring
   uint32_t gstage;          // stages this warp has used so far (slot / parity counter)
@@ -449,7 +474,11 @@ __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg
       else if (mapped_lane) read_cols_mapped(rd - lane_off, off, c);
       else read_cols(rd, c);
     } else {
+#if SOBEL4_TMA_CLD
+      read_cols_p(cx.ringp + (rd - cx.ring), c);
+#else
       read_cols(rd, c);
+#endif
     }
     uint32_t vx[kNC], vy[kNC], vd[kNC], vt[kNC];
     if (tail) {
@@ -562,6 +591,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinCtas)
   ItemCtx cx;
   cx.map = &map;
   cx.ring = smem_addr(&rings[warp]);
+  cx.ringp = &rings[warp].slot[0][0];
   cx.gstage = 0;
   if (lane == 0) {
     for (int i = 0; i < kSlots; ++i)
@@ -609,6 +639,7 @@ __global__ void __launch_bounds__(kWarps * 32, kMinCtas)
   const int warp = threadIdx.x >> 5;
   ItemCtx cx;
   cx.ring = smem_addr(&rings[warp]);
+  cx.ringp = &rings[warp].slot[0][0];
   cx.gstage = 0;
   if (lane == 0) {
     for (int i = 0; i < kSlots; ++i)

@@ -80,3 +80,27 @@ def test_tune_batched_keeps_results_exact(handle):
     for im, o in zip(imgs, outs):
         got, guards = o.read()
         assert guards and np.array_equal(got, oracle.sobel4(im, "reflect101", "u8"))
+
+
+def test_tune_config_reports_the_chosen_kernel(handle):
+    """The configuration query follows the tuned table; every tuned strip height
+    keeps the TMA-staged output exact."""
+    st, kind, nc, R = pkg.sobel4_tune_config(handle, 2048, 2048, 0)
+    assert st == 0 and kind == 1 and nc == 4 and R % 4 == 0 and R >= 8   # built-in rule
+    assert pkg.sobel4_tune(handle, 2048, 2048, 0, 0)[0] == 0
+    st, kind2, nc2, R2 = pkg.sobel4_tune_config(handle, 2048, 2048, 0)
+    assert st == 0 and kind2 in (0, 1) and nc2 in (2, 4) and R2 >= 4
+    img = synth.uniform(2048, 2048, 6)
+    got, guards = run_placed(torch, handle, img, "valid", "f32")
+    assert guards and np.array_equal(got, oracle.sobel4(img, "valid", "f32", threads=8))
+    for R in (8, 12, 20, 44, 128):
+        st, h = pkg.sobel4_create(0, pkg.VARIANTS["rg"], rows_per_strip=R)
+        assert st == 0
+        try:
+            assert pkg.sobel4_tune_config(h, 300, 700, 0)[3] == R
+            small = synth.rects_noise(300, 700, R)
+            out, g = run_placed(torch, h, small, "reflect101", "u8", src_pitch=704)
+            assert g and np.array_equal(out, oracle.sobel4(small, "reflect101", "u8")), R
+        finally:
+            pkg.sobel4_destroy(h)
+    assert pkg.sobel4_tune_config(handle, 0, 10, 0)[0] == 1
