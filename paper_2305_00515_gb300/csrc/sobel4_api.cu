@@ -60,7 +60,8 @@ namespace {
 #endif
 
 constexpr int kSlots = 4;           // batch descriptor slots in flight per handle
-constexpr int kQueuePairs = 256;    // single-image work-queue counter pairs per handle
+constexpr int kQueuePairs = 256;    // single-image work-queue counter blocks per handle
+constexpr int kQueueWords = 4;      // words per block: two counter pairs (a launch may need two)
 constexpr int kDefaultNC = SOBEL4_DEFAULT_NC;  // RG columns per lane unless the handle says otherwise
 constexpr int kDefaultR = 16;       // RG strip height for large images (measured best on 8192^2)
 constexpr int kBatchR = 16;         // RG strip height for batches
@@ -255,7 +256,7 @@ ImageDesc make_desc(const uint8_t *src, size_t sp, void *dst, size_t dp, int32_t
 }
 
 unsigned int *next_pair(sobel4_ctx *h) {
-  return h->d_pairs + 2 * (h->next_pair++ % (uint32_t)kQueuePairs);
+  return h->d_pairs + kQueueWords * (h->next_pair++ % (uint32_t)kQueuePairs);
 }
 
 // pair: the RG kernel's counter pair, or nullptr for the handle's next one.
@@ -274,6 +275,7 @@ sobel4_status launch_one(sobel4_ctx *h, const uint8_t *src, size_t sp, void *dst
       e = launch_tma_single(src, sp, dst, dp, H, W, border, fmt, R, h->sm_count,
                             pair ? pair : next_pair(h), h->d_err, stream, h->lose_stage);
       h->lose_stage = -1;
+      h->launches += tma_launches(H, W, border, fmt, dst, dp, R, h->sm_count) - 1;
     } else {
       const ImageDesc im = make_desc(src, sp, dst, dp, H, W, R, nc);
       e = launch_rg_single(im, border, fmt, R, nc, h->sm_count, pair ? pair : next_pair(h),
@@ -339,10 +341,10 @@ sobel4_status sobel4_create(sobel4_handle *out, int32_t device, const sobel4_opt
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
   // kQueuePairs counter pairs, then the error word (own 256-byte line).
-  const size_t pair_bytes = sizeof(unsigned int) * 2 * kQueuePairs + 256;
+  const size_t pair_bytes = sizeof(unsigned int) * kQueueWords * kQueuePairs + 256;
   if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_pairs, pair_bytes);
   if (e == cudaSuccess) e = cudaMemset(h->d_pairs, 0, pair_bytes);
-  if (e == cudaSuccess) h->d_err = h->d_pairs + 2 * kQueuePairs;
+  if (e == cudaSuccess) h->d_err = h->d_pairs + kQueueWords * kQueuePairs;
   for (int i = 0; i < kSlots && e == cudaSuccess; ++i)
     e = cudaEventCreateWithFlags(&h->slots[i].done, cudaEventDisableTiming);
   if (e != cudaSuccess) {
@@ -521,6 +523,7 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
   }
   int n_lane = 0, n_tma = 0;
   int64_t total = 0, total_tma = 0;
+  bool tma_all_fast = true;
   for (int32_t i = 0; i < n; ++i) {
     const sobel4_image &m = imgs[i];
     if (tma_ok && tma_eligible(m.src, m.src_pitch)) {
@@ -530,6 +533,7 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
       if (e != cudaSuccess) return cuda_fail(h, e);
       total_tma += items;
       ++n_tma;
+      tma_all_fast = tma_all_fast && tma_batch_all_fast(m.width, border, fmt, m.dst, m.dst_pitch);
     } else {
       ImageDesc d = make_desc(m.src, m.src_pitch, m.dst, m.dst_pitch, m.height, m.width, R, bnc);
       d.item0 = total;
@@ -550,9 +554,9 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
     const int64_t want = (total_tma + kWarpsPerCta - 1) / kWarpsPerCta;
     const int grid = (int)std::min<int64_t>(want, (int64_t)h->sm_count * bctas);
     e = launch_tma_batched(slot.d_tma, n_tma, total_tma, slot.d_queue + 32, border, fmt, Rt,
-                           std::max(grid, 1), h->sm_count, h->d_err, stream);
+                           std::max(grid, 1), h->sm_count, h->d_err, stream, tma_all_fast);
     if (e != cudaSuccess) return cuda_fail(h, e);
-    h->launches += 1;
+    h->launches += tma_all_fast ? 1 : 2;
   }
   if (n_lane) {
     const int64_t want = (total + kWarpsPerCta - 1) / kWarpsPerCta;

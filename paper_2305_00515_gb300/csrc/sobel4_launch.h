@@ -26,9 +26,11 @@ cudaError_t launch_rg_batched(const ImageDesc *d_descs, int n_img, int64_t total
 
 // TMA-staged RG kernel (sobel4_tma.cuh) over one image whose source address
 // and pitch are multiples of 16 bytes (tma_eligible).  R must equal
-// tma_round_R(R) (a multiple of the kernel's row-step unroll).  Same
-// counter-pair contract as launch_rg_single; a stage wait that runs out sets
-// bit 0 of *err and the kernel returns early.
+// tma_round_R(R) (a multiple of the kernel's row-step unroll).  `pair` points
+// to four zeroed words: when a large image has both fast-path items and
+// others, two kernels run (a lean one for the fast items, then one for the
+// rest), each with its own counter pair; both leave their pair zero.  A
+// stage wait that runs out sets bit 0 of *err and the kernel returns early.
 bool tma_eligible(const uint8_t *src, size_t sp);
 int tma_pick_R(int fmt, int sm_count, int32_t H, int32_t W);
 int tma_round_R(int R);
@@ -46,9 +48,16 @@ cudaError_t launch_tma_single(const uint8_t *src, size_t sp, void *dst, size_t d
 size_t tma_batch_desc_bytes();
 cudaError_t tma_fill_batch_desc(void *out, const uint8_t *src, size_t sp, void *dst, size_t dp,
                                 int32_t H, int32_t W, int R, int64_t item0, int64_t *items);
+// d_queue: two zeroed counters (fast-path items, then the others); all_fast
+// (every image's items on the fast path, see tma_batch_all_fast) skips the
+// second kernel.
 cudaError_t launch_tma_batched(const void *d_descs, int n_img, int64_t total,
                                unsigned int *d_queue, int border, int fmt, int R, int grid,
-                               int sm_count, unsigned int *err, cudaStream_t st);
+                               int sm_count, unsigned int *err, cudaStream_t st, bool all_fast);
+bool tma_batch_all_fast(int32_t W, int border, int fmt, const void *dst, size_t dp);
+// Kernel launches launch_tma_single makes for an image (1 or 2).
+int tma_launches(int32_t H, int32_t W, int border, int fmt, const void *dst, size_t dp, int R,
+                 int sm_count);
 
 // DIRECT kernel (one thread per output pixel).
 cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, cudaStream_t st);
@@ -63,8 +72,9 @@ struct HandleInfo {
 };
 __attribute__((visibility("hidden"))) HandleInfo handle_info(sobel4_handle h);
 __attribute__((visibility("hidden"))) void note_launches(sobel4_handle h, int64_t delta);
-// sobel4_run with a caller-owned RG counter pair (two zeroed words in device
-// memory; nullptr takes the handle's next one).  A captured graph must own its
+// sobel4_run with caller-owned RG counters (four zeroed words in device
+// memory: a launch may use two counter pairs; nullptr takes the handle's next
+// block).  A captured graph must own its
 // pair, because every replay of the graph reuses it.
 __attribute__((visibility("hidden"))) sobel4_status run_with_pair(
     sobel4_handle h, const uint8_t *d_src, size_t src_pitch, void *d_dst, size_t dst_pitch,

@@ -19,7 +19,7 @@ struct Slot {
   void *h_out = nullptr;     // pinned
   uint8_t *d_in = nullptr;
   uint8_t *d_out = nullptr;
-  unsigned int *d_pair = nullptr;  // the captured kernel's own work-queue counter pair
+  unsigned int *d_pair = nullptr;  // the captured kernels' own work-queue counters (4 words)
   cudaStream_t stream = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t done = nullptr;
@@ -37,6 +37,7 @@ struct sobel4_pipeline_ctx {
   int border = 0, fmt = 0;
   size_t in_pitch = 0, out_pitch = 0, in_bytes = 0, out_bytes = 0;
   std::vector<Slot> slots;
+  int64_t kernels_per_frame = 1;  // kernels in one slot's captured graph
 };
 
 namespace {
@@ -88,8 +89,8 @@ extern "C" sobel4_status sobel4_pipeline_create(sobel4_handle h, int32_t height,
     if (e == cudaSuccess) e = cudaHostAlloc(&s.h_out, p->out_bytes, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaMalloc((void **)&s.d_in, p->in_bytes);
     if (e == cudaSuccess) e = cudaMalloc((void **)&s.d_out, p->out_bytes);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&s.d_pair, 2 * sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMemset(s.d_pair, 0, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&s.d_pair, 4 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(s.d_pair, 0, 4 * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
     if (e != cudaSuccess) break;
@@ -124,7 +125,10 @@ extern "C" sobel4_status sobel4_pipeline_create(sobel4_handle h, int32_t height,
     return st;
   }
   // Capturing recorded the kernels into the graphs without launching them.
-  sobel4::note_launches(h, -(int64_t)(sobel4_launch_count(h) - launches0));
+  // Captures are not launches; each replay launches this many kernels.
+  const uint64_t captured = sobel4_launch_count(h) - launches0;
+  p->kernels_per_frame = p->slots.empty() ? 1 : (int64_t)(captured / p->slots.size());
+  sobel4::note_launches(h, -(int64_t)captured);
   *out = p;
   return SOBEL4_OK;
 }
@@ -149,7 +153,7 @@ extern "C" sobel4_status sobel4_pipeline_submit(sobel4_pipeline p, int32_t slot)
   if (e == cudaSuccess) e = cudaEventRecord(s.done, s.stream);
   if (e != cudaSuccess) return SOBEL4_ERR_CUDA;
   s.pending = true;
-  sobel4::note_launches(p->h, 1);
+  sobel4::note_launches(p->h, p->kernels_per_frame);
   return SOBEL4_OK;
 }
 

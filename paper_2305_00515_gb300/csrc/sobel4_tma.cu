@@ -31,11 +31,11 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-template <int FMT>
+template <int FMT, int MODE>
 int tma_resident() {
   static const int r = [] {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tma::tma_single_kernel<FMT>,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tma::tma_single_kernel<FMT, MODE>,
                                                       tma::kWarps * 32, 0) != cudaSuccess ||
         b < 1) {
       (void)cudaGetLastError();
@@ -46,11 +46,55 @@ int tma_resident() {
   return r;
 }
 
-int resident_for(int fmt) {
+template <int MODE>
+int resident_mode(int fmt) {
   switch (fmt) {
-    case kF32: return tma_resident<kF32>();
-    case kU8: return tma_resident<kU8>();
-    default: return tma_resident<kS16x4>();
+    case kF32: return tma_resident<kF32, MODE>();
+    case kU8: return tma_resident<kU8, MODE>();
+    default: return tma_resident<kS16x4, MODE>();
+  }
+}
+
+int resident_for(int fmt) { return resident_mode<tma::kFastOnly>(fmt); }
+
+// Which kernels an image needs: every item on the fast path (one lean
+// kernel), none (one general kernel), or both kinds: two launches when the
+// image is large enough to fill the GPU twice over, else one kernel that
+// carries both paths.
+enum Plan { kPlanFast, kPlanGeneral, kPlanBoth, kPlanAll };
+
+Plan plan_for(int32_t W, int border, int fmt, int dst_align, int64_t items, int sm_count) {
+  const int vec_need = fmt == kF32 ? 16 : (fmt == kU8 ? 4 : 8);
+  if (dst_align < vec_need || W < tma::kCols) return kPlanGeneral;
+  if (W % tma::kCols == 0 && (border == kValid || border == kConstant0)) return kPlanFast;
+  const int64_t warps = (int64_t)sm_count * resident_for(fmt) * tma::kWarps;
+  return items >= 2 * warps ? kPlanBoth : kPlanAll;
+}
+
+template <int FMT, int MODE>
+void launch_single_mode(const CUtensorMap &map, const tma::TmaImage &im, int border, int R,
+                        int items, int sm_count, unsigned int *pair, unsigned int *err,
+                        cudaStream_t st) {
+  const int64_t cap = (int64_t)sm_count * tma_resident<FMT, MODE>();
+  const int64_t grid = std::min<int64_t>((items + tma::kWarps - 1) / tma::kWarps, cap);
+  tma::tma_single_kernel<FMT, MODE><<<(unsigned)grid, tma::kWarps * 32, 0, st>>>(
+      map, im, border, R, items, pair, err);
+}
+
+template <int FMT>
+void launch_single_plan(Plan plan, const CUtensorMap &map, const tma::TmaImage &im, int border,
+                        int R, int items, int sm_count, unsigned int *pair, unsigned int *err,
+                        cudaStream_t st) {
+  if (plan == kPlanFast) {
+    launch_single_mode<FMT, tma::kFastOnly>(map, im, border, R, items, sm_count, pair, err, st);
+  } else if (plan == kPlanGeneral) {
+    launch_single_mode<FMT, tma::kGeneralOnly>(map, im, border, R, items, sm_count, pair, err, st);
+  } else if (plan == kPlanAll) {
+    launch_single_mode<FMT, tma::kAll>(map, im, border, R, items, sm_count, pair, err, st);
+  } else {
+    launch_single_mode<FMT, tma::kFastOnly>(map, im, border, R, items, sm_count, pair, err, st);
+    launch_single_mode<FMT, tma::kGeneralOnly>(map, im, border, R, items, sm_count, pair + 2,
+                                               err, st);
   }
 }
 
@@ -127,22 +171,29 @@ cudaError_t launch_tma_single(const uint8_t *src, size_t sp, void *dst, size_t d
   im.lose_stage = lose_stage;
   const int64_t items = (int64_t)im.n_seg * im.n_band;
   if (items >= (1ll << 31)) return cudaErrorInvalidValue;
-  const int64_t cap = (int64_t)sm_count * resident_for(fmt);
-  const int64_t grid = std::min<int64_t>((items + tma::kWarps - 1) / tma::kWarps, cap);
+  const Plan plan = plan_for(W, border, fmt, im.dst_align, items, sm_count);
   (void)cudaGetLastError();  // report this launch only, not an earlier failed call
-  const dim3 g((unsigned)grid), b(tma::kWarps * 32);
   switch (fmt) {
     case kF32:
-      tma::tma_single_kernel<kF32><<<g, b, 0, st>>>(map, im, border, R, (int)items, pair, err);
+      launch_single_plan<kF32>(plan, map, im, border, R, (int)items, sm_count, pair, err, st);
       break;
     case kU8:
-      tma::tma_single_kernel<kU8><<<g, b, 0, st>>>(map, im, border, R, (int)items, pair, err);
+      launch_single_plan<kU8>(plan, map, im, border, R, (int)items, sm_count, pair, err, st);
       break;
     default:
-      tma::tma_single_kernel<kS16x4><<<g, b, 0, st>>>(map, im, border, R, (int)items, pair, err);
+      launch_single_plan<kS16x4>(plan, map, im, border, R, (int)items, sm_count, pair, err, st);
       break;
   }
   return cudaGetLastError();
+}
+
+int tma_launches(int32_t H, int32_t W, int border, int fmt, const void *dst, size_t dp, int R,
+                 int sm_count) {
+  const tma::TmaImage im = make_image(nullptr, 0, (void *)dst, dp, H, W, R);
+  return plan_for(W, border, fmt, im.dst_align, (int64_t)im.n_seg * im.n_band, sm_count) ==
+                 kPlanBoth
+             ? 2
+             : 1;
 }
 
 size_t tma_batch_desc_bytes() { return sizeof(tma::TmaBatchDesc); }
@@ -160,26 +211,44 @@ cudaError_t tma_fill_batch_desc(void *out, const uint8_t *src, size_t sp, void *
 
 cudaError_t launch_tma_batched(const void *d_descs, int n_img, int64_t total,
                                unsigned int *d_queue, int border, int fmt, int R, int grid,
-                               int sm_count, unsigned int *err, cudaStream_t st) {
+                               int sm_count, unsigned int *err, cudaStream_t st, bool all_fast) {
   if (R < tma::kUnroll || R % tma::kUnroll || total >= (1ll << 31)) return cudaErrorInvalidValue;
-  const int64_t cap = (int64_t)sm_count * resident_for(fmt);
-  grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, cap));
   const tma::TmaBatchDesc *d = (const tma::TmaBatchDesc *)d_descs;
   (void)cudaGetLastError();  // report this launch only, not an earlier failed call
-  const dim3 g((unsigned)grid), b(tma::kWarps * 32);
+  auto go = [&](auto kernel, int res, unsigned int *queue) {
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(grid, (int64_t)sm_count * res));
+    kernel<<<g, tma::kWarps * 32, 0, st>>>(d, n_img, (int)total, queue, border, R, err);
+  };
   switch (fmt) {
     case kF32:
-      tma::tma_batched_kernel<kF32><<<g, b, 0, st>>>(d, n_img, (int)total, d_queue, border, R, err);
+      go(tma::tma_batched_kernel<kF32, tma::kFastOnly>, tma_resident<kF32, tma::kFastOnly>(),
+         d_queue);
+      if (!all_fast)
+        go(tma::tma_batched_kernel<kF32, tma::kGeneralOnly>,
+           tma_resident<kF32, tma::kGeneralOnly>(), d_queue + 1);
       break;
     case kU8:
-      tma::tma_batched_kernel<kU8><<<g, b, 0, st>>>(d, n_img, (int)total, d_queue, border, R, err);
+      go(tma::tma_batched_kernel<kU8, tma::kFastOnly>, tma_resident<kU8, tma::kFastOnly>(),
+         d_queue);
+      if (!all_fast)
+        go(tma::tma_batched_kernel<kU8, tma::kGeneralOnly>,
+           tma_resident<kU8, tma::kGeneralOnly>(), d_queue + 1);
       break;
     default:
-      tma::tma_batched_kernel<kS16x4><<<g, b, 0, st>>>(d, n_img, (int)total, d_queue, border, R,
-                                                      err);
+      go(tma::tma_batched_kernel<kS16x4, tma::kFastOnly>,
+         tma_resident<kS16x4, tma::kFastOnly>(), d_queue);
+      if (!all_fast)
+        go(tma::tma_batched_kernel<kS16x4, tma::kGeneralOnly>,
+           tma_resident<kS16x4, tma::kGeneralOnly>(), d_queue + 1);
       break;
   }
   return cudaGetLastError();
+}
+
+bool tma_batch_all_fast(int32_t W, int border, int fmt, const void *dst, size_t dp) {
+  int a = 1;
+  while (a < 16 && (((uintptr_t)dst | (uintptr_t)dp) % (uintptr_t)(2 * a)) == 0) a *= 2;
+  return plan_for(W, border, fmt, a, 0, 1) == kPlanFast;
 }
 
 }  // namespace sobel4

@@ -59,7 +59,14 @@ static_assert(kUnroll == 2 || kUnroll == 4, "the stage length must be a multiple
 #ifndef SOBEL4_TMA_MIN_CTAS
 #define SOBEL4_TMA_MIN_CTAS 4
 #endif
-constexpr int kMinCtas = SOBEL4_TMA_MIN_CTAS;
+#ifndef SOBEL4_TMA_FAST_CTAS
+#define SOBEL4_TMA_FAST_CTAS 4
+#endif
+// Kernel modes: every item, only fast-path items, only the other items.  A
+// kernel without the general path needs fewer registers and no spills.
+enum Mode : int { kAll = 0, kFastOnly = 1, kGeneralOnly = 2 };
+template <int MODE>
+constexpr int min_ctas() { return MODE == kFastOnly ? SOBEL4_TMA_FAST_CTAS : SOBEL4_TMA_MIN_CTAS; }
 
 // Upper bound on one mbarrier wait (globaltimer nanoseconds) before the
 // kernel gives up, records the failure and leaves.
@@ -579,10 +586,25 @@ __device__ __forceinline__ bool fast_item(const TmaImage &im, int border, int se
   return x0 >= 2 && x0 + kCols + 2 <= im.W && ya >= 2 && ya + 2 * R + 2 <= im.H;
 }
 
+// Runs one item through the variant its geometry needs; a kernel that runs
+// only fast items (or only the others) carries only that code.
+template <int FMT, int MODE>
+__device__ __forceinline__ bool run_item(const TmaImage &im, int border, int seg, int band, int R,
+                                         int lane, ItemCtx &cx, unsigned int *err, bool fast) {
+  if (MODE != kFastOnly && !fast)
+    return tma_item<FMT, true, false>(im, border, seg, band, R, lane, cx, err);
+  if constexpr (MODE != kGeneralOnly) {
+    if (band * 2 * R + 2 * R <= im.H)
+      return tma_item<FMT, false, true>(im, border, seg, band, R, lane, cx, err);
+    return tma_item<FMT, false, false>(im, border, seg, band, R, lane, cx, err);
+  }
+  return false;
+}
+
 // The single-image kernel: persistent CTAs of 4 warps; each warp pulls items
 // (band-major) from the counter pair[0]; the last warp out resets the pair.
-template <int FMT>
-__global__ void __launch_bounds__(kWarps * 32, kMinCtas)
+template <int FMT, int MODE>
+__global__ void __launch_bounds__(kWarps * 32, min_ctas<MODE>())
     tma_single_kernel(const __grid_constant__ CUtensorMap map, TmaImage im, int border, int R,
                       int n_items, unsigned int *pair, unsigned int *err) {
   __shared__ WarpRing rings[kWarps];
@@ -608,13 +630,9 @@ __global__ void __launch_bounds__(kWarps * 32, kMinCtas)
     const int band = item / im.n_seg;
     const int seg = item - band * im.n_seg;
     cx.lose_stage = item == 0 ? im.lose_stage : -1;
-    const bool full = band * 2 * R + 2 * R <= im.H;
-    const bool ok = !fast_item(im, border, seg, band, R, FMT)
-                        ? tma_item<FMT, true, false>(im, border, seg, band, R, lane, cx, err)
-                        : (full ? tma_item<FMT, false, true>(im, border, seg, band, R, lane, cx, err)
-                                : tma_item<FMT, false, false>(im, border, seg, band, R, lane, cx,
-                                                              err));
-    if (!ok) break;
+    const bool fast = fast_item(im, border, seg, band, R, FMT);
+    if ((MODE == kFastOnly && !fast) || (MODE == kGeneralOnly && fast)) continue;
+    if (!run_item<FMT, MODE>(im, border, seg, band, R, lane, cx, err, fast)) break;
   }
   if (lane == 0) {
     __threadfence();  // this warp's last fetch is performed before it counts out
@@ -630,8 +648,8 @@ __global__ void __launch_bounds__(kWarps * 32, kMinCtas)
 // The batched kernel: persistent CTAs of 4 warps pull items (image by image,
 // band-major) from *queue (zeroed by the host before the launch); a warp
 // finds an item's image by binary search over the descriptors' first items.
-template <int FMT>
-__global__ void __launch_bounds__(kWarps * 32, kMinCtas)
+template <int FMT, int MODE>
+__global__ void __launch_bounds__(kWarps * 32, min_ctas<MODE>())
     tma_batched_kernel(const TmaBatchDesc *__restrict__ descs, int n_img, int total,
                        unsigned int *queue, int border, int R, unsigned int *err) {
   __shared__ WarpRing rings[kWarps];
@@ -661,23 +679,19 @@ __global__ void __launch_bounds__(kWarps * 32, kMinCtas)
       else hi = mid - 1;
     }
     const TmaBatchDesc *d = descs + lo;
+    const TmaImage im = d->im;
+    const int local = (int)(item - d->item0);
+    const int band = local / im.n_seg;
+    const int seg = local - band * im.n_seg;
+    const bool fast = fast_item(im, border, seg, band, R, FMT);
+    if ((MODE == kFastOnly && !fast) || (MODE == kGeneralOnly && fast)) continue;
     if (lo != cur) {
       if (lane == 0) tensormap_acquire(&d->map);
       cur = lo;
     }
     cx.map = &d->map;
     cx.lose_stage = -1;
-    const TmaImage im = d->im;
-    const int local = (int)(item - d->item0);
-    const int band = local / im.n_seg;
-    const int seg = local - band * im.n_seg;
-    const bool full = band * 2 * R + 2 * R <= im.H;
-    const bool ok = !fast_item(im, border, seg, band, R, FMT)
-                        ? tma_item<FMT, true, false>(im, border, seg, band, R, lane, cx, err)
-                        : (full ? tma_item<FMT, false, true>(im, border, seg, band, R, lane, cx, err)
-                                : tma_item<FMT, false, false>(im, border, seg, band, R, lane, cx,
-                                                              err));
-    if (!ok) break;
+    if (!run_item<FMT, MODE>(im, border, seg, band, R, lane, cx, err, fast)) break;
   }
 }
 
