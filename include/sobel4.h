@@ -83,11 +83,13 @@ typedef enum { SOBEL4_OUT_F32 = 0, SOBEL4_OUT_U8 = 1, SOBEL4_OUT_S16X4 = 2 } sob
  * global memory (the paper's "GM" kernel, Section 5.2).  RG is the
  * register-window kernel (Section 4.3): threads across columns, rows walked
  * sequentially, the x/y masks factored into 1x5 passes (Eq. 6-7), the
- * diagonals through K_d+ / K_d- (Eq. 10-19), next rows prefetched.  When the
- * source address and pitch are multiples of 16 bytes, RG stages rows with
- * 2-D tensor copies (TMA) into a per-warp shared-memory ring; otherwise each
- * lane copies 16-byte granules (cp.async).  RG_LANECOPY forces the second
- * staging for every image (both give identical results).
+ * diagonals through K_d+ / K_d- (Eq. 10-19), next rows prefetched.  RG
+ * stages rows with asynchronous copies into a per-warp shared-memory ring:
+ * 2-D tensor copies (TMA) when the source address and pitch are multiples of
+ * 16 bytes, else 1-D bulk copies of each row's 16-byte granules; destinations
+ * that are not vector-aligned take lane-shifted aligned stores.
+ * RG_LANECOPY selects the older staging in which each lane copies granules
+ * itself (cp.async); all variants give identical results.
  */
 typedef enum {
   SOBEL4_VARIANT_AUTO = 0,
@@ -269,9 +271,10 @@ sobel4_status sobel4_tune_batched(sobel4_handle h, const sobel4_image *h_images,
 int32_t sobel4_tune_entries(sobel4_handle h);
 
 /*
- * The configuration this handle uses for single images of height x width in
- * format fmt whose rows are 16-byte aligned: *kernel = 1 for the TMA-staged
- * kernel, 0 for the lane-copy one; its columns per lane and strip height
+ * The configuration this handle uses for single VALID images of height x
+ * width in format fmt whose source and destination rows are 16-byte aligned:
+ * *kernel = 1 for the TMA-staged kernel, 0 for the lane-copy one; its columns
+ * per lane and strip height
  * (tuned if sobel4_tune or a loaded cache covers the shape, else the
  * built-in rule).  Errors: INVALID_ARG.
  */

@@ -61,7 +61,7 @@ namespace {
 
 constexpr int kSlots = 4;           // batch descriptor slots in flight per handle
 constexpr int kQueuePairs = 256;    // single-image work-queue counter blocks per handle
-constexpr int kQueueWords = 4;      // words per block: two counter pairs (a launch may need two)
+constexpr int kQueueWords = 4;      // words per block: one counter pair, padded to 16 bytes
 constexpr int kDefaultNC = SOBEL4_DEFAULT_NC;  // RG columns per lane unless the handle says otherwise
 constexpr int kDefaultR = 16;       // RG strip height for large images (measured best on 8192^2)
 constexpr int kBatchR = 16;         // RG strip height for batches
@@ -208,19 +208,19 @@ const TuneEntry *find_tuned(const sobel4_ctx *h, int kind, int32_t H, int32_t W,
   return nullptr;
 }
 
-// The RG configuration for one image: which staging (TMA needs a 16-byte
-// aligned source and pitch), columns per lane and strip height.  Explicit
-// options first, then the tuned table, then the heuristics.
-void rg_config(const sobel4_ctx *h, const uint8_t *src, size_t sp, int32_t H, int32_t W, int fmt,
-               bool *use_tma, int *nc, int *R) {
+// The RG configuration for one image: which kernel family (the TMA family
+// stages any source: tensor copies for 16-byte aligned rows, bulk row copies
+// otherwise), columns per lane and strip height.  Explicit options first,
+// then the tuned table, then the heuristics.
+void rg_config(const sobel4_ctx *h, const uint8_t *src, size_t sp, const void *dst, size_t dp,
+               int32_t H, int32_t W, int border, int fmt, bool *use_tma, int *nc, int *R) {
   const TuneEntry *t = find_tuned(h, 0, H, W, fmt);
-  *use_tma = h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced && tma_eligible(src, sp) &&
-             !(t && t->kernel == 0);
+  *use_tma = h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced && !(t && t->kernel == 0);
   if (*use_tma) {
     *nc = 4;
     if (h->rows_per_strip > 0) *R = tma_round_R(h->rows_per_strip);
     else if (t && t->kernel == 1) *R = t->R;
-    else *R = tma_pick_R(fmt, h->sm_count, H, W);
+    else *R = tma_pick_R(fmt, h->sm_count, H, W, tma_all_fast(W, border, fmt, src, sp, dst, dp));
     return;
   }
   const bool lane_entry = t && t->kernel == 0;
@@ -270,12 +270,11 @@ sobel4_status launch_one(sobel4_ctx *h, const uint8_t *src, size_t sp, void *dst
   } else {
     int nc, R;
     bool use_tma;
-    rg_config(h, src, sp, H, W, fmt, &use_tma, &nc, &R);
+    rg_config(h, src, sp, dst, dp, H, W, border, fmt, &use_tma, &nc, &R);
     if (use_tma) {
       e = launch_tma_single(src, sp, dst, dp, H, W, border, fmt, R, h->sm_count,
                             pair ? pair : next_pair(h), h->d_err, stream, h->lose_stage);
       h->lose_stage = -1;
-      h->launches += tma_launches(H, W, border, fmt, dst, dp, R, h->sm_count) - 1;
     } else {
       const ImageDesc im = make_desc(src, sp, dst, dp, H, W, R, nc);
       e = launch_rg_single(im, border, fmt, R, nc, h->sm_count, pair ? pair : next_pair(h),
@@ -475,10 +474,12 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
     }
     return SOBEL4_OK;
   }
+  // The tuned entry for batches names the kernel family and its parameters.
   const TuneEntry *bt = find_tuned(h, 1, 0, 0, fmt);
-  const int R = h->rows_per_strip > 0 ? h->rows_per_strip : (bt ? bt->R : kBatchR);
-  const int bnc = h->nc_forced ? h->nc : (bt ? bt->nc : h->nc);
-  const int bctas = bt ? bt->ctas : h->ctas_per_sm;
+  const TuneEntry *bl = bt && bt->kernel == 0 ? bt : nullptr;
+  const int R = h->rows_per_strip > 0 ? h->rows_per_strip : (bl ? bl->R : kBatchR);
+  const int bnc = h->nc_forced ? h->nc : (bl ? bl->nc : h->nc);
+  const int bctas = bl ? bl->ctas : h->ctas_per_sm;
   BatchSlot &slot = h->slots[h->next_slot];
   h->next_slot = (h->next_slot + 1) % kSlots;
   cudaError_t e = cudaSuccess;
@@ -507,41 +508,55 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
     if (e != cudaSuccess) return cuda_fail(h, e);
     slot.cap = cap;
   }
-  // Images whose rows start on 16-byte boundaries go to the TMA-staged
-  // batched kernel, the others to the lane-copy one (two launches at most).
-  const bool tma_ok = h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced;
-  // TMA strip height: explicit option, else about two items per resident warp
-  // over the batch's TMA-eligible images (8 .. 256 rows).
+  // Every image goes to the TMA-family batched kernel unless the handle asks
+  // for lane copies: 16-byte aligned sources in one launch group (tensor
+  // copies), the others in a second (bulk row copies).
+  const bool tma_ok = h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced && !bl;
+  // TMA strip height: explicit option, else the tuned one, else about 64
+  // items per resident warp over the batch (8 .. 64 rows): many short items
+  // balance a ragged batch better than fewer tall ones.
   int Rt = tma_round_R(R);
   if (tma_ok && h->rows_per_strip <= 0) {
-    int64_t seg_rows = 0;
-    for (int32_t i = 0; i < n; ++i)
-      if (tma_eligible(imgs[i].src, imgs[i].src_pitch))
-        seg_rows += (int64_t)((imgs[i].width + 127) / 128) * imgs[i].height;
-    const int64_t warps = (int64_t)h->sm_count * 4 * kWarpsPerCta;
-    Rt = tma_round_R((int)std::min<int64_t>(256, std::max<int64_t>(8, seg_rows / (4 * warps))));
-  }
-  int n_lane = 0, n_tma = 0;
-  int64_t total = 0, total_tma = 0;
-  bool tma_all_fast = true;
-  for (int32_t i = 0; i < n; ++i) {
-    const sobel4_image &m = imgs[i];
-    if (tma_ok && tma_eligible(m.src, m.src_pitch)) {
-      int64_t items = 0;
-      e = tma_fill_batch_desc(slot.h_tma + tma_batch_desc_bytes() * n_tma, m.src, m.src_pitch,
-                              m.dst, m.dst_pitch, m.height, m.width, Rt, total_tma, &items);
-      if (e != cudaSuccess) return cuda_fail(h, e);
-      total_tma += items;
-      ++n_tma;
-      tma_all_fast = tma_all_fast && tma_batch_all_fast(m.width, border, fmt, m.dst, m.dst_pitch);
+    if (bt && bt->kernel == 1) {
+      Rt = bt->R;
     } else {
+      int64_t seg_rows = 0;
+      for (int32_t i = 0; i < n; ++i)
+        seg_rows += (int64_t)((imgs[i].width + 127) / 128) * imgs[i].height;
+      const int64_t warps = (int64_t)h->sm_count * 4 * kWarpsPerCta;
+      Rt = tma_round_R((int)std::min<int64_t>(64, std::max<int64_t>(8, seg_rows / (128 * warps))));
+    }
+  }
+  int n_lane = 0, n_tma = 0, n_grp[2] = {0, 0};
+  int64_t total = 0, total_grp[2] = {0, 0};
+  bool all_fast[2] = {true, true};
+  if (tma_ok) {
+    for (int g = 0; g < 2; ++g) {  // g = 0: tensor staging, 1: bulk staging
+      for (int32_t i = 0; i < n; ++i) {
+        const sobel4_image &m = imgs[i];
+        if (tma_eligible(m.src, m.src_pitch) != (g == 0)) continue;
+        int64_t items = 0;
+        e = tma_fill_batch_desc(slot.h_tma + tma_batch_desc_bytes() * n_tma, m.src, m.src_pitch,
+                                m.dst, m.dst_pitch, m.height, m.width, Rt, total_grp[g], &items);
+        if (e != cudaSuccess) return cuda_fail(h, e);
+        total_grp[g] += items;
+        ++n_grp[g];
+        ++n_tma;
+        all_fast[g] = all_fast[g] && tma_all_fast(m.width, border, fmt, m.src, m.src_pitch,
+                                                        m.dst, m.dst_pitch);
+      }
+    }
+  } else {
+    for (int32_t i = 0; i < n; ++i) {
+      const sobel4_image &m = imgs[i];
       ImageDesc d = make_desc(m.src, m.src_pitch, m.dst, m.dst_pitch, m.height, m.width, R, bnc);
       d.item0 = total;
       total += (int64_t)d.n_seg * d.n_band;
       slot.h_desc[n_lane++] = d;
     }
   }
-  if (total >= (1ll << 31) || total_tma >= (1ll << 31)) return SOBEL4_ERR_UNSUPPORTED;
+  if (total >= (1ll << 31) || total_grp[0] >= (1ll << 31) || total_grp[1] >= (1ll << 31))
+    return SOBEL4_ERR_UNSUPPORTED;
   e = cudaMemsetAsync(slot.d_queue, 0, 256, stream);
   if (e == cudaSuccess && n_lane)
     e = cudaMemcpyAsync(slot.d_desc, slot.h_desc, sizeof(ImageDesc) * n_lane,
@@ -550,13 +565,16 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
     e = cudaMemcpyAsync(slot.d_tma, slot.h_tma, tma_batch_desc_bytes() * n_tma,
                         cudaMemcpyHostToDevice, stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
-  if (n_tma) {
-    const int64_t want = (total_tma + kWarpsPerCta - 1) / kWarpsPerCta;
-    const int grid = (int)std::min<int64_t>(want, (int64_t)h->sm_count * bctas);
-    e = launch_tma_batched(slot.d_tma, n_tma, total_tma, slot.d_queue + 32, border, fmt, Rt,
-                           std::max(grid, 1), h->sm_count, h->d_err, stream, tma_all_fast);
+  for (int g = 0; g < 2; ++g) {
+    if (!n_grp[g]) continue;
+    const int64_t want = (total_grp[g] + kWarpsPerCta - 1) / kWarpsPerCta;
+    const int grid = (int)std::min<int64_t>(want, 1 << 30);  // capped at residency below
+    const size_t off = g == 0 ? 0 : tma_batch_desc_bytes() * n_grp[0];
+    e = launch_tma_batched(slot.d_tma + off, n_grp[g], total_grp[g], slot.d_queue + 32 + 8 * g,
+                           border, fmt, Rt, std::max(grid, 1), h->sm_count, h->d_err, stream,
+                           all_fast[g], g == 1);
     if (e != cudaSuccess) return cuda_fail(h, e);
-    h->launches += tma_all_fast ? 1 : 2;
+    h->launches += 1;
   }
   if (n_lane) {
     const int64_t want = (total + kWarpsPerCta - 1) / kWarpsPerCta;
@@ -810,8 +828,8 @@ void upsert(sobel4_ctx *h, const TuneEntry &t) {
 bool valid_entry(const TuneEntry &t) {
   return (t.kind == 0 || t.kind == 1) && t.hb >= 0 && t.hb <= 31 && t.wb >= 0 && t.wb <= 31 &&
          t.fmt >= 0 && t.fmt <= 2 && (t.nc == 2 || t.nc == 4) && t.R >= 1 && t.R <= (1 << 20) &&
-         t.ctas >= 1 && t.ctas <= 64 && (t.kernel == 0 || (t.kernel == 1 && t.kind == 0 &&
-                                                           t.nc == 4 && t.R == tma_round_R(t.R)));
+         t.ctas >= 1 && t.ctas <= 64 && (t.kernel == 0 || (t.kernel == 1 && t.nc == 4 &&
+                                                           t.R == tma_round_R(t.R)));
 }
 
 }  // namespace
@@ -850,7 +868,8 @@ extern "C" sobel4_status sobel4_tune(sobel4_handle h, int32_t height, int32_t wi
       // plus the heuristic's choice.
       const int top = tma_round_R(std::max(8, (height + 1) / 2));
       for (int R = 8; R <= 128 && R <= top; R += 8) cands.push_back(R);
-      const int r0 = tma_pick_R(fmt, h->sm_count, height, width);
+      const int r0 = tma_pick_R(fmt, h->sm_count, height, width,
+                                tma_all_fast(width, border, fmt, src, sp, dst, dp));
       if (std::find(cands.begin(), cands.end(), r0) == cands.end()) cands.push_back(r0);
     }
     for (size_t b = 0; b < cands.size() && e == cudaSuccess; ++b) {
@@ -902,29 +921,40 @@ extern "C" sobel4_status sobel4_tune_batched(sobel4_handle h, const sobel4_image
   const int ctas[3] = {2, 4, 6};
   cudaError_t e = cudaSuccess;
   sobel4_status st = SOBEL4_OK;
+  auto try_entry = [&](const TuneEntry &cand) {
+    h->tuned = saved;
+    upsert(h, cand);
+    float us = 0.f;
+    e = median_us(h->own_stream, [&]() {
+      st = sobel4_run_batched(h, imgs, n, border, fmt, h->own_stream);
+      return st == SOBEL4_OK ? cudaSuccess : cudaErrorUnknown;
+    }, &us);
+    if (st != SOBEL4_OK) return;
+    if (e != cudaSuccess) {
+      st = cuda_fail(h, e);
+      return;
+    }
+    if (!have || us < best.us) {
+      best = cand;
+      best.us = us;
+      have = true;
+    }
+  };
+  // TMA-family kernel (any alignment): strip heights 8 .. 64.
+  if (h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced) {
+    const int Rt[6] = {8, 16, 24, 32, 48, 64};
+    for (int b = 0; b < 6 && st == SOBEL4_OK; ++b) {
+      if (h->rows_per_strip > 0 && Rt[b] != tma_round_R(h->rows_per_strip)) continue;
+      try_entry({1, 0, 0, (int)fmt, 4, Rt[b], h->ctas_per_sm, 0, 1});
+    }
+  }
+  // Lane-copy kernel: columns per lane, strip height, CTAs per SM.
   for (int a = 0; a < 2 && st == SOBEL4_OK; ++a) {
     if (h->nc_forced && ncs[a] != h->nc) continue;
     for (int b = 0; b < 3 && st == SOBEL4_OK; ++b) {
       if (h->rows_per_strip > 0 && Rs[b] != h->rows_per_strip) continue;
       for (int c = 0; c < 3 && st == SOBEL4_OK; ++c) {
-        const TuneEntry cand = {1, 0, 0, (int)fmt, ncs[a], Rs[b], ctas[c], 0, 0};
-        h->tuned = saved;
-        upsert(h, cand);
-        float us = 0.f;
-        e = median_us(h->own_stream, [&]() {
-          st = sobel4_run_batched(h, imgs, n, border, fmt, h->own_stream);
-          return st == SOBEL4_OK ? cudaSuccess : cudaErrorUnknown;
-        }, &us);
-        if (st != SOBEL4_OK) break;
-        if (e != cudaSuccess) {
-          st = cuda_fail(h, e);
-          break;
-        }
-        if (!have || us < best.us) {
-          best = cand;
-          best.us = us;
-          have = true;
-        }
+        try_entry({1, 0, 0, (int)fmt, ncs[a], Rs[b], ctas[c], 0, 0});
       }
     }
   }
@@ -943,12 +973,14 @@ extern "C" sobel4_status sobel4_tune_config(sobel4_handle h, int32_t height, int
   if (!h || !kernel || !columns_per_lane || !rows_per_strip || height < 1 || width < 1 ||
       fmt < SOBEL4_OUT_F32 || fmt > SOBEL4_OUT_S16X4)
     return SOBEL4_ERR_INVALID_ARG;
-  // The configuration a launch with 16-byte aligned rows would use.
+  // The configuration a VALID launch with 16-byte aligned rows would use.
   static const uint8_t kAligned[16] __attribute__((aligned(16))) = {0};
   bool use_tma = false;
   int nc = 0, R = 0;
   DeviceGuard g(h->device);
-  rg_config(h, kAligned, ((size_t)width + 15) & ~(size_t)15, height, width, fmt, &use_tma, &nc, &R);
+  rg_config(h, kAligned, ((size_t)width + 15) & ~(size_t)15, kAligned,
+            ((size_t)width * elem_size(fmt) + 15) & ~(size_t)15, height, width, SOBEL4_BORDER_VALID,
+            fmt, &use_tma, &nc, &R);
   *kernel = use_tma ? 1 : 0;
   *columns_per_lane = nc;
   *rows_per_strip = R;

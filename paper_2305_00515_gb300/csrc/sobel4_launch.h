@@ -24,15 +24,16 @@ cudaError_t launch_rg_batched(const ImageDesc *d_descs, int n_img, int64_t total
                               unsigned int *d_queue, int border, int fmt, int R, int nc,
                               int grid, int sm_count, cudaStream_t st);
 
-// TMA-staged RG kernel (sobel4_tma.cuh) over one image whose source address
-// and pitch are multiples of 16 bytes (tma_eligible).  R must equal
-// tma_round_R(R) (a multiple of the kernel's row-step unroll).  `pair` points
-// to four zeroed words: when a large image has both fast-path items and
-// others, two kernels run (a lean one for the fast items, then one for the
-// rest), each with its own counter pair; both leave their pair zero.  A
-// stage wait that runs out sets bit 0 of *err and the kernel returns early.
+// TMA-family RG kernel (sobel4_tma.cuh) over one image of any alignment:
+// sources whose address and pitch are multiples of 16 bytes (tma_eligible)
+// are staged with 2-D tensor copies, others with 1-D bulk copies of each
+// row's 16-byte granules.  R must equal tma_round_R(R) (a multiple of the
+// kernel's row-step unroll).  One kernel runs (a lean one when every item
+// takes the fast path); `pair` points to two zeroed counter words, which the
+// kernel leaves zero.  A stage wait that runs out sets bit 0 of *err and the
+// kernel returns early.
 bool tma_eligible(const uint8_t *src, size_t sp);
-int tma_pick_R(int fmt, int sm_count, int32_t H, int32_t W);
+int tma_pick_R(int fmt, int sm_count, int32_t H, int32_t W, bool all_fast);
 int tma_round_R(int R);
 // lose_stage >= 0 (failure injection for tests) withholds that stage's copy
 // for the first item, so that one warp's bounded wait runs out.
@@ -41,24 +42,22 @@ cudaError_t launch_tma_single(const uint8_t *src, size_t sp, void *dst, size_t d
                               unsigned int *pair, unsigned int *err, cudaStream_t st,
                               int lose_stage = -1);
 
-// TMA-staged batches: the host fills one descriptor (tma_batch_desc_bytes
+// TMA-family batches: the host fills one descriptor (tma_batch_desc_bytes
 // bytes, 64-byte aligned) per image, copies them to the device and launches
 // min(grid, resident CTAs) CTAs that pull items from *d_queue (zeroed before
-// the launch).  Every image must be tma_eligible; R as for launch_tma_single.
+// the launch).  One launch takes images of one staging: all tma_eligible
+// (bulk = false) or all not (bulk = true); R as for launch_tma_single.
 size_t tma_batch_desc_bytes();
 cudaError_t tma_fill_batch_desc(void *out, const uint8_t *src, size_t sp, void *dst, size_t dp,
                                 int32_t H, int32_t W, int R, int64_t item0, int64_t *items);
-// d_queue: two zeroed counters (fast-path items, then the others); all_fast
-// (every image's items on the fast path, see tma_batch_all_fast) skips the
-// second kernel.
+// d_queue: one zeroed counter; all_fast (every image's items on the fast
+// path with vector stores, see tma_all_fast) selects the lean kernel.
 cudaError_t launch_tma_batched(const void *d_descs, int n_img, int64_t total,
                                unsigned int *d_queue, int border, int fmt, int R, int grid,
-                               int sm_count, unsigned int *err, cudaStream_t st, bool all_fast);
-bool tma_batch_all_fast(int32_t W, int border, int fmt, const void *dst, size_t dp);
-// Kernel launches launch_tma_single makes for an image (1 or 2).
-int tma_launches(int32_t H, int32_t W, int border, int fmt, const void *dst, size_t dp, int R,
-                 int sm_count);
-
+                               int sm_count, unsigned int *err, cudaStream_t st, bool all_fast,
+                               bool bulk);
+bool tma_all_fast(int32_t W, int border, int fmt, const uint8_t *src, size_t sp, const void *dst,
+                  size_t dp);
 // DIRECT kernel (one thread per output pixel).
 cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, cudaStream_t st);
 

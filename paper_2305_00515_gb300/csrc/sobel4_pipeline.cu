@@ -19,7 +19,7 @@ struct Slot {
   void *h_out = nullptr;     // pinned
   uint8_t *d_in = nullptr;
   uint8_t *d_out = nullptr;
-  unsigned int *d_pair = nullptr;  // the captured kernels' own work-queue counters (4 words)
+  unsigned int *d_pair = nullptr;  // the captured kernel's work-queue counter pair (4 words)
   cudaStream_t stream = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t done = nullptr;

@@ -1,12 +1,14 @@
-// sobel4_tma.cu — host side of the TMA-staged kernel: the source tensor map
+// sobel4_tma.cu — host side of the TMA-family kernels: the source tensor map
 // (encoded through the driver entry point, so the library needs no -lcuda),
-// the strip-height rule and the launch.
+// the choice of staging (tensor copies for 16-byte aligned rows, bulk row
+// copies otherwise), the strip-height rule and the launch plan.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "sobel4_launch.h"
-#include "sobel4_tma.cuh"
+#include "sobel4_tma_fmt.cuh"
 
 #ifndef SOBEL4_TMA_L2PROMO
 #define SOBEL4_TMA_L2PROMO 3  // L2 fill granule of the copies: 0 none, 1 64 B, 2 128 B, 3 256 B
@@ -31,98 +33,36 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-template <int FMT, int MODE>
-int tma_resident() {
-  static const int r = [] {
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tma::tma_single_kernel<FMT, MODE>,
-                                                      tma::kWarps * 32, 0) != cudaSuccess ||
-        b < 1) {
-      (void)cudaGetLastError();
-      b = 1;
-    }
-    return b;
-  }();
-  return r;
-}
-
-template <int MODE>
-int resident_mode(int fmt) {
+int resident(int fmt, int mode, int st) {
   switch (fmt) {
-    case kF32: return tma_resident<kF32, MODE>();
-    case kU8: return tma_resident<kU8, MODE>();
-    default: return tma_resident<kS16x4, MODE>();
+    case kF32: return TmaFmt<kF32>::resident(mode, st);
+    case kU8: return TmaFmt<kU8>::resident(mode, st);
+    default: return TmaFmt<kS16x4>::resident(mode, st);
   }
 }
 
-int resident_for(int fmt) { return resident_mode<tma::kFastOnly>(fmt); }
+int resident_for(int fmt) { return resident(fmt, tma::kFastOnly, tma::kTensor); }
 
-// Which kernels an image needs: every item on the fast path (one lean
-// kernel), none (one general kernel), or both kinds: two launches when the
-// image is large enough to fill the GPU twice over, else one kernel that
-// carries both paths.
-enum Plan { kPlanFast, kPlanGeneral, kPlanBoth, kPlanAll };
-
-Plan plan_for(int32_t W, int border, int fmt, int dst_align, int64_t items, int sm_count) {
-  const int vec_need = fmt == kF32 ? 16 : (fmt == kU8 ? 4 : 8);
-  if (dst_align < vec_need || W < tma::kCols) return kPlanGeneral;
-  if (W % tma::kCols == 0 && (border == kValid || border == kConstant0)) return kPlanFast;
-  const int64_t warps = (int64_t)sm_count * resident_for(fmt) * tma::kWarps;
-  return items >= 2 * warps ? kPlanBoth : kPlanAll;
-}
-
-template <int FMT, int MODE>
-void launch_single_mode(const CUtensorMap &map, const tma::TmaImage &im, int border, int R,
-                        int items, int sm_count, unsigned int *pair, unsigned int *err,
-                        cudaStream_t st) {
-  const int64_t cap = (int64_t)sm_count * tma_resident<FMT, MODE>();
-  const int64_t grid = std::min<int64_t>((items + tma::kWarps - 1) / tma::kWarps, cap);
-  tma::tma_single_kernel<FMT, MODE><<<(unsigned)grid, tma::kWarps * 32, 0, st>>>(
-      map, im, border, R, items, pair, err);
-}
-
-template <int FMT>
-void launch_single_plan(Plan plan, const CUtensorMap &map, const tma::TmaImage &im, int border,
-                        int R, int items, int sm_count, unsigned int *pair, unsigned int *err,
-                        cudaStream_t st) {
-  if (plan == kPlanFast) {
-    launch_single_mode<FMT, tma::kFastOnly>(map, im, border, R, items, sm_count, pair, err, st);
-  } else if (plan == kPlanGeneral) {
-    launch_single_mode<FMT, tma::kGeneralOnly>(map, im, border, R, items, sm_count, pair, err, st);
-  } else if (plan == kPlanAll) {
-    launch_single_mode<FMT, tma::kAll>(map, im, border, R, items, sm_count, pair, err, st);
-  } else {
-    launch_single_mode<FMT, tma::kFastOnly>(map, im, border, R, items, sm_count, pair, err, st);
-    launch_single_mode<FMT, tma::kGeneralOnly>(map, im, border, R, items, sm_count, pair + 2,
-                                               err, st);
-  }
-}
-
-}  // namespace
-
-bool tma_eligible(const uint8_t *src, size_t sp) {
+// The tensor staging needs 16-byte aligned rows and the driver's encoder.
+bool tensor_ok(const uint8_t *src, size_t sp) {
   return ((uintptr_t)src % 16 == 0) && (sp % 16 == 0) && sp < (1ull << 40) &&
          encode_fn() != nullptr;
 }
 
-int tma_round_R(int R) {
-  R = std::max(R, tma::kUnroll);
-  return (R + tma::kUnroll - 1) / tma::kUnroll * tma::kUnroll;
-}
+// Which kernel an image needs: every item on the fast path with vector
+// stores (the lean kernel), none (the general kernel), or anything else (one
+// kernel that carries both paths and the realigned stores, and hands the edge
+// items out first).
+enum Plan { kPlanFast, kPlanGeneral, kPlanAll };
 
-int tma_pick_R(int fmt, int sm_count, int32_t H, int32_t W) {
-  const int64_t n_seg = (W + tma::kCols - 1) / tma::kCols;
-  // About two items per resident warp: the second round absorbs the spread
-  // of per-warp speeds better than one item each (measured on 8192^2).
-  const int64_t warps = (int64_t)sm_count * resident_for(fmt) * tma::kWarps;
-  const int64_t bands = std::max<int64_t>(1, (2 * warps + n_seg - 1) / n_seg);
-  int64_t R = (H + 2 * bands - 1) / (2 * bands);
-  R = std::max<int64_t>(R, 8);
-  R = (R + tma::kUnroll - 1) / tma::kUnroll * tma::kUnroll;
-  return (int)std::min<int64_t>(R, 1 << 20);
+Plan plan_for(int32_t W, int border, int fmt, int dst_align, int st) {
+  const int vec_need = fmt == kF32 ? 16 : (fmt == kU8 ? 4 : 8);
+  if (W < tma::kCols) return kPlanGeneral;
+  if (dst_align >= vec_need && W % tma::kCols == 0 &&
+      (border == kValid || (st == tma::kTensor && border == kConstant0)))
+    return kPlanFast;
+  return kPlanAll;
 }
-
-namespace {
 
 // The source tensor map: 2-D uint8 {W, H}, row stride sp, box 160 x 8,
 // zero fill outside the image.
@@ -157,43 +97,70 @@ tma::TmaImage make_image(const uint8_t *src, size_t sp, void *dst, size_t dp, in
   return im;
 }
 
+void single(int fmt, int mode, int st, const CUtensorMap &map, const tma::TmaImage &im,
+            int border, int R, int items, int sm_count, unsigned int *pair, unsigned int *err,
+            cudaStream_t s) {
+  const int64_t cap = (int64_t)sm_count * resident(fmt, mode, st);
+  const int grid = (int)std::min<int64_t>((items + tma::kWarps - 1) / tma::kWarps, cap);
+  switch (fmt) {
+    case kF32:
+      TmaFmt<kF32>::single(mode, st, map, im, border, R, items, grid, pair, err, s);
+      break;
+    case kU8:
+      TmaFmt<kU8>::single(mode, st, map, im, border, R, items, grid, pair, err, s);
+      break;
+    default:
+      TmaFmt<kS16x4>::single(mode, st, map, im, border, R, items, grid, pair, err, s);
+      break;
+  }
+}
+
 }  // namespace
+
+bool tma_eligible(const uint8_t *src, size_t sp) { return tensor_ok(src, sp); }
+
+int tma_round_R(int R) {
+  R = std::max(R, tma::kUnroll);
+  return (R + tma::kUnroll - 1) / tma::kUnroll * tma::kUnroll;
+}
+
+int tma_pick_R(int fmt, int sm_count, int32_t H, int32_t W, bool all_fast) {
+  const int64_t n_seg = (W + tma::kCols - 1) / tma::kCols;
+  // About two items per resident warp when every item takes the fast path:
+  // the second round absorbs the spread of per-warp speeds better than one
+  // item each (measured on 8192^2).  About six otherwise, so that the slower
+  // edge items, handed out first, stay short beside the rest.
+  const int64_t warps = (int64_t)sm_count * resident_for(fmt) * tma::kWarps;
+  const int64_t per_warp = all_fast ? 2 : 6;
+  const int64_t bands = std::max<int64_t>(1, (per_warp * warps + n_seg - 1) / n_seg);
+  int64_t R = (H + 2 * bands - 1) / (2 * bands);
+  R = std::max<int64_t>(R, 8);
+  R = (R + tma::kUnroll - 1) / tma::kUnroll * tma::kUnroll;
+  return (int)std::min<int64_t>(R, 1 << 20);
+}
 
 cudaError_t launch_tma_single(const uint8_t *src, size_t sp, void *dst, size_t dp, int32_t H,
                               int32_t W, int border, int fmt, int R, int sm_count,
                               unsigned int *pair, unsigned int *err, cudaStream_t st,
                               int lose_stage) {
   if (R < tma::kUnroll || R % tma::kUnroll) return cudaErrorInvalidValue;
+  const int staging = tensor_ok(src, sp) ? tma::kTensor : tma::kBulk;
   CUtensorMap map;
-  cudaError_t e = encode_map(&map, src, sp, H, W);
-  if (e != cudaSuccess) return e;
+  memset(&map, 0, sizeof(map));
+  if (staging == tma::kTensor) {
+    const cudaError_t e = encode_map(&map, src, sp, H, W);
+    if (e != cudaSuccess) return e;
+  }
   tma::TmaImage im = make_image(src, sp, dst, dp, H, W, R);
   im.lose_stage = lose_stage;
   const int64_t items = (int64_t)im.n_seg * im.n_band;
   if (items >= (1ll << 31)) return cudaErrorInvalidValue;
-  const Plan plan = plan_for(W, border, fmt, im.dst_align, items, sm_count);
+  const Plan plan = plan_for(W, border, fmt, im.dst_align, staging);
+  const int mode = plan == kPlanFast ? tma::kFastOnly
+                                     : (plan == kPlanGeneral ? tma::kGeneralOnly : tma::kAll);
   (void)cudaGetLastError();  // report this launch only, not an earlier failed call
-  switch (fmt) {
-    case kF32:
-      launch_single_plan<kF32>(plan, map, im, border, R, (int)items, sm_count, pair, err, st);
-      break;
-    case kU8:
-      launch_single_plan<kU8>(plan, map, im, border, R, (int)items, sm_count, pair, err, st);
-      break;
-    default:
-      launch_single_plan<kS16x4>(plan, map, im, border, R, (int)items, sm_count, pair, err, st);
-      break;
-  }
+  single(fmt, mode, staging, map, im, border, R, (int)items, sm_count, pair, err, st);
   return cudaGetLastError();
-}
-
-int tma_launches(int32_t H, int32_t W, int border, int fmt, const void *dst, size_t dp, int R,
-                 int sm_count) {
-  const tma::TmaImage im = make_image(nullptr, 0, (void *)dst, dp, H, W, R);
-  return plan_for(W, border, fmt, im.dst_align, (int64_t)im.n_seg * im.n_band, sm_count) ==
-                 kPlanBoth
-             ? 2
-             : 1;
 }
 
 size_t tma_batch_desc_bytes() { return sizeof(tma::TmaBatchDesc); }
@@ -201,54 +168,51 @@ size_t tma_batch_desc_bytes() { return sizeof(tma::TmaBatchDesc); }
 cudaError_t tma_fill_batch_desc(void *out, const uint8_t *src, size_t sp, void *dst, size_t dp,
                                 int32_t H, int32_t W, int R, int64_t item0, int64_t *items) {
   tma::TmaBatchDesc *d = (tma::TmaBatchDesc *)out;
-  cudaError_t e = encode_map(&d->map, src, sp, H, W);
-  if (e != cudaSuccess) return e;
+  memset(&d->map, 0, sizeof(d->map));
+  if (tensor_ok(src, sp)) {
+    const cudaError_t e = encode_map(&d->map, src, sp, H, W);
+    if (e != cudaSuccess) return e;
+  }
   d->im = make_image(src, sp, dst, dp, H, W, R);
   d->item0 = item0;
   *items = (int64_t)d->im.n_seg * d->im.n_band;
   return cudaSuccess;
 }
 
-cudaError_t launch_tma_batched(const void *d_descs, int n_img, int64_t total,
-                               unsigned int *d_queue, int border, int fmt, int R, int grid,
-                               int sm_count, unsigned int *err, cudaStream_t st, bool all_fast) {
-  if (R < tma::kUnroll || R % tma::kUnroll || total >= (1ll << 31)) return cudaErrorInvalidValue;
-  const tma::TmaBatchDesc *d = (const tma::TmaBatchDesc *)d_descs;
-  (void)cudaGetLastError();  // report this launch only, not an earlier failed call
-  auto go = [&](auto kernel, int res, unsigned int *queue) {
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(grid, (int64_t)sm_count * res));
-    kernel<<<g, tma::kWarps * 32, 0, st>>>(d, n_img, (int)total, queue, border, R, err);
-  };
-  switch (fmt) {
-    case kF32:
-      go(tma::tma_batched_kernel<kF32, tma::kFastOnly>, tma_resident<kF32, tma::kFastOnly>(),
-         d_queue);
-      if (!all_fast)
-        go(tma::tma_batched_kernel<kF32, tma::kGeneralOnly>,
-           tma_resident<kF32, tma::kGeneralOnly>(), d_queue + 1);
-      break;
-    case kU8:
-      go(tma::tma_batched_kernel<kU8, tma::kFastOnly>, tma_resident<kU8, tma::kFastOnly>(),
-         d_queue);
-      if (!all_fast)
-        go(tma::tma_batched_kernel<kU8, tma::kGeneralOnly>,
-           tma_resident<kU8, tma::kGeneralOnly>(), d_queue + 1);
-      break;
-    default:
-      go(tma::tma_batched_kernel<kS16x4, tma::kFastOnly>,
-         tma_resident<kS16x4, tma::kFastOnly>(), d_queue);
-      if (!all_fast)
-        go(tma::tma_batched_kernel<kS16x4, tma::kGeneralOnly>,
-           tma_resident<kS16x4, tma::kGeneralOnly>(), d_queue + 1);
-      break;
-  }
-  return cudaGetLastError();
-}
-
-bool tma_batch_all_fast(int32_t W, int border, int fmt, const void *dst, size_t dp) {
+bool tma_all_fast(int32_t W, int border, int fmt, const uint8_t *src, size_t sp,
+                        const void *dst, size_t dp) {
   int a = 1;
   while (a < 16 && (((uintptr_t)dst | (uintptr_t)dp) % (uintptr_t)(2 * a)) == 0) a *= 2;
-  return plan_for(W, border, fmt, a, 0, 1) == kPlanFast;
+  const int staging = tensor_ok(src, sp) ? tma::kTensor : tma::kBulk;
+  return plan_for(W, border, fmt, a, staging) == kPlanFast;
+}
+
+cudaError_t launch_tma_batched(const void *d_descs, int n_img, int64_t total,
+                               unsigned int *d_queue, int border, int fmt, int R, int grid,
+                               int sm_count, unsigned int *err, cudaStream_t st, bool all_fast,
+                               bool bulk) {
+  if (R < tma::kUnroll || R % tma::kUnroll || total >= (1ll << 31)) return cudaErrorInvalidValue;
+  const tma::TmaBatchDesc *d = (const tma::TmaBatchDesc *)d_descs;
+  const int staging = bulk ? tma::kBulk : tma::kTensor;
+  (void)cudaGetLastError();  // report this launch only, not an earlier failed call
+  auto go = [&](int mode, unsigned int *queue) {
+    const int g = (int)std::max<int64_t>(
+        1, std::min<int64_t>(grid, (int64_t)sm_count * resident(fmt, mode, staging)));
+    switch (fmt) {
+      case kF32:
+        TmaFmt<kF32>::batched(mode, staging, d, n_img, (int)total, queue, border, R, g, err, st);
+        break;
+      case kU8:
+        TmaFmt<kU8>::batched(mode, staging, d, n_img, (int)total, queue, border, R, g, err, st);
+        break;
+      default:
+        TmaFmt<kS16x4>::batched(mode, staging, d, n_img, (int)total, queue, border, R, g, err,
+                                st);
+        break;
+    }
+  };
+  go(all_fast ? tma::kFastOnly : tma::kAll, d_queue);
+  return cudaGetLastError();
 }
 
 }  // namespace sobel4

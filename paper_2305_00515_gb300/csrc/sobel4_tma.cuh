@@ -40,12 +40,28 @@ namespace tma {
 
 constexpr int kNC = 4;                        // columns per lane
 constexpr int kCols = 32 * kNC;               // columns per warp segment
-constexpr int kBoxW = 160;                    // staged bytes per row: columns x0-16 .. x0+143
+constexpr int kBoxW = 160;                    // tensor box width: columns x0-16 .. x0+143
 constexpr int kStageRows = 8;                 // rows per stage and strip
 constexpr int kSlots = 3;                     // ring slots per warp
-constexpr int kStripBytes = kStageRows * kBoxW;     // 1280
-constexpr int kSlotBytes = 2 * kStripBytes;         // 2560 (strip a, then strip b)
 constexpr int kWarps = 4;                     // warps per CTA
+
+// Two stagings share the kernel.  kTensor: 2-D tensor copies (TMA) of a box
+// of 160 x 8 bytes per strip; needs 16-byte aligned rows.  kBulk: 1-D bulk
+// copies (cp.async.bulk), one per row, of the 16-byte granules that hold the
+// row's bytes for columns x0-2 .. x0+129 (at most 176 bytes), for rows of any
+// alignment; each row slot keeps a 16-byte pad in front of the data and the
+// slot keeps, per row, the byte offset of column x0-2 from the copied data.
+enum Staging : int { kTensor = 0, kBulk = 1 };
+template <int ST>
+struct Geo {
+  static constexpr int kRowPitch = ST == kBulk ? 192 : kBoxW;  // bytes per staged row
+  static constexpr int kRowData = ST == kBulk ? 16 : 0;        // copied bytes start here
+  static constexpr int kStrip = kStageRows * kRowPitch;
+  static constexpr int kHdr = 2 * kStrip;                      // per-row offsets (kBulk)
+  static constexpr int kSlot = 2 * kStrip + (ST == kBulk ? 64 : 0);
+};
+constexpr int kStripBytes = Geo<kTensor>::kStrip;    // 1280
+constexpr int kSlotBytes = Geo<kTensor>::kSlot;      // 2560 (strip a, then strip b)
 #ifndef SOBEL4_TMA_UNROLL
 #define SOBEL4_TMA_UNROLL 4
 #endif
@@ -72,8 +88,9 @@ constexpr int min_ctas() { return MODE == kFastOnly ? SOBEL4_TMA_FAST_CTAS : SOB
 // kernel gives up, records the failure and leaves.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
+template <int ST>
 struct __align__(128) WarpRing {
-  uint8_t slot[kSlots][kSlotBytes];
+  uint8_t slot[kSlots][Geo<ST>::kSlot];
   uint64_t bar[kSlots];
 };
 
@@ -155,6 +172,23 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
       : "memory");
 }
 
+// 1-D bulk copy of `bytes` (a multiple of 16) from 16-byte aligned global
+// `src` into 16-byte aligned shared `dst`, completing `bar`.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes,
+                                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ int32_t lds_s32(uint32_t a) {
+  int32_t v;
+  asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ uint32_t lds_u16(uint32_t a) {
   uint16_t v;
   asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
@@ -173,8 +207,9 @@ __device__ __forceinline__ uint32_t lds_u8(uint32_t a) {
 
 // Packed columns c[0..7] (columns x-2 .. x+5 of both strips) from the staged
 // rows: column x-2 of strip a at shared address `a`, of strip b at a + kStripBytes.
+template <int STRIP = kStripBytes>
 __device__ __forceinline__ void read_cols(uint32_t a, uint32_t c[8]) {
-  const uint32_t b = a + kStripBytes;
+  const uint32_t b = a + STRIP;
   const uint32_t a0 = lds_u16(a), a1 = lds_u32(a + 2), a2 = lds_u16(a + 6);
   const uint32_t b0 = lds_u16(b), b1 = lds_u32(b + 2), b2 = lds_u16(b + 6);
   c[0] = __byte_perm(a0, b0, 0x6420);
@@ -192,7 +227,7 @@ __device__ __forceinline__ void read_cols(uint32_t a, uint32_t c[8]) {
 // The same through a generic pointer into the ring (plain loads the compiler
 // may schedule freely after the stage's barrier wait).
 __device__ __forceinline__ void read_cols_p(const uint8_t *a, uint32_t c[8]) {
-  const uint8_t *b = a + kStripBytes;
+  const uint8_t *b = a + kStripBytes;  // tensor staging
   const uint32_t a0 = *(const uint16_t *)a, a1 = *(const uint32_t *)(a + 2);
   const uint32_t a2 = *(const uint16_t *)(a + 6);
   const uint32_t b0 = *(const uint16_t *)b, b1 = *(const uint32_t *)(b + 2);
@@ -209,29 +244,57 @@ __device__ __forceinline__ void read_cols_p(const uint8_t *a, uint32_t c[8]) {
   c[7] = __byte_perm(a2, b2, 0x7531);
 }
 
-// Edge lanes under REPLICATE / REFLECT101: column j comes from staged byte
-// offset off[j] of the row (the mapped column).
-__device__ __forceinline__ void read_cols_mapped(uint32_t row_a, const uint32_t off[8],
-                                                 uint32_t c[8]) {
-#pragma unroll
-  for (int j = 0; j < 8; ++j)
-    c[j] = lds_u8(row_a + off[j]) | (lds_u8(row_a + kStripBytes + off[j]) << 16);
+// Packed columns from rows staged at any byte offset (bulk staging): column
+// x-2 of strip a at shared address `a`, of strip b at `b`; the 8 bytes of each
+// are funnel-shifted out of three aligned words (the shift is the same for
+// every lane of a row).
+__device__ __forceinline__ void read_cols_any(uint32_t a, uint32_t b, uint32_t c[8]) {
+  const uint32_t qa = a & ~3u, qb = b & ~3u;
+  const uint32_t sa = (a & 3u) * 8u, sb = (b & 3u) * 8u;
+  const uint32_t a0 = lds_u32(qa), a1 = lds_u32(qa + 4), a2 = lds_u32(qa + 8);
+  const uint32_t b0 = lds_u32(qb), b1 = lds_u32(qb + 4), b2 = lds_u32(qb + 8);
+  const uint32_t la0 = __funnelshift_r(a0, a1, sa), la1 = __funnelshift_r(a1, a2, sa);
+  const uint32_t lb0 = __funnelshift_r(b0, b1, sb), lb1 = __funnelshift_r(b1, b2, sb);
+  const uint32_t t0 = __byte_perm(la0, lb0, 0x5140), t1 = __byte_perm(la0, lb0, 0x7362);
+  const uint32_t t2 = __byte_perm(la1, lb1, 0x5140), t3 = __byte_perm(la1, lb1, 0x7362);
+  c[0] = __byte_perm(t0, 0u, 0x4140);
+  c[1] = __byte_perm(t0, 0u, 0x4342);
+  c[2] = __byte_perm(t1, 0u, 0x4140);
+  c[3] = __byte_perm(t1, 0u, 0x4342);
+  c[4] = __byte_perm(t2, 0u, 0x4140);
+  c[5] = __byte_perm(t2, 0u, 0x4342);
+  c[6] = __byte_perm(t3, 0u, 0x4140);
+  c[7] = __byte_perm(t3, 0u, 0x4342);
 }
 
-// Rows outside the image under REPLICATE / REFLECT101: the strip's bytes come
-// from the mapped row (and mapped columns) in global memory; the other strip
-// reads its staged row.
-__device__ __forceinline__ void gather_cols(const TmaImage &im, uint32_t row_a,
-                                            const uint32_t off[8], int x, int ra, int rb,
-                                            bool out_a, bool out_b, int border, uint32_t c[8]) {
+// Edge lanes under REPLICATE / REFLECT101: column j comes from staged byte
+// offset off[j] (relative to column x0-2) of each strip's row.
+__device__ __forceinline__ void read_cols_mapped(uint32_t base_a, uint32_t base_b,
+                                                 const int32_t off[8], uint32_t c[8]) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    c[j] = lds_u8(base_a + off[j]) | (lds_u8(base_b + off[j]) << 16);
+}
+
+// Edge items of the general path: each strip's byte for column x-2+j is the
+// staged byte at the mapped column (off[j], relative to column x0-2) when the
+// strip's row is inside the image, else the mapped row's byte in global
+// memory (REPLICATE / REFLECT101) or 0 (CONSTANT0, VALID); zmask marks
+// columns outside the image that read 0 (CONSTANT0).
+__device__ __forceinline__ void gather_cols(const TmaImage &im, uint32_t base_a, uint32_t base_b,
+                                            const int32_t off[8], uint32_t zmask, int x, int ra,
+                                            int rb, bool out_a, bool out_b, int border,
+                                            uint32_t c[8]) {
   bool z;
+  const bool mapped = border == kReplicate || border == kReflect101;
   const uint8_t *ga = im.src + (uint64_t)(uint32_t)map_index(ra, im.H, border, &z) * im.sp;
   const uint8_t *gb = im.src + (uint64_t)(uint32_t)map_index(rb, im.H, border, &z) * im.sp;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const int col = map_index(x - 2 + j, im.W, border, &z);
-    const uint32_t va = out_a ? (uint32_t)__ldg(ga + col) : lds_u8(row_a + off[j]);
-    const uint32_t vb = out_b ? (uint32_t)__ldg(gb + col) : lds_u8(row_a + kStripBytes + off[j]);
+    uint32_t va = out_a ? (mapped ? (uint32_t)__ldg(ga + col) : 0u) : lds_u8(base_a + off[j]);
+    uint32_t vb = out_b ? (mapped ? (uint32_t)__ldg(gb + col) : 0u) : lds_u8(base_b + off[j]);
+    if ((zmask >> j) & 1u) va = vb = 0u;
     c[j] = va | (vb << 16);
   }
 }
@@ -241,7 +304,98 @@ __device__ __forceinline__ void gather_cols(const TmaImage &im, uint32_t row_a,
 // x..x+3.  GEN: per-column and per-row masks (edge items); otherwise four
 // columns of both rows, vector stores.
 // ---------------------------------------------------------------------------
-template <int FMT, bool GEN>
+// Stores of one row's four elements per lane into a destination row that is
+// not vector-aligned.  Every lane's run starts at the same offset m from an
+// aligned chunk (runs are one chunk wide), so the warp shifts its elements up
+// by one lane: lanes 1..31 each write one whole aligned chunk made of the
+// previous lane's last m elements and their own first 4-m; lane 0 writes the
+// head of the first chunk and lane 31 the tail of the last element by element,
+// so that no store touches another segment's columns.  Every lane calls these
+// (they shuffle); `on` is warp-uniform.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void st4_f32_realigned(float *p, const float v[4], bool on) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t m = ((uint32_t)(uintptr_t)p >> 2) & 3u;  // elements past the chunk start
+  const float p1 = __shfl_up_sync(0xffffffffu, v[1], 1);
+  const float p2 = __shfl_up_sync(0xffffffffu, v[2], 1);
+  const float p3 = __shfl_up_sync(0xffffffffu, v[3], 1);
+  if (!on) return;
+  if (m == 0) {
+    *(float4 *)p = make_float4(v[0], v[1], v[2], v[3]);
+    return;
+  }
+  const float o0 = m == 1 ? p3 : (m == 2 ? p2 : p1);
+  const float o1 = m == 1 ? v[0] : (m == 2 ? p3 : p2);
+  const float o2 = m == 1 ? v[1] : (m == 2 ? v[0] : p3);
+  const float o3 = m == 1 ? v[2] : (m == 2 ? v[1] : v[0]);
+  if (lane > 0) {
+    *(float4 *)(p - m) = make_float4(o0, o1, o2, o3);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k < 4 - (int)m) p[k] = v[k];
+  }
+  if (lane == 31) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k >= 4 - (int)m) p[k] = v[k];
+  }
+}
+
+__device__ __forceinline__ void st4_u8_realigned(uint8_t *p, uint32_t w, bool on) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t m = (uint32_t)(uintptr_t)p & 3u;
+  const uint32_t prev = __shfl_up_sync(0xffffffffu, w, 1);
+  if (!on) return;
+  if (m == 0) {
+    *(uint32_t *)p = w;
+    return;
+  }
+  if (lane > 0) {
+    *(uint32_t *)(p - m) = __funnelshift_l(prev, w, 8u * m);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k < 4 - (int)m) p[k] = (uint8_t)(w >> (8 * k));
+  }
+  if (lane == 31) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k >= 4 - (int)m) p[k] = (uint8_t)(w >> (8 * k));
+  }
+}
+
+// w0 holds elements 0, 1 and w1 elements 2, 3 (little-endian int16 pairs).
+__device__ __forceinline__ void st4_s16_realigned(int16_t *p, uint32_t w0, uint32_t w1, bool on) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t m = ((uint32_t)(uintptr_t)p >> 1) & 3u;
+  const uint32_t q0 = __shfl_up_sync(0xffffffffu, w0, 1);
+  const uint32_t q1 = __shfl_up_sync(0xffffffffu, w1, 1);
+  if (!on) return;
+  if (m == 0) {
+    *(uint2 *)p = make_uint2(w0, w1);
+    return;
+  }
+  const uint64_t cur = ((uint64_t)w1 << 32) | w0, prev = ((uint64_t)q1 << 32) | q0;
+  const uint64_t out = (cur << (16u * m)) | (prev >> (64u - 16u * m));
+  if (lane > 0) {
+    *(uint2 *)(p - m) = make_uint2((uint32_t)out, (uint32_t)(out >> 32));
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k < 4 - (int)m) p[k] = (int16_t)(cur >> (16 * k));
+  }
+  if (lane == 31) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k >= 4 - (int)m) p[k] = (int16_t)(cur >> (16 * k));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// RA (fast path only): the destination rows are not vector-aligned; the
+// realigned stores above take the place of the vector stores.
+template <int FMT, bool GEN, bool RA>
 __device__ __forceinline__ void store_rows(const TmaImage &im, uint8_t *row_a, uint8_t *row_b,
                                            int x, const uint32_t vx[4], const uint32_t vy[4],
                                            const uint32_t vd[4], const uint32_t vt[4],
@@ -260,8 +414,13 @@ __device__ __forceinline__ void store_rows(const TmaImage &im, uint8_t *row_a, u
                                     __byte_perm(v[2], v[3], 0x5410) ^ 0x80008000u);
         const uint2 lb = make_uint2(__byte_perm(v[0], v[1], 0x7632),
                                     __byte_perm(v[2], v[3], 0x7632));
-        if (st_a) *(uint2 *)pa = la;
-        if (st_b) *(uint2 *)pb = lb;
+        if constexpr (RA) {
+          st4_s16_realigned(pa, la.x, la.y, st_a);
+          st4_s16_realigned(pb, lb.x, lb.y, st_b);
+        } else {
+          if (st_a) *(uint2 *)pa = la;
+          if (st_b) *(uint2 *)pb = lb;
+        }
       } else {
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -282,8 +441,13 @@ __device__ __forceinline__ void store_rows(const TmaImage &im, uint8_t *row_a, u
     for (int k = 0; k < 4; ++k) magnitude_f32x2(sa[k], sb[k], ga[k], gb[k]);
     float *pa = (float *)row_a + x, *pb = (float *)row_b + x;
     if (!GEN) {
-      if (st_a) *(float4 *)pa = make_float4(ga[0], ga[1], ga[2], ga[3]);
-      if (st_b) *(float4 *)pb = make_float4(gb[0], gb[1], gb[2], gb[3]);
+      if constexpr (RA) {
+        st4_f32_realigned(pa, ga, st_a);
+        st4_f32_realigned(pb, gb, st_b);
+      } else {
+        if (st_a) *(float4 *)pa = make_float4(ga[0], ga[1], ga[2], ga[3]);
+        if (st_b) *(float4 *)pb = make_float4(gb[0], gb[1], gb[2], gb[3]);
+      }
     } else {
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -319,8 +483,13 @@ __device__ __forceinline__ void store_rows(const TmaImage &im, uint8_t *row_a, u
     const uint32_t wa = ua[0] | (ua[1] << 8) | (ua[2] << 16) | (ua[3] << 24);
     const uint32_t wb = ub[0] | (ub[1] << 8) | (ub[2] << 16) | (ub[3] << 24);
     if (!GEN) {
-      if (st_a) *(uint32_t *)pa = wa;
-      if (st_b) *(uint32_t *)pb = wb;
+      if constexpr (RA) {
+        st4_u8_realigned(pa, wa, st_a);
+        st4_u8_realigned(pb, wb, st_b);
+      } else {
+        if (st_a) *(uint32_t *)pa = wa;
+        if (st_b) *(uint32_t *)pb = wb;
+      }
     } else if (vec && colmask == 0xFu) {
       if (st_a) *(uint32_t *)pa = wa;
       if (st_b) *(uint32_t *)pb = wb;
@@ -371,16 +540,22 @@ __device__ __forceinline__ void zero_row4(const TmaImage &im, int y, int x) {
 // One warp item.  Returns false when a stage wait ran out (recorded in *err).
 // ---------------------------------------------------------------------------
 struct ItemCtx {
-  const CUtensorMap *map;   // source image, box 160 x 8
+  const CUtensorMap *map;   // source image (tensor staging), box 160 x 8
   const uint8_t *ringp;     // the same ring as a generic pointer
   int lose_stage;           // stage of this item whose copy is withheld (-1: none)
   uint32_t ring;            // shared address of this warp's ring
   uint32_t gstage;          // stages this warp has used so far (slot / parity counter)
 };
 
+template <int ST>
+__device__ __forceinline__ uint32_t bar_addr(const ItemCtx &cx, uint32_t g) {
+  return cx.ring + (uint32_t)(kSlots * Geo<ST>::kSlot + 8 * (g % kSlots));
+}
+
 // Waits until stage counter g has landed (all lanes agree on the outcome).
+template <int ST>
 __device__ __forceinline__ bool wait_stage(const ItemCtx &cx, uint32_t g, unsigned int *err) {
-  const uint32_t bar = cx.ring + (uint32_t)(kSlots * kSlotBytes + 8 * (g % kSlots));
+  const uint32_t bar = bar_addr<ST>(cx, g);
   const uint32_t parity = (g / kSlots) & 1u;
   if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
   const uint64_t t0 = global_ns();
@@ -395,52 +570,91 @@ __device__ __forceinline__ bool wait_stage(const ItemCtx &cx, uint32_t g, unsign
 
 // After a failed wait: let the copies this warp still has in flight land
 // (bounded), so that none writes into shared memory after the CTA is gone.
+template <int ST>
 __device__ __forceinline__ void drain_stages(const ItemCtx &cx, uint32_t g_from, uint32_t g_to) {
   for (uint32_t g = g_from; g < g_to; ++g) {
-    const uint32_t bar = cx.ring + (uint32_t)(kSlots * kSlotBytes + 8 * (g % kSlots));
+    const uint32_t bar = bar_addr<ST>(cx, g);
     const uint64_t t0 = global_ns();
     while (!mbar_try_wait(bar, (g / kSlots) & 1u) && global_ns() - t0 < kWaitLimitNs) {
     }
   }
 }
 
+// Copies stage j of an item (rows 8j .. 8j+7 of both strips) into ring slot
+// g % kSlots.  All lanes call it after a warp barrier.  Tensor staging: lane
+// 0 issues two box copies.  Bulk staging: lane 8s+k copies row k of strip s
+// (the granules that hold columns x0-2 .. x0+129 of an image row; rows outside
+// the image are not copied) and records the offset of column x0-2 from the
+// copied data; lane 0 arms the barrier with the stage's total byte count
+// before any copy is issued.
+template <int ST>
+__device__ __forceinline__ void issue_stage(const TmaImage &im, const ItemCtx &cx, int x0, int ya,
+                                            int yb, int j, uint32_t g, int lane) {
+  using G = Geo<ST>;
+  const uint32_t slot = cx.ring + (uint32_t)(G::kSlot * (g % kSlots));
+  const uint32_t bar = bar_addr<ST>(cx, g);
+  if (j == cx.lose_stage) return;  // injected loss: this stage's wait must run out
+  if constexpr (ST == kTensor) {
+    if (lane == 0) {
+      fence_proxy_async();
+      mbar_expect_tx(bar, (uint32_t)G::kSlot);
+      tma_load_2d(slot, cx.map, x0 - 16, ya - 2 + kStageRows * j, bar);
+      tma_load_2d(slot + (uint32_t)G::kStrip, cx.map, x0 - 16, yb - 2 + kStageRows * j, bar);
+    }
+  } else {
+    uint32_t bytes = 0;
+    const uint8_t *from = nullptr;
+    uint32_t to = 0;
+    if (lane < 2 * kStageRows) {
+      const int s = lane / kStageRows, k = lane % kStageRows;
+      const int y = (s ? yb : ya) - 2 + kStageRows * j + k;
+      to = slot + (uint32_t)(s * G::kStrip + k * G::kRowPitch + G::kRowData);
+      int32_t hdr = 0;
+      if (y >= 0 && y < im.H) {
+        const uintptr_t row = (uintptr_t)im.src + (uintptr_t)(uint32_t)y * im.sp;
+        const uintptr_t lo = row + (uintptr_t)max(x0 - 2, 0);
+        const uintptr_t hi = row + (uintptr_t)min(x0 + kCols + 2, im.W);
+        const uintptr_t g0 = lo & ~(uintptr_t)15;
+        from = (const uint8_t *)g0;
+        bytes = (uint32_t)(((hi + 15) & ~(uintptr_t)15) - g0);
+        hdr = (int32_t)((intptr_t)(row + (uintptr_t)(x0 - 2)) - (intptr_t)g0);
+      }
+      *(int32_t *)(cx.ringp + (slot - cx.ring) + G::kHdr + 4 * lane) = hdr;
+    }
+    const uint32_t total = __reduce_add_sync(0xffffffffu, bytes);
+    if (lane == 0) mbar_expect_tx(bar, total);
+    __syncwarp();
+    if (bytes) {
+      fence_proxy_async();
+      bulk_load(to, from, bytes, bar);
+    }
+  }
+}
+
 // FULL: every output row of both strips lies inside the image (no row checks).
-template <int FMT, bool GEN, bool FULL>
-__device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg, int band,
+// RA (fast path): realigned stores for a destination that is not vector-aligned.
+template <int FMT, bool GEN, bool FULL, int ST, bool RA>
+// ya: first row of strip a; R: this item's strip height (see strip_rows).
+__device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg, int ya,
                                          int R, int lane, ItemCtx &cx, unsigned int *err) {
+  using G = Geo<ST>;
   const int H = im.H, W = im.W;
   const int x0 = seg * kCols;
   const int x = x0 + kNC * lane;
-  const int ya = band * 2 * R;
   const int yb = ya + R;
   const int steps = R + 4;
   const int n_stages = (steps + kStageRows - 1) / kStageRows;
   const uint32_t g0 = cx.gstage;
-  const bool map_rows = GEN && (border == kReplicate || border == kReflect101);
-
-  // Producer: lane 0 copies stage j (rows 8j .. 8j+7 of both strips).
-  auto issue = [&](int j) {
-    if (j == cx.lose_stage) return;  // injected loss: this stage's wait must run out
-    const uint32_t g = g0 + (uint32_t)j;
-    const uint32_t slot = cx.ring + (uint32_t)(kSlotBytes * (g % kSlots));
-    const uint32_t bar = cx.ring + (uint32_t)(kSlots * kSlotBytes + 8 * (g % kSlots));
-    mbar_expect_tx(bar, (uint32_t)kSlotBytes);
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-      tma_load_2d(slot + (uint32_t)(s * kStripBytes), cx.map, x0 - 16,
-                  (s ? yb : ya) - 2 + kStageRows * j, bar);
-  };
+  const bool mapped_rule = border == kReplicate || border == kReflect101;
 
   __syncwarp();  // every lane is done with the ring slots about to be refilled
-  if (lane == 0) {
-    fence_proxy_async();
-    for (int j = 0; j < kSlots && j < n_stages; ++j) issue(j);
-  }
+  for (int j = 0; j < kSlots && j < n_stages; ++j)
+    issue_stage<ST>(im, cx, x0, ya, yb, j, g0 + (uint32_t)j, lane);
 
   // Edge-item bookkeeping.
-  uint32_t colmask = 0xFu, framemask = 0u;
-  bool mapped_lane = false;
-  uint32_t off[8];
+  uint32_t colmask = 0xFu, framemask = 0u, zmask = 0u;
+  bool edge_lane = false;
+  int32_t off[8];
   const int na = min(R, H - ya);           // output rows of strip a inside the image
   const int nb = max(0, min(R, H - yb));   // ... of strip b
   bool vec = true;
@@ -451,14 +665,20 @@ __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg
       if (x + k < W) colmask |= 1u << k;
       if (border == kValid && (x + k < 2 || x + k > W - 3)) framemask |= 1u << k;
     }
-    mapped_lane = (border == kReplicate || border == kReflect101) && (x - 2 < 0 || x + 5 >= W);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
+      const int col = x - 2 + j;
       bool z;
-      const int m = map_index(x - 2 + j, W, border, &z);
-      const int o = m - (x0 - 16);
-      off[j] = (uint32_t)(o < 0 ? 0 : (o > kBoxW - 1 ? kBoxW - 1 : o));
+      const int m = map_index(col, W, border, &z);
+      const int o = m - (x0 - 2);  // staged offset relative to column x0-2
+      off[j] = o < 0 ? 0 : (o > kCols + 3 ? kCols + 3 : o);
+      if (ST == kBulk && border != kReplicate && border != kReflect101 && (col < 0 || col >= W))
+        zmask |= 1u << j;
     }
+    // Lanes whose columns cross an image edge read through the mapping (the
+    // bulk staging also for CONSTANT0, whose outside columns read 0).
+    edge_lane = (mapped_rule || (ST == kBulk && border == kConstant0)) &&
+                (x - 2 < 0 || x + 5 >= W);
     const int vec_need = FMT == kF32 ? 16 : (FMT == kU8 ? 4 : 8);
     vec = im.dst_align >= vec_need;
   }
@@ -468,31 +688,45 @@ __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg
   for (int k = 0; k < kNC; ++k) st[k] = col_zero();
   uint8_t *row_a = (uint8_t *)im.dst + (uint64_t)(uint32_t)ya * im.dp;
   uint8_t *row_b = (uint8_t *)im.dst + (uint64_t)(uint32_t)min(yb, H - 1) * im.dp;
-  const uint32_t lane_off = (uint32_t)(14 + kNC * lane);  // column x-2 in a staged row
 
-  auto step = [&](uint32_t rd, int s, bool tail) {
+  // rd: shared address of staged row k (data start) of strip a in the stage.
+  auto step = [&](uint32_t rd, int k, int s, bool tail) {
     const int i = s - 4;  // output row of this step within each strip
+    // Shared addresses of column x0-2 in strip a's and strip b's row.
+    uint32_t base_a, base_b;
+    if constexpr (ST == kTensor) {
+      base_a = rd + 14;
+      base_b = base_a + G::kStrip;
+    } else {
+      const uint32_t slot = rd - (uint32_t)(k * G::kRowPitch + G::kRowData);
+      base_a = rd + (uint32_t)lds_s32(slot + G::kHdr + 4 * k);
+      base_b = rd + (uint32_t)G::kStrip + (uint32_t)lds_s32(slot + G::kHdr + 4 * (kStageRows + k));
+    }
     uint32_t c[8];
     if (GEN) {
       const int ra = ya - 2 + s, rb = yb - 2 + s;  // input rows of this step
-      const bool out_a = map_rows && (ra < 0 || ra >= H);
-      const bool out_b = map_rows && (rb < 0 || rb >= H);
-      if (out_a || out_b) gather_cols(im, rd - lane_off, off, x, ra, rb, out_a, out_b, border, c);
-      else if (mapped_lane) read_cols_mapped(rd - lane_off, off, c);
-      else read_cols(rd, c);
-    } else {
+      const bool out_a = ra < 0 || ra >= H, out_b = rb < 0 || rb >= H;
+      if (((mapped_rule || ST == kBulk) && (out_a || out_b)) || edge_lane)
+        gather_cols(im, base_a, base_b, off, zmask, x, ra, rb, out_a, out_b, border, c);
+      else if (ST == kTensor)
+        read_cols<G::kStrip>(base_a + kNC * lane, c);
+      else
+        read_cols_any(base_a + kNC * lane, base_b + kNC * lane, c);
+    } else if constexpr (ST == kTensor) {
 #if SOBEL4_TMA_CLD
-      read_cols_p(cx.ringp + (rd - cx.ring), c);
+      read_cols_p(cx.ringp + (base_a + kNC * lane - cx.ring), c);
 #else
-      read_cols(rd, c);
+      read_cols<G::kStrip>(base_a + kNC * lane, c);
 #endif
+    } else {
+      read_cols_any(base_a + kNC * lane, base_b + kNC * lane, c);
     }
     uint32_t vx[kNC], vy[kNC], vd[kNC], vt[kNC];
     if (tail) {
 #pragma unroll
-      for (int k = 0; k < kNC; ++k)
-        column_step<true>(c[k], c[k + 1], c[k + 2], c[k + 3], c[k + 4], st[k], vx[k], vy[k],
-                          vd[k], vt[k]);
+      for (int q = 0; q < kNC; ++q)
+        column_step<true>(c[q], c[q + 1], c[q + 2], c[q + 3], c[q + 4], st[q], vx[q], vy[q],
+                          vd[q], vt[q]);
       const bool st_a = FULL || i < na, st_b = FULL || i < nb;
       bool zero_a = false, zero_b = false;
       if (GEN) {
@@ -501,27 +735,27 @@ __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg
           zero_b = yb + i < 2 || yb + i > H - 3;
         }
       }
-      store_rows<FMT, GEN>(im, row_a, row_b, x, vx, vy, vd, vt, st_a, st_b, zero_a, zero_b,
-                           colmask, framemask, vec);
+      store_rows<FMT, GEN, RA>(im, row_a, row_b, x, vx, vy, vd, vt, st_a, st_b, zero_a, zero_b,
+                               colmask, framemask, vec);
       row_a += im.dp;
       row_b += im.dp;
     } else {
 #pragma unroll
-      for (int k = 0; k < kNC; ++k)
-        column_step<false>(c[k], c[k + 1], c[k + 2], c[k + 3], c[k + 4], st[k], vx[k], vy[k],
-                           vd[k], vt[k]);
+      for (int q = 0; q < kNC; ++q)
+        column_step<false>(c[q], c[q + 1], c[q + 2], c[q + 3], c[q + 4], st[q], vx[q], vy[q],
+                           vd[q], vt[q]);
     }
   };
 
-  if (!wait_stage(cx, g0, err)) {
-    drain_stages(cx, g0 + 1, g0 + (uint32_t)min(kSlots, n_stages));
+  if (!wait_stage<ST>(cx, g0, err)) {
+    drain_stages<ST>(cx, g0 + 1, g0 + (uint32_t)min(kSlots, n_stages));
     return false;
   }
-  uint32_t rd = cx.ring + (uint32_t)(kSlotBytes * (g0 % kSlots)) + lane_off;
+  uint32_t rd = cx.ring + (uint32_t)(G::kSlot * (g0 % kSlots) + G::kRowData);
 #pragma unroll
   for (int s = 0; s < 4; ++s)  // rows 0..3 only fill the window
-    step(rd + (uint32_t)(s * kBoxW), s, false);
-  rd += 4 * kBoxW;
+    step(rd + (uint32_t)(s * G::kRowPitch), s, s, false);
+  rd += 4 * G::kRowPitch;
   // Main loop: kUnroll row steps per trip (R is a multiple of kUnroll, so the
   // trips tile the steps and the stage boundaries fall on trip boundaries).
 #pragma unroll 1
@@ -529,32 +763,43 @@ __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg
     if ((s & (kStageRows - 1)) == 0) {
       const int j = s / kStageRows;
       __syncwarp();  // stage j-1 has been read by every lane
-      if (lane == 0 && j - 1 + kSlots < n_stages) {
-        fence_proxy_async();
-        issue(j - 1 + kSlots);
-      }
-      if (!wait_stage(cx, g0 + (uint32_t)j, err)) {
-        drain_stages(cx, g0 + (uint32_t)j + 1, g0 + (uint32_t)min(j - 1 + kSlots + 1, n_stages));
+      if (j - 1 + kSlots < n_stages)
+        issue_stage<ST>(im, cx, x0, ya, yb, j - 1 + kSlots, g0 + (uint32_t)(j - 1 + kSlots),
+                        lane);
+      if (!wait_stage<ST>(cx, g0 + (uint32_t)j, err)) {
+        drain_stages<ST>(cx, g0 + (uint32_t)j + 1,
+                         g0 + (uint32_t)min(j - 1 + kSlots + 1, n_stages));
         return false;
       }
-      rd = cx.ring + (uint32_t)(kSlotBytes * ((g0 + (uint32_t)j) % kSlots)) + lane_off;
+      rd = cx.ring + (uint32_t)(G::kSlot * ((g0 + (uint32_t)j) % kSlots) + G::kRowData);
     }
+    const int k0 = s & (kStageRows - 1);
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) step(rd + (uint32_t)(u * kBoxW), s + u, true);
-    rd += kUnroll * kBoxW;
+    for (int u = 0; u < kUnroll; ++u) step(rd + (uint32_t)(u * G::kRowPitch), k0 + u, s + u, true);
+    rd += kUnroll * G::kRowPitch;
   }
   cx.gstage = g0 + (uint32_t)n_stages;
   if (!GEN && border == kValid) {
     // The paper's rule leaves the 2-pixel frame at 0.  The fast path computed
-    // it from zero-filled halos; the lane that stored each frame element now
-    // overwrites it (same thread, later store).
+    // it from halos that may hold anything outside the image; the lane that
+    // stored each frame element now overwrites it (same thread, later store;
+    // with realigned stores a neighbouring lane stored it, and the warp
+    // barrier orders the two).
+    if constexpr (RA) __syncwarp();
     const int yr[2] = {ya, yb}, nr[2] = {na, nb};
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
       const int f[4] = {0, 1, H - 2, H - 1};
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        if (f[q] >= yr[t] && f[q] < yr[t] + nr[t] && (q < 2 || f[q] > 1)) zero_row4<FMT>(im, f[q], x);
+        if (f[q] >= yr[t] && f[q] < yr[t] + nr[t] && (q < 2 || f[q] > 1)) {
+          if constexpr (RA) {
+#pragma unroll
+            for (int k = 0; k < kNC; ++k) zero_px<FMT>(im, f[q], x + k);
+          } else {
+            zero_row4<FMT>(im, f[q], x);
+          }
+        }
     }
     // Frame columns {0, 1, W-2, W-1} inside the segment: all lanes share the
     // rows; the barrier orders the stores of the lanes that computed them.
@@ -572,67 +817,143 @@ __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg
   return true;
 }
 
-// An item for the fast path: every lane's four columns inside the image, a
-// destination that takes one vector store per lane and row, and either a
-// border rule the copy engine's zero fill serves (CONSTANT0; VALID with the
-// frame zeroed afterwards) or every input row and column inside the image.
-__device__ __forceinline__ bool fast_item(const TmaImage &im, int border, int seg, int band,
+// An item for the fast path: every lane's four columns inside the image and
+// either a border rule the staging serves as is (VALID, frame zeroed afterwards;
+// CONSTANT0 with tensor staging, whose copies zero-fill) or every input row and
+// column inside the image.
+template <int ST>
+__device__ __forceinline__ bool fast_item(const TmaImage &im, int border, int seg, int ya,
                                           int R, int fmt) {
   const int x0 = seg * kCols;
-  const int ya = band * 2 * R;
-  const int vec_need = fmt == kF32 ? 16 : (fmt == kU8 ? 4 : 8);
-  if (im.dst_align < vec_need || x0 + kCols > im.W) return false;
-  if (border == kValid || border == kConstant0) return true;
+  (void)fmt;
+  if (x0 + kCols > im.W) return false;
+  if (border == kValid || (ST == kTensor && border == kConstant0)) return true;
   return x0 >= 2 && x0 + kCols + 2 <= im.W && ya >= 2 && ya + 2 * R + 2 <= im.H;
+}
+
+// Item order: the frame of edge items first, then the interior.  Edge items
+// take the general path, whose steps cost more than the fast path's; handing
+// them out first lets the fast items fill in around them instead of leaving
+// them as the tail of the launch.  The fast items form the rectangle of bands
+// [bl, bh) x segments [sl, sh) (the complement of fast_item's rules without
+// the destination test); item i maps to (seg, band) by taking, in turn, the
+// frame bands x all segments, the inner bands x frame segments, and the
+// inner rectangle band-major.  The mapping is a bijection on [0, n_seg *
+// n_band) for any bounds, so it never decides correctness.
+template <int ST>
+__device__ __forceinline__ void item_coords(const TmaImage &im, int border, int R, int i,
+                                            int *seg, int *band) {
+  const int S = im.n_seg, B = im.n_band;
+  const bool inner_rule = !(border == kValid || (ST == kTensor && border == kConstant0));
+  int sl = 0, sh = im.W / kCols, bl = 0, bh = B;
+  if (inner_rule) {
+    sl = 1;
+    sh = im.W >= kCols + 2 ? (im.W - kCols - 2) / kCols + 1 : 0;
+    bl = 1;
+    bh = im.H >= 2 * R + 2 ? (im.H - 2 * R - 2) / (2 * R) + 1 : 0;
+  }
+  sh = max(sh, sl);
+  bh = max(bh, bl);
+  const int nb_in = bh - bl, ns_in = sh - sl;
+  const int nA = (B - nb_in) * S;
+  if (i < nA) {
+    const int k = i / S;
+    *band = k < bl ? k : bh + (k - bl);
+    *seg = i - k * S;
+    return;
+  }
+  i -= nA;
+  const int ns_edge = S - ns_in;
+  if (i < nb_in * ns_edge) {
+    const int b = i / ns_edge, k = i - b * ns_edge;
+    *band = bl + b;
+    *seg = k < sl ? k : sh + (k - sl);
+    return;
+  }
+  i -= nb_in * ns_edge;
+  const int b = i / ns_in;
+  *band = bl + b;
+  *seg = sl + (i - b * ns_in);
+}
+
+// Strip height of the items of a band: R, except in a last band with fewer
+// than 2R rows, whose rows are split evenly between the two strips (rounded
+// up to the row-step unroll), so that no strip runs far past the image.
+__device__ __forceinline__ int strip_rows(const TmaImage &im, int band, int R) {
+  const int left = im.H - band * 2 * R;
+  if (left >= 2 * R) return R;
+  const int half = (left + 1) / 2;
+  return min(R, (half + kUnroll - 1) / kUnroll * kUnroll);
 }
 
 // Runs one item through the variant its geometry needs; a kernel that runs
 // only fast items (or only the others) carries only that code.
-template <int FMT, int MODE>
-__device__ __forceinline__ bool run_item(const TmaImage &im, int border, int seg, int band, int R,
+template <int FMT, int MODE, int ST>
+__device__ __forceinline__ bool run_item(const TmaImage &im, int border, int seg, int ya, int R,
                                          int lane, ItemCtx &cx, unsigned int *err, bool fast) {
   if (MODE != kFastOnly && !fast)
-    return tma_item<FMT, true, false>(im, border, seg, band, R, lane, cx, err);
-  if constexpr (MODE != kGeneralOnly) {
-    if (band * 2 * R + 2 * R <= im.H)
-      return tma_item<FMT, false, true>(im, border, seg, band, R, lane, cx, err);
-    return tma_item<FMT, false, false>(im, border, seg, band, R, lane, cx, err);
+    return tma_item<FMT, true, false, ST, false>(im, border, seg, ya, R, lane, cx, err);
+  const bool full = ya + 2 * R <= im.H;
+  if constexpr (MODE == kFastOnly) {
+    if (full) return tma_item<FMT, false, true, ST, false>(im, border, seg, ya, R, lane, cx, err);
+    return tma_item<FMT, false, false, ST, false>(im, border, seg, ya, R, lane, cx, err);
+  } else if constexpr (MODE == kAll) {
+    constexpr int vec_need = FMT == kF32 ? 16 : (FMT == kU8 ? 4 : 8);
+    if (im.dst_align >= vec_need) {
+      if (full) return tma_item<FMT, false, true, ST, false>(im, border, seg, ya, R, lane, cx, err);
+      return tma_item<FMT, false, false, ST, false>(im, border, seg, ya, R, lane, cx, err);
+    }
+    if (full) return tma_item<FMT, false, true, ST, true>(im, border, seg, ya, R, lane, cx, err);
+    return tma_item<FMT, false, false, ST, true>(im, border, seg, ya, R, lane, cx, err);
   }
   return false;
 }
 
+template <int ST>
+__device__ __forceinline__ void init_ring(ItemCtx &cx, WarpRing<ST> &ring, int lane) {
+  cx.ring = smem_addr(&ring);
+  cx.ringp = &ring.slot[0][0];
+  cx.gstage = 0;
+  cx.lose_stage = -1;
+  if (lane == 0) {
+    for (int i = 0; i < kSlots; ++i)
+      mbar_init(cx.ring + (uint32_t)(kSlots * Geo<ST>::kSlot + 8 * i), 1u);
+    mbar_init_fence();
+  }
+  if constexpr (ST == kBulk) {
+    // Zero the pads and offsets once so that no read of the ring ever meets
+    // uninitialised bytes.
+    for (int i = lane; i < kSlots * Geo<ST>::kSlot / 4; i += 32)
+      ((uint32_t *)&ring.slot[0][0])[i] = 0u;
+  }
+  __syncwarp();
+}
+
 // The single-image kernel: persistent CTAs of 4 warps; each warp pulls items
 // (band-major) from the counter pair[0]; the last warp out resets the pair.
-template <int FMT, int MODE>
+// `map` is used by the tensor staging only.
+template <int FMT, int MODE, int ST>
 __global__ void __launch_bounds__(kWarps * 32, min_ctas<MODE>())
     tma_single_kernel(const __grid_constant__ CUtensorMap map, TmaImage im, int border, int R,
                       int n_items, unsigned int *pair, unsigned int *err) {
-  __shared__ WarpRing rings[kWarps];
+  __shared__ WarpRing<ST> rings[kWarps];
   const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
   ItemCtx cx;
+  init_ring<ST>(cx, rings[threadIdx.x >> 5], lane);
   cx.map = &map;
-  cx.ring = smem_addr(&rings[warp]);
-  cx.ringp = &rings[warp].slot[0][0];
-  cx.gstage = 0;
-  if (lane == 0) {
-    for (int i = 0; i < kSlots; ++i)
-      mbar_init(cx.ring + (uint32_t)(kSlots * kSlotBytes + 8 * i), 1u);
-    mbar_init_fence();
-  }
-  __syncwarp();
   for (;;) {
     unsigned int got = 0;
     if (lane == 0) got = atomicAdd(&pair[0], 1u);
     got = __shfl_sync(0xffffffffu, got, 0);
     if (got >= (unsigned int)n_items) break;
     const int item = (int)got;
-    const int band = item / im.n_seg;
-    const int seg = item - band * im.n_seg;
+    int seg, band;
+    item_coords<ST>(im, border, R, item, &seg, &band);
     cx.lose_stage = item == 0 ? im.lose_stage : -1;
-    const bool fast = fast_item(im, border, seg, band, R, FMT);
+    const int ya = band * 2 * R, Ri = strip_rows(im, band, R);
+    const bool fast = fast_item<ST>(im, border, seg, ya, Ri, FMT);
     if ((MODE == kFastOnly && !fast) || (MODE == kGeneralOnly && fast)) continue;
-    if (!run_item<FMT, MODE>(im, border, seg, band, R, lane, cx, err, fast)) break;
+    if (!run_item<FMT, MODE, ST>(im, border, seg, ya, Ri, lane, cx, err, fast)) break;
   }
   if (lane == 0) {
     __threadfence();  // this warp's last fetch is performed before it counts out
@@ -644,27 +965,17 @@ __global__ void __launch_bounds__(kWarps * 32, min_ctas<MODE>())
   }
 }
 
-
 // The batched kernel: persistent CTAs of 4 warps pull items (image by image,
 // band-major) from *queue (zeroed by the host before the launch); a warp
 // finds an item's image by binary search over the descriptors' first items.
-template <int FMT, int MODE>
+template <int FMT, int MODE, int ST>
 __global__ void __launch_bounds__(kWarps * 32, min_ctas<MODE>())
     tma_batched_kernel(const TmaBatchDesc *__restrict__ descs, int n_img, int total,
                        unsigned int *queue, int border, int R, unsigned int *err) {
-  __shared__ WarpRing rings[kWarps];
+  __shared__ WarpRing<ST> rings[kWarps];
   const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
   ItemCtx cx;
-  cx.ring = smem_addr(&rings[warp]);
-  cx.ringp = &rings[warp].slot[0][0];
-  cx.gstage = 0;
-  if (lane == 0) {
-    for (int i = 0; i < kSlots; ++i)
-      mbar_init(cx.ring + (uint32_t)(kSlots * kSlotBytes + 8 * i), 1u);
-    mbar_init_fence();
-  }
-  __syncwarp();
+  init_ring<ST>(cx, rings[threadIdx.x >> 5], lane);
   int cur = -1;
   for (;;) {
     unsigned int got = 0;
@@ -680,18 +991,18 @@ __global__ void __launch_bounds__(kWarps * 32, min_ctas<MODE>())
     }
     const TmaBatchDesc *d = descs + lo;
     const TmaImage im = d->im;
-    const int local = (int)(item - d->item0);
-    const int band = local / im.n_seg;
-    const int seg = local - band * im.n_seg;
-    const bool fast = fast_item(im, border, seg, band, R, FMT);
+    int seg, band;
+    item_coords<ST>(im, border, R, (int)(item - d->item0), &seg, &band);
+    const int ya = band * 2 * R, Ri = strip_rows(im, band, R);
+    const bool fast = fast_item<ST>(im, border, seg, ya, Ri, FMT);
     if ((MODE == kFastOnly && !fast) || (MODE == kGeneralOnly && fast)) continue;
-    if (lo != cur) {
+    if (ST == kTensor && lo != cur) {
       if (lane == 0) tensormap_acquire(&d->map);
       cur = lo;
     }
     cx.map = &d->map;
     cx.lose_stage = -1;
-    if (!run_item<FMT, MODE>(im, border, seg, band, R, lane, cx, err, fast)) break;
+    if (!run_item<FMT, MODE, ST>(im, border, seg, ya, Ri, lane, cx, err, fast)) break;
   }
 }
 

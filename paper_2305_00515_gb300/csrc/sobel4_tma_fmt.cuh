@@ -1,0 +1,92 @@
+// sobel4_tma_fmt.cuh — launch helpers of the TMA-family kernels for one
+// output format, explicitly instantiated once per format in
+// sobel4_tma_{f32,u8,s16}.cu so the kernel variants compile in parallel.
+#pragma once
+
+#include <algorithm>
+
+#include "sobel4_tma.cuh"
+
+namespace sobel4 {
+
+template <int FMT>
+struct TmaFmt {
+  // Resident CTAs per SM of the single-image kernel (mode, staging).
+  static int resident(int mode, int st);
+  static void single(int mode, int st, const CUtensorMap &map, const tma::TmaImage &im,
+                     int border, int R, int items, int grid, unsigned int *pair,
+                     unsigned int *err, cudaStream_t s);
+  static void batched(int mode, int st, const tma::TmaBatchDesc *d, int n_img, int total,
+                      unsigned int *queue, int border, int R, int grid, unsigned int *err,
+                      cudaStream_t s);
+};
+
+namespace tma_detail {
+
+template <typename K>
+int occupancy(K kernel) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, tma::kWarps * 32, 0) !=
+          cudaSuccess ||
+      b < 1) {
+    (void)cudaGetLastError();
+    b = 1;
+  }
+  return b;
+}
+
+template <int FMT, int MODE, int ST>
+int resident_of() {
+  static const int r = occupancy(tma::tma_single_kernel<FMT, MODE, ST>);
+  return r;
+}
+
+}  // namespace tma_detail
+
+#define SOBEL4_TMA_SWITCH(MODE_, ST_, CALL)                                         \
+  do {                                                                              \
+    if ((ST_) == tma::kTensor) {                                                    \
+      if ((MODE_) == tma::kFastOnly) { CALL(tma::kFastOnly, tma::kTensor); }        \
+      else if ((MODE_) == tma::kGeneralOnly) { CALL(tma::kGeneralOnly, tma::kTensor); } \
+      else { CALL(tma::kAll, tma::kTensor); }                                       \
+    } else {                                                                        \
+      if ((MODE_) == tma::kFastOnly) { CALL(tma::kFastOnly, tma::kBulk); }          \
+      else if ((MODE_) == tma::kGeneralOnly) { CALL(tma::kGeneralOnly, tma::kBulk); } \
+      else { CALL(tma::kAll, tma::kBulk); }                                         \
+    }                                                                               \
+  } while (0)
+
+template <int FMT>
+int TmaFmt<FMT>::resident(int mode, int st) {
+#define SOBEL4_RES(M, S) return tma_detail::resident_of<FMT, M, S>()
+  SOBEL4_TMA_SWITCH(mode, st, SOBEL4_RES);
+#undef SOBEL4_RES
+}
+
+template <int FMT>
+void TmaFmt<FMT>::single(int mode, int st, const CUtensorMap &map, const tma::TmaImage &im,
+                         int border, int R, int items, int grid, unsigned int *pair,
+                         unsigned int *err, cudaStream_t s) {
+#define SOBEL4_SINGLE(M, S)                                                                  \
+  tma::tma_single_kernel<FMT, M, S><<<(unsigned)grid, tma::kWarps * 32, 0, s>>>(map, im, border, \
+                                                                           R, items, pair, err)
+  SOBEL4_TMA_SWITCH(mode, st, SOBEL4_SINGLE);
+#undef SOBEL4_SINGLE
+}
+
+template <int FMT>
+void TmaFmt<FMT>::batched(int mode, int st, const tma::TmaBatchDesc *d, int n_img, int total,
+                          unsigned int *queue, int border, int R, int grid, unsigned int *err,
+                          cudaStream_t s) {
+#define SOBEL4_BATCH(M, S)                                                                    \
+  tma::tma_batched_kernel<FMT, M, S><<<(unsigned)grid, tma::kWarps * 32, 0, s>>>(d, n_img, total, \
+                                                                            queue, border, R, err)
+  SOBEL4_TMA_SWITCH(mode, st, SOBEL4_BATCH);
+#undef SOBEL4_BATCH
+}
+
+extern template struct TmaFmt<kF32>;
+extern template struct TmaFmt<kU8>;
+extern template struct TmaFmt<kS16x4>;
+
+}  // namespace sobel4

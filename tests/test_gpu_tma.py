@@ -105,3 +105,25 @@ def test_device_status_clean_after_runs(handles):
     for name in ("tma", "tma_r4"):
         run_placed(torch, handles[name], img, "valid", "f32")
         assert pkg.sobel4_device_status(handles[name]) == 0
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+def test_realigned_stores_every_phase(handles, fmt):
+    """Fast-path items into destinations at every sub-vector offset, with a
+    pitch that moves the offset from row to row, from aligned and unaligned
+    sources: the lane-shifted stores, the head and tail elements of each
+    segment and the zeroed frame of the paper's rule."""
+    e = ELEM[fmt]
+    vec = {"f32": 16, "u8": 4, "s16x4": 8}[fmt]
+    for (H, W) in ((40, 256), (33, 384), (70, 517)):
+        img = synth.rects_noise(H, W, 3 * W + H)
+        for border in BORDERS:
+            want = oracle.sobel4(img, border, fmt)
+            for doff in range(e, vec, e):
+                for (sp, soff) in ((ceil16(W), 0), (W + 1, 3)):
+                    for name in ("tma", "tma_r4"):
+                        got, guards = run_placed(torch, handles[name], img, border, fmt,
+                                                 src_pitch=sp, src_offset=soff,
+                                                 dst_pitch=W * e + e, dst_offset=doff)
+                        assert guards, f"{name} {H}x{W} {border} doff {doff}: outside payload"
+                        assert_same(got, want, f"{name} {H}x{W} {border} doff {doff} sp {sp}")
