@@ -179,12 +179,16 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """DRAM bytes per launch of the RG kernel from the committed ncu summary
-    (profiles/tma_f32_8192_full.md, lines "kernel_source_hash: ..." and
+KERNELS = {0: ("lanecopy", "rg_single_kernel<F32>"), 1: ("tma", "tma_single_kernel<F32>"),
+           2: ("tc", "tc_single_kernel<F32>")}
+
+
+def recorded_traffic(stem: str):
+    """DRAM bytes per launch of the timed kernel from its committed ncu summary
+    (profiles/<stem>_f32_8192_full.md, lines "kernel_source_hash: ..." and
     "dram_bytes_per_launch: ..."), only when that capture was taken on the
     current kernel source; otherwise None."""
-    path = os.path.join(ROOT, "profiles", "tma_f32_8192_full.md")
+    path = os.path.join(ROOT, "profiles", f"{stem}_f32_8192_full.md")
     if not os.path.exists(path):
         return None
     fields = {}
@@ -468,12 +472,14 @@ def run_ours(args, world, rank, local):
     # The library's autotuner (untimed) picks the kernel and strip height for
     # this shape, as a serving deployment would once per shape.
     tuned = None
+    _, kind0, _, _ = pkg.sobel4_tune_config(h, H, W, 0)
+    stem, kernel_name = KERNELS[kind0]
     if not args.no_tune:
         st, _ = pkg.sobel4_tune(h, H, W, 0, 0)
         assert st == 0, pkg.sobel4_status_string(st)
         _, kind, ncl, rps = pkg.sobel4_tune_config(h, H, W, 0)
-        tuned = {"kernel": "tma" if kind == 1 else "lanecopy", "columns_per_lane": ncl,
-                 "rows_per_strip": rps}
+        stem, kernel_name = KERNELS[kind]
+        tuned = {"kernel": KERNELS[kind][0], "columns_per_lane": ncl, "rows_per_strip": rps}
     stream = torch.cuda.Stream(device=dev)
     sh = stream.cuda_stream
 
@@ -522,7 +528,7 @@ def run_ours(args, world, rank, local):
     mean_kernel_s = statistics.fmean(kern_ms) * 1e-3
     peak, peak_kind = measured_peaks()
     achieved = px * BYTES_PER_PX / mean_kernel_s / 1e9
-    traffic = recorded_traffic()
+    traffic = recorded_traffic(stem)
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -568,7 +574,7 @@ def run_ours(args, world, rank, local):
                          f"(> 2x L2) instead of a flush", "autotuned": tuned},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "tma_single_kernel<F32>", "peak_kind": peak_kind,
+                     "kernel": kernel_name, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": px * BYTES_PER_PX,
                      "mean_kernel_us": mean_kernel_s * 1e6,
                      "p50_kernel_us": statistics.median(kern_ms) * 1e3},

@@ -89,13 +89,19 @@ typedef enum { SOBEL4_OUT_F32 = 0, SOBEL4_OUT_U8 = 1, SOBEL4_OUT_S16X4 = 2 } sob
  * 16 bytes, else 1-D bulk copies of each row's 16-byte granules; destinations
  * that are not vector-aligned take lane-shifted aligned stores.
  * RG_LANECOPY selects the older staging in which each lane copies granules
- * itself (cp.async); all variants give identical results.
+ * itself (cp.async).  TC runs the tensor-core kernel (the masks of Eq. 3 as
+ * banded f16 matrix products with fp32 accumulators in tensor memory) on the
+ * images it covers (VALID, F32, source and destination rows on 16-byte
+ * boundaries, width a multiple of 4) and RG on the others; AUTO uses it for
+ * a shape only where sobel4_tune measured it fastest.  All variants give
+ * identical results.
  */
 typedef enum {
   SOBEL4_VARIANT_AUTO = 0,
   SOBEL4_VARIANT_DIRECT = 1,
   SOBEL4_VARIANT_RG = 2,
-  SOBEL4_VARIANT_RG_LANECOPY = 3
+  SOBEL4_VARIANT_RG_LANECOPY = 3,
+  SOBEL4_VARIANT_TC = 4
 } sobel4_variant;
 
 /* Creation options; pass NULL for defaults (all fields 0). */
@@ -273,8 +279,8 @@ int32_t sobel4_tune_entries(sobel4_handle h);
 /*
  * The configuration this handle uses for single VALID images of height x
  * width in format fmt whose source and destination rows are 16-byte aligned:
- * *kernel = 1 for the TMA-staged kernel, 0 for the lane-copy one; its columns
- * per lane and strip height
+ * *kernel = 2 for the tensor-core kernel, 1 for the TMA-staged register-window
+ * kernel, 0 for the lane-copy one; its columns per lane and strip height
  * (tuned if sobel4_tune or a loaded cache covers the shape, else the
  * built-in rule).  Errors: INVALID_ARG.
  */

@@ -32,7 +32,7 @@ __all__ = [
 _PKG = os.path.dirname(os.path.abspath(__file__))
 BORDERS = {"valid": 0, "replicate": 1, "reflect101": 2, "constant0": 3}
 FORMATS = {"f32": 0, "u8": 1, "s16x4": 2}
-VARIANTS = {"auto": 0, "direct": 1, "rg": 2, "rg_lanecopy": 3}
+VARIANTS = {"auto": 0, "direct": 1, "rg": 2, "rg_lanecopy": 3, "tc": 4}
 ELEM_SIZE = {"f32": 4, "u8": 1, "s16x4": 2}
 STATUS = {0: "SOBEL4_OK", 1: "SOBEL4_ERR_INVALID_ARG", 2: "SOBEL4_ERR_UNSUPPORTED",
           3: "SOBEL4_ERR_OOM", 4: "SOBEL4_ERR_CUDA", 5: "SOBEL4_ERR_TIMEOUT"}

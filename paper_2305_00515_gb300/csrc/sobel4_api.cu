@@ -105,7 +105,7 @@ struct TuneEntry {
   int kind, hb, wb, fmt;
   int nc, R, ctas;
   float us;
-  int kernel;  // single images: 0 = lane-copy staging, 1 = TMA staging
+  int kernel;  // 0 = lane-copy staging, 1 = TMA staging, 2 = tensor-core kernel (single images)
 };
 
 struct sobel4_ctx {
@@ -230,6 +230,18 @@ void rg_config(const sobel4_ctx *h, const uint8_t *src, size_t sp, const void *d
   else *R = pick_R(h, H, W);
 }
 
+// The tensor-core kernel serves the images it covers on TC handles, and on
+// AUTO handles without register-window options where the tuned table names it
+// for the shape.
+bool use_tc(const sobel4_ctx *h, const uint8_t *src, size_t sp, const void *dst, size_t dp,
+            int32_t H, int32_t W, int border, int fmt) {
+  if (!tc_eligible(src, sp, dst, dp, H, W, border, fmt)) return false;
+  if (h->variant == SOBEL4_VARIANT_TC) return true;
+  if (h->variant != SOBEL4_VARIANT_AUTO || h->nc_forced || h->rows_per_strip > 0) return false;
+  const TuneEntry *t = find_tuned(h, 0, H, W, fmt);
+  return t && t->kernel == 2;
+}
+
 int pow2_align(uintptr_t v) {
   int a = 1;
   while (a < 16 && v % (uintptr_t)(2 * a) == 0) a *= 2;
@@ -267,6 +279,10 @@ sobel4_status launch_one(sobel4_ctx *h, const uint8_t *src, size_t sp, void *dst
   if (h->variant == SOBEL4_VARIANT_DIRECT) {
     const ImageDesc im = make_desc(src, sp, dst, dp, H, W, 1, h->nc);
     e = launch_direct(im, border, fmt, stream);
+  } else if (use_tc(h, src, sp, dst, dp, H, W, border, fmt)) {
+    e = launch_tc_single(src, sp, dst, dp, H, W, border, fmt, h->sm_count, h->d_err, stream,
+                         h->lose_stage);
+    h->lose_stage = -1;
   } else {
     int nc, R;
     bool use_tma;
@@ -318,7 +334,7 @@ const char *sobel4_status_string(sobel4_status s) {
 sobel4_status sobel4_create(sobel4_handle *out, int32_t device, const sobel4_options *opt) {
   if (!out) return SOBEL4_ERR_INVALID_ARG;
   *out = nullptr;
-  if (opt && (opt->variant < 0 || opt->variant > SOBEL4_VARIANT_RG_LANECOPY || opt->rows_per_strip < 0 ||
+  if (opt && (opt->variant < 0 || opt->variant > SOBEL4_VARIANT_TC || opt->rows_per_strip < 0 ||
               opt->rows_per_strip > 4096 || opt->persistent_ctas_per_sm < 0 ||
               opt->persistent_ctas_per_sm > 64 ||
               (opt->columns_per_lane != 0 && opt->columns_per_lane != 2 &&
@@ -402,7 +418,7 @@ sobel4_status sobel4_device_status(sobel4_handle h) {
 uint64_t sobel4_launch_count(sobel4_handle h) { return h ? h->launches : 0; }
 
 sobel4_status sobel4_set_variant(sobel4_handle h, int32_t variant) {
-  if (!h || variant < SOBEL4_VARIANT_AUTO || variant > SOBEL4_VARIANT_RG_LANECOPY)
+  if (!h || variant < SOBEL4_VARIANT_AUTO || variant > SOBEL4_VARIANT_TC)
     return SOBEL4_ERR_INVALID_ARG;
   h->variant = variant;
   return SOBEL4_OK;
@@ -829,7 +845,8 @@ bool valid_entry(const TuneEntry &t) {
   return (t.kind == 0 || t.kind == 1) && t.hb >= 0 && t.hb <= 31 && t.wb >= 0 && t.wb <= 31 &&
          t.fmt >= 0 && t.fmt <= 2 && (t.nc == 2 || t.nc == 4) && t.R >= 1 && t.R <= (1 << 20) &&
          t.ctas >= 1 && t.ctas <= 64 && (t.kernel == 0 || (t.kernel == 1 && t.nc == 4 &&
-                                                           t.R == tma_round_R(t.R)));
+                                                           t.R == tma_round_R(t.R)) ||
+                                         (t.kernel == 2 && t.kind == 0));
 }
 
 }  // namespace
@@ -857,6 +874,18 @@ extern "C" sobel4_status sobel4_tune(sobel4_handle h, int32_t height, int32_t wi
       have = true;
     }
   };
+  // Tensor-core kernel (AUTO and TC handles, the images it covers).
+  if (e == cudaSuccess &&
+      (h->variant == SOBEL4_VARIANT_AUTO || h->variant == SOBEL4_VARIANT_TC) && !h->nc_forced &&
+      h->rows_per_strip <= 0 && tc_eligible(src, sp, dst, dp, height, width, border, fmt)) {
+    float us = 0.f;
+    e = median_us(h->own_stream, [&]() {
+      h->launches += 1;
+      return launch_tc_single(src, sp, dst, dp, height, width, border, fmt, h->sm_count,
+                              h->d_err, h->own_stream);
+    }, &us);
+    if (e == cudaSuccess) consider(2, 4, 8, us);
+  }
   // TMA-staged kernel: a few strip heights, including the one that gives every
   // resident warp about one item.
   if (h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced && tma_eligible(src, sp)) {
@@ -978,10 +1007,12 @@ extern "C" sobel4_status sobel4_tune_config(sobel4_handle h, int32_t height, int
   bool use_tma = false;
   int nc = 0, R = 0;
   DeviceGuard g(h->device);
-  rg_config(h, kAligned, ((size_t)width + 15) & ~(size_t)15, kAligned,
-            ((size_t)width * elem_size(fmt) + 15) & ~(size_t)15, height, width, SOBEL4_BORDER_VALID,
-            fmt, &use_tma, &nc, &R);
+  const size_t sp = ((size_t)width + 15) & ~(size_t)15;
+  const size_t dp = ((size_t)width * elem_size(fmt) + 15) & ~(size_t)15;
+  rg_config(h, kAligned, sp, kAligned, dp, height, width, SOBEL4_BORDER_VALID, fmt, &use_tma, &nc,
+            &R);
   *kernel = use_tma ? 1 : 0;
+  if (use_tc(h, kAligned, sp, kAligned, dp, height, width, SOBEL4_BORDER_VALID, fmt)) *kernel = 2;
   *columns_per_lane = nc;
   *rows_per_strip = R;
   return SOBEL4_OK;

@@ -58,6 +58,24 @@ cudaError_t launch_tma_batched(const void *d_descs, int n_img, int64_t total,
                                bool bulk);
 bool tma_all_fast(int32_t W, int border, int fmt, const uint8_t *src, size_t sp, const void *dst,
                   size_t dp);
+// A 2-D tensor map (uint8 or float32 elements) over `base` with row pitch
+// `pitch` bytes, H x W elements, a box of box_w x box_h elements, zero fill,
+// and optionally the 128-byte shared-memory swizzle; `map` points to a
+// 64-byte aligned CUtensorMap.  base and pitch must be multiples of 16.
+cudaError_t tma_encode_2d(void *map, const void *base, bool f32, size_t pitch, int32_t H,
+                          int32_t W, int box_w, int box_h, bool swizzle128);
+
+// Tensor-core kernel (sobel4_tc.cuh): VALID, F32, a width that is a multiple
+// of 4, a source that is tma_eligible and a destination whose address and
+// pitch are multiples of 16 bytes (tc_eligible).  A wait that runs out sets bit 0 of *err;
+// lose_tile >= 0 (failure injection for tests) withholds the copy of that
+// CTA-local tile so that the waits run out.
+bool tc_eligible(const uint8_t *src, size_t sp, const void *dst, size_t dp, int32_t H, int32_t W,
+                 int border, int fmt);
+cudaError_t launch_tc_single(const uint8_t *src, size_t sp, void *dst, size_t dp, int32_t H,
+                             int32_t W, int border, int fmt, int sm_count, unsigned int *err,
+                             cudaStream_t st, int lose_tile = -1);
+
 // DIRECT kernel (one thread per output pixel).
 cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, cudaStream_t st);
 

@@ -119,6 +119,23 @@ void single(int fmt, int mode, int st, const CUtensorMap &map, const tma::TmaIma
 
 bool tma_eligible(const uint8_t *src, size_t sp) { return tensor_ok(src, sp); }
 
+cudaError_t tma_encode_2d(void *map, const void *base, bool f32, size_t pitch, int32_t H,
+                          int32_t W, int box_w, int box_h, bool swizzle128) {
+  if (!base || (uintptr_t)base % 16 || pitch % 16 || pitch >= (1ull << 40) || !encode_fn())
+    return cudaErrorInvalidValue;
+  const cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+  const cuuint64_t strides[1] = {(cuuint64_t)pitch};
+  const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult cr = encode_fn()(
+      (CUtensorMap *)map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+      (void *)base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+      swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+      f32 ? CU_TENSOR_MAP_L2_PROMOTION_NONE : (CUtensorMapL2promotion)SOBEL4_TMA_L2PROMO,
+      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return cr == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 int tma_round_R(int R) {
   R = std::max(R, tma::kUnroll);
   return (R + tma::kUnroll - 1) / tma::kUnroll * tma::kUnroll;
