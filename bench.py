@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rows-per-strip", type=int, default=0)
+    ap.add_argument("--variant", choices=["auto", "rg", "tc"], default="auto",
+                    help="kernel variant of the timed handle (auto: the tuner's choice)")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (built-in strip-height rule)")
     ap.add_argument("--no-extras", action="store_true",
@@ -467,7 +469,7 @@ def run_ours(args, world, rank, local):
     nsets = max(2, -(-2 * L2_BYTES // per_set) + 1)
     srcs = [torch.from_numpy(img).to(f"cuda:{dev}") for _ in range(nsets)]
     outs = [torch.empty((H, W), dtype=torch.float32, device=f"cuda:{dev}") for _ in range(nsets)]
-    st, h = pkg.sobel4_create(dev, 0, args.rows_per_strip)
+    st, h = pkg.sobel4_create(dev, pkg.VARIANTS[args.variant], args.rows_per_strip)
     assert st == 0, pkg.sobel4_status_string(st)
     # The library's autotuner (untimed) picks the kernel and strip height for
     # this shape, as a serving deployment would once per shape.

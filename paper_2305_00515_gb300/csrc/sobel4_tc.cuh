@@ -208,14 +208,29 @@ __device__ __forceinline__ void bulk_wait0() {
 // ---------------------------------------------------------------------------
 // Bounded waits.  Single-thread form (copy, product and store issuers) and
 // warp form (all lanes agree).  Both give up early once another role raised
-// the abort flag.
+// the abort flag.  Each probe lets the hardware suspend the thread for up to
+// kSuspendNs until the phase completes, so waiting warps do not spin on the
+// issue slots the working warps need.
 // ---------------------------------------------------------------------------
+constexpr uint32_t kSuspendNs = 20000;
+
+__device__ __forceinline__ bool try_wait_suspend(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(kSuspendNs)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ bool wait_one(uint32_t bar, uint32_t parity, volatile uint32_t *abort,
                                          unsigned int *err) {
   if (tma::mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = tma::global_ns();
   for (;;) {
-    if (tma::mbar_try_wait(bar, parity)) return true;
+    if (try_wait_suspend(bar, parity)) return true;
     if (*abort) return false;
     if (tma::global_ns() - t0 > tma::kWaitLimitNs) {
       atomicOr(err, 1u);
@@ -230,7 +245,7 @@ __device__ __forceinline__ bool wait_warp(uint32_t bar, uint32_t parity, volatil
   if (__all_sync(0xffffffffu, tma::mbar_try_wait(bar, parity))) return true;
   const uint64_t t0 = tma::global_ns();
   for (;;) {
-    if (__all_sync(0xffffffffu, tma::mbar_try_wait(bar, parity))) return true;
+    if (__all_sync(0xffffffffu, try_wait_suspend(bar, parity))) return true;
     if (__any_sync(0xffffffffu, *abort != 0u)) return false;
     if (__any_sync(0xffffffffu, tma::global_ns() - t0 > tma::kWaitLimitNs)) {
       if ((threadIdx.x & 31) == 0) {
