@@ -131,6 +131,11 @@ struct sobel4_ctx {
   size_t d_in_bytes = 0;
   uint8_t *d_out = nullptr;
   size_t d_out_bytes = 0;
+  // Banded host-buffer runs: copy streams, per-band events, output ring.
+  cudaStream_t h2d_stream = nullptr, d2h_stream[2] = {nullptr, nullptr};
+  std::vector<cudaEvent_t> band_events;  // 3 per band: input landed, computed, downloaded
+  uint8_t *d_ring = nullptr;
+  size_t d_ring_bytes = 0;
   std::vector<TuneEntry> tuned;
   char device_name[256] = {0};
 };
@@ -389,8 +394,19 @@ sobel4_status sobel4_destroy(sobel4_handle h) {
     cudaStreamSynchronize(h->own_stream);
     cudaStreamDestroy(h->own_stream);
   }
+  if (h->h2d_stream) {
+    cudaStreamSynchronize(h->h2d_stream);
+    cudaStreamDestroy(h->h2d_stream);
+  }
+  for (cudaStream_t st : h->d2h_stream)
+    if (st) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
+  for (cudaEvent_t ev : h->band_events) cudaEventDestroy(ev);
   if (h->d_in) cudaFree(h->d_in);
   if (h->d_out) cudaFree(h->d_out);
+  if (h->d_ring) cudaFree(h->d_ring);
   if (h->d_pairs) cudaFree(h->d_pairs);
   delete h;
   return SOBEL4_OK;
@@ -617,7 +633,7 @@ sobel4_status sobel4_run_host(sobel4_handle h, const uint8_t *h_src, size_t src_
   const size_t row_out = (size_t)width * elem_size(fmt);
   const size_t dp = (row_out + 15) & ~(size_t)15;
   const size_t in_bytes = sp * (size_t)height;
-  const size_t out_bytes = dp * (size_t)height * planes(fmt);
+  const int np = planes(fmt);
   cudaError_t e = cudaSuccess;
   if (h->d_in_bytes < in_bytes) {
     if (h->d_in) cudaFree(h->d_in);
@@ -627,23 +643,107 @@ sobel4_status sobel4_run_host(sobel4_handle h, const uint8_t *h_src, size_t src_
     if (e != cudaSuccess) return cuda_fail(h, e);
     h->d_in_bytes = in_bytes;
   }
-  if (h->d_out_bytes < out_bytes) {
-    if (h->d_out) cudaFree(h->d_out);
-    h->d_out = nullptr;
-    h->d_out_bytes = 0;
-    e = cudaMalloc((void **)&h->d_out, out_bytes);
+  // Large images run as row bands through three streams, so that the upload
+  // of band k+1, the kernel of band k and the download of band k-1 overlap:
+  // the call then takes about as long as its larger copy direction instead
+  // of the sum of both copies and the kernel.  Band k computes the sub-image
+  // of its rows plus the 2-row halos above and below (the border rule applies
+  // at the image's own top and bottom only; a sub-image's halo rows are
+  // computed but never downloaded) into one slot of a 3-slot output ring.
+  const size_t out_total = dp * (size_t)height * (size_t)np;
+  const int32_t kMinBandRows = 256;
+  int32_t bands = 1;
+  if (out_total >= ((size_t)16 << 20) && height >= 2 * kMinBandRows)
+    bands = std::min<int32_t>(16, height / kMinBandRows);
+  if (bands == 1) {
+    const size_t out_bytes = out_total;
+    if (h->d_out_bytes < out_bytes) {
+      if (h->d_out) cudaFree(h->d_out);
+      h->d_out = nullptr;
+      h->d_out_bytes = 0;
+      e = cudaMalloc((void **)&h->d_out, out_bytes);
+      if (e != cudaSuccess) return cuda_fail(h, e);
+      h->d_out_bytes = out_bytes;
+    }
+    cudaStream_t st = h->own_stream;
+    e = cudaMemcpy2DAsync(h->d_in, sp, h_src, src_pitch, (size_t)width, (size_t)height,
+                          cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(h, e);
-    h->d_out_bytes = out_bytes;
+    sobel4_status s = launch_one(h, h->d_in, sp, h->d_out, dp, height, width, border, fmt, st);
+    if (s != SOBEL4_OK) return s;
+    e = cudaMemcpy2DAsync(h_dst, dst_pitch, h->d_out, dp, row_out, (size_t)height * np,
+                          cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    return SOBEL4_OK;
   }
-  cudaStream_t st = h->own_stream;
-  e = cudaMemcpy2DAsync(h->d_in, sp, h_src, src_pitch, (size_t)width, (size_t)height,
-                        cudaMemcpyHostToDevice, st);
+  const int32_t hb = (height + bands - 1) / bands;  // rows per band (the last may be shorter)
+  bands = (height + hb - 1) / hb;
+  const size_t slot_bytes = dp * (size_t)(hb + 4) * (size_t)np;
+  if (h->d_ring_bytes < 3 * slot_bytes) {
+    if (h->d_ring) cudaFree(h->d_ring);
+    h->d_ring = nullptr;
+    h->d_ring_bytes = 0;
+    e = cudaMalloc((void **)&h->d_ring, 3 * slot_bytes);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    h->d_ring_bytes = 3 * slot_bytes;
+  }
+  if (!h->h2d_stream) e = cudaStreamCreateWithFlags(&h->h2d_stream, cudaStreamNonBlocking);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+    if (!h->d2h_stream[i]) e = cudaStreamCreateWithFlags(&h->d2h_stream[i], cudaStreamNonBlocking);
+  while (e == cudaSuccess && h->band_events.size() < (size_t)(3 * bands)) {
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) h->band_events.push_back(ev);
+  }
   if (e != cudaSuccess) return cuda_fail(h, e);
-  sobel4_status s = launch_one(h, h->d_in, sp, h->d_out, dp, height, width, border, fmt, st);
-  if (s != SOBEL4_OK) return s;
-  e = cudaMemcpy2DAsync(h_dst, dst_pitch, h->d_out, dp, row_out, (size_t)height * planes(fmt),
-                        cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaEvent_t *ev_in = h->band_events.data();
+  cudaEvent_t *ev_done = ev_in + bands;
+  cudaEvent_t *ev_out = ev_done + bands;
+  // Downloads alternate between two streams (bands k and k+1 in flight together).
+  const cudaStream_t up = h->h2d_stream, comp = h->own_stream;
+  // The caller's earlier work on the handle's stream finishes first.
+  e = cudaEventRecord(ev_out[0], comp);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(up, ev_out[0], 0);
+  for (int32_t k = 0; k < bands && e == cudaSuccess; ++k) {
+    const int32_t r0 = k * hb, r1 = std::min(height, r0 + hb);
+    e = cudaMemcpy2DAsync(h->d_in + (size_t)r0 * sp, sp, h_src + (size_t)r0 * src_pitch,
+                          src_pitch, (size_t)width, (size_t)(r1 - r0), cudaMemcpyHostToDevice, up);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_in[k], up);
+  }
+  for (int32_t k = 0; k < bands && e == cudaSuccess; ++k) {
+    const int32_t r0 = k * hb, r1 = std::min(height, r0 + hb);
+    const int32_t s0 = std::max(0, r0 - 2), s1 = std::min(height, r1 + 2);
+    e = cudaStreamWaitEvent(comp, ev_in[k], 0);
+    if (e == cudaSuccess && k + 1 < bands) e = cudaStreamWaitEvent(comp, ev_in[k + 1], 0);
+    if (e == cudaSuccess && k >= 3) e = cudaStreamWaitEvent(comp, ev_out[k - 3], 0);
+    if (e != cudaSuccess) break;
+    uint8_t *slot = h->d_ring + (size_t)(k % 3) * slot_bytes;
+    sobel4_status s = launch_one(h, h->d_in + (size_t)s0 * sp, sp, slot, dp, s1 - s0, width,
+                                 border, fmt, comp);
+    if (s != SOBEL4_OK) {
+      cudaStreamSynchronize(up);
+      cudaStreamSynchronize(h->d2h_stream[0]);
+      cudaStreamSynchronize(h->d2h_stream[1]);
+      return s;
+    }
+    const cudaStream_t down = h->d2h_stream[k & 1];
+    e = cudaEventRecord(ev_done[k], comp);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(down, ev_done[k], 0);
+    for (int p = 0; p < np && e == cudaSuccess; ++p) {
+      const uint8_t *from = slot + ((size_t)p * (size_t)(s1 - s0) + (size_t)(r0 - s0)) * dp;
+      uint8_t *to = (uint8_t *)h_dst + ((size_t)p * (size_t)height + (size_t)r0) * dst_pitch;
+      e = cudaMemcpy2DAsync(to, dst_pitch, from, dp, row_out, (size_t)(r1 - r0),
+                            cudaMemcpyDeviceToHost, down);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev_out[k], down);
+  }
+  cudaError_t e2 = cudaStreamSynchronize(up);
+  cudaError_t e3 = cudaStreamSynchronize(comp);
+  cudaError_t e4 = cudaStreamSynchronize(h->d2h_stream[0]);
+  cudaError_t e5 = cudaStreamSynchronize(h->d2h_stream[1]);
+  if (e4 == cudaSuccess) e4 = e5;
+  if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : (e3 != cudaSuccess ? e3 : e4);
   if (e != cudaSuccess) return cuda_fail(h, e);
   return SOBEL4_OK;
 }

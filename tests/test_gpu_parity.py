@@ -159,3 +159,21 @@ def test_run_host_end_to_end():
         padded[:, :77] = synth.uniform(64, 77, 2)
         got = s.run_host(padded[:, :77])
         assert_same(got, oracle.sobel4(padded[:, :77]), "host padded")
+
+
+@pytest.mark.parametrize("border", ("valid", "replicate", "reflect101", "constant0"))
+def test_run_host_banded(border):
+    """Host-buffer runs large enough to be split into row bands (upload, kernel
+    and download of neighbouring bands overlapped): every border rule, each
+    format, a padded host source, and band seams at every row."""
+    with pkg.Sobel4(0) as s:
+        for (H, W, fmt) in ((1300, 3300, "f32"), (1100, 2000, "s16x4"), (4100, 4100, "u8")):
+            img = synth.rects_noise(H, W, H ^ W)
+            got = s.run_host(img, border=border, fmt=fmt)
+            assert_same(got, oracle.sobel4(img, border, fmt, threads=NCPU), f"{H}x{W} {fmt}")
+        padded = np.zeros((1301, 3320), np.uint8)
+        padded[:, :3303] = synth.uniform(1301, 3303, 4)
+        view = padded[:, :3303]
+        got = s.run_host(view, border=border)
+        assert_same(got, oracle.sobel4(np.ascontiguousarray(view), border, "f32", threads=NCPU),
+                    "padded host source")
