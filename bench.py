@@ -375,12 +375,23 @@ def bench_serving(torch, pkg, synth, seconds: float):
     res = {}
     for name, plain in (("batched", 0), ("plain_launch_per_request", 1)):
         res[name] = run(plain, t_arr)
+    # Saturation bursts: one short unrecorded burst per mode, then two rounds
+    # alternating the modes; each mode reports its faster round (a single
+    # burst's span moved by up to 2x with what ran before it in the process).
     burst = np.zeros(min(len(t_arr), 2000))
-    for name, plain in (("burst_batched", 0), ("burst_plain", 1)):
-        res[name] = run(plain, burst)
+    for plain in (1, 0):
+        run(plain, burst[:200])
+    rounds = {"burst_batched": [], "burst_plain": []}
+    for _ in range(2):
+        for name, plain in (("burst_plain", 1), ("burst_batched", 0)):
+            rounds[name].append(run(plain, burst))
+    for name, rs in rounds.items():
+        res[name] = min(rs, key=lambda r: r["span_s"])
+        res[name]["spans_s"] = [r["span_s"] for r in rs]
     return {"workload": f"Poisson 400 req/s for {seconds:.0f} s ({len(t_arr)} requests), "
                         "640x480 40% / 1280x720 30% / 1920x1080 20% / 3840x2160 10%, F32, "
-                        "8 GiB admission budget; burst = 2000 requests at t=0", **res}
+                        "8 GiB admission budget; burst = 2000 requests at t=0 (faster of two "
+                        "alternating rounds after a warm-up burst)", **res}
 
 
 # ----------------------------------------------------------------------------

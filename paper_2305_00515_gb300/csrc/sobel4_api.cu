@@ -79,6 +79,46 @@ struct BatchSlot {
   bool pending = false;
 };
 
+// Descriptor upload through kernel parameters: each launch carries up to
+// kParamChunk bytes of host data in its (large) parameter block and writes
+// them to device memory; the first also zeroes the slot's 64 work-queue
+// words.  Parameters travel with the launch command, so the upload never waits
+// behind bulk copies that the caller has queued on the copy engines (a serving
+// loop uploads the next requests while a batch runs).
+constexpr int kParamChunk = 31744;  // bytes per launch (the limit is 32764 with the other arguments)
+struct ParamChunk {
+  uint4 w[kParamChunk / 16];
+};
+
+__global__ void param_copy_kernel(const __grid_constant__ ParamChunk chunk, uint4 *dst, int n16,
+                                  unsigned int *queue) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+  if (queue && t < 64) queue[t] = 0u;
+  for (int i = t; i < n16; i += stride) dst[i] = chunk.w[i];
+}
+
+// Uploads `bytes` (a multiple of 16) from host `src` to device `dst`.  Zeroes
+// `queue` with the first launch when it is not null.
+cudaError_t param_upload(const void *src, void *dst, size_t bytes, unsigned int *queue,
+                         cudaStream_t st) {
+  static ParamChunk chunk;  // host staging of one launch's parameter block
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t off = 0;
+  do {
+    const size_t n = std::min(bytes - off, (size_t)kParamChunk);
+    if (n) memcpy(&chunk, (const uint8_t *)src + off, n);
+    (void)cudaGetLastError();
+    param_copy_kernel<<<2, 256, 0, st>>>(chunk, (uint4 *)((uint8_t *)dst + off), (int)(n / 16),
+                                         queue);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    queue = nullptr;
+    off += n;
+  } while (off < bytes);
+  return cudaSuccess;
+}
+
 size_t elem_size(int fmt) { return fmt == kF32 ? 4 : (fmt == kU8 ? 1 : 2); }
 int planes(int fmt) { return fmt == kS16x4 ? 4 : 1; }
 
@@ -307,6 +347,32 @@ sobel4_status launch_one(sobel4_ctx *h, const uint8_t *src, size_t sp, void *dst
   return SOBEL4_OK;
 }
 
+// (Re)allocates a batch slot's descriptor buffers for `cap` images.  Handles
+// start with kInitialSlotCap so that batches of ordinary size never allocate
+// (freeing device memory waits for the whole device, which a serving loop
+// must not do between batches).
+constexpr int kInitialSlotCap = 256;
+
+cudaError_t grow_slot(BatchSlot &slot, int cap) {
+  if (slot.h_desc) cudaFreeHost(slot.h_desc);
+  if (slot.d_desc) cudaFree(slot.d_desc);
+  if (slot.h_tma) cudaFreeHost(slot.h_tma);
+  if (slot.d_tma) cudaFree(slot.d_tma);
+  slot.h_desc = nullptr;
+  slot.d_desc = nullptr;
+  slot.h_tma = nullptr;
+  slot.d_tma = nullptr;
+  slot.cap = 0;
+  const size_t tb = tma_batch_desc_bytes() * cap;
+  cudaError_t e = cudaHostAlloc((void **)&slot.h_desc, sizeof(ImageDesc) * cap, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&slot.d_desc, sizeof(ImageDesc) * cap);
+  if (e == cudaSuccess) e = cudaHostAlloc((void **)&slot.h_tma, tb, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&slot.d_tma, tb);
+  if (e == cudaSuccess && !slot.d_queue) e = cudaMalloc((void **)&slot.d_queue, 256);
+  if (e == cudaSuccess) slot.cap = cap;
+  return e;
+}
+
 void free_slot(BatchSlot &s) {
   if (s.done && s.pending) cudaEventSynchronize(s.done);
   if (s.h_desc) cudaFreeHost(s.h_desc);
@@ -365,8 +431,10 @@ sobel4_status sobel4_create(sobel4_handle *out, int32_t device, const sobel4_opt
   if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_pairs, pair_bytes);
   if (e == cudaSuccess) e = cudaMemset(h->d_pairs, 0, pair_bytes);
   if (e == cudaSuccess) h->d_err = h->d_pairs + kQueueWords * kQueuePairs;
-  for (int i = 0; i < kSlots && e == cudaSuccess; ++i)
+  for (int i = 0; i < kSlots && e == cudaSuccess; ++i) {
     e = cudaEventCreateWithFlags(&h->slots[i].done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = grow_slot(h->slots[i], kInitialSlotCap);
+  }
   if (e != cudaSuccess) {
     sobel4_destroy(h);
     return SOBEL4_ERR_CUDA;
@@ -521,42 +589,35 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
     slot.pending = false;
   }
   if (slot.cap < n) {
-    int cap = std::max(n, 2 * slot.cap);
-    if (slot.h_desc) cudaFreeHost(slot.h_desc);
-    if (slot.d_desc) cudaFree(slot.d_desc);
-    if (slot.h_tma) cudaFreeHost(slot.h_tma);
-    if (slot.d_tma) cudaFree(slot.d_tma);
-    slot.h_desc = nullptr;
-    slot.d_desc = nullptr;
-    slot.h_tma = nullptr;
-    slot.d_tma = nullptr;
-    slot.cap = 0;
-    const size_t tb = tma_batch_desc_bytes() * cap;
-    e = cudaHostAlloc((void **)&slot.h_desc, sizeof(ImageDesc) * cap, cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&slot.d_desc, sizeof(ImageDesc) * cap);
-    if (e == cudaSuccess) e = cudaHostAlloc((void **)&slot.h_tma, tb, cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&slot.d_tma, tb);
-    if (e == cudaSuccess && !slot.d_queue) e = cudaMalloc((void **)&slot.d_queue, 256);
+    e = grow_slot(slot, std::max(n, 2 * slot.cap));
     if (e != cudaSuccess) return cuda_fail(h, e);
-    slot.cap = cap;
   }
   // Every image goes to the TMA-family batched kernel unless the handle asks
   // for lane copies: 16-byte aligned sources in one launch group (tensor
   // copies), the others in a second (bulk row copies).
   const bool tma_ok = h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced && !bl;
-  // TMA strip height: explicit option, else the tuned one, else about 64
-  // items per resident warp over the batch (8 .. 64 rows): many short items
-  // balance a ragged batch better than fewer tall ones.
+  // TMA strip height: explicit option, else the tuned one, else by the
+  // batch's make-up.  When every image runs on the fast path, about four
+  // items per resident warp (8 .. 128 rows): taller strips spend less on the
+  // 4-row window fill.  Otherwise about 64 items per warp (8 .. 64 rows): many
+  // short items balance the slower edge items of a ragged batch.
   int Rt = tma_round_R(R);
   if (tma_ok && h->rows_per_strip <= 0) {
     if (bt && bt->kernel == 1) {
       Rt = bt->R;
     } else {
       int64_t seg_rows = 0;
-      for (int32_t i = 0; i < n; ++i)
-        seg_rows += (int64_t)((imgs[i].width + 127) / 128) * imgs[i].height;
+      bool every_fast = true;
+      for (int32_t i = 0; i < n; ++i) {
+        const sobel4_image &m = imgs[i];
+        seg_rows += (int64_t)((m.width + 127) / 128) * m.height;
+        every_fast = every_fast && tma_all_fast(m.width, border, fmt, m.src, m.src_pitch, m.dst,
+                                                m.dst_pitch);
+      }
       const int64_t warps = (int64_t)h->sm_count * 4 * kWarpsPerCta;
-      Rt = tma_round_R((int)std::min<int64_t>(64, std::max<int64_t>(8, seg_rows / (128 * warps))));
+      Rt = every_fast
+               ? tma_round_R((int)std::min<int64_t>(128, std::max<int64_t>(8, seg_rows / (8 * warps))))
+               : tma_round_R((int)std::min<int64_t>(64, std::max<int64_t>(8, seg_rows / (128 * warps))));
     }
   }
   int n_lane = 0, n_tma = 0, n_grp[2] = {0, 0};
@@ -589,14 +650,14 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
   }
   if (total >= (1ll << 31) || total_grp[0] >= (1ll << 31) || total_grp[1] >= (1ll << 31))
     return SOBEL4_ERR_UNSUPPORTED;
-  e = cudaMemsetAsync(slot.d_queue, 0, 256, stream);
-  if (e == cudaSuccess && n_lane)
-    e = cudaMemcpyAsync(slot.d_desc, slot.h_desc, sizeof(ImageDesc) * n_lane,
-                        cudaMemcpyHostToDevice, stream);
+  // The descriptors reach the device in kernel parameters (param_upload), not
+  // by a host-to-device copy, which would queue behind the caller's uploads.
+  e = param_upload(slot.h_desc, slot.d_desc, sizeof(ImageDesc) * n_lane, slot.d_queue, stream);
   if (e == cudaSuccess && n_tma)
-    e = cudaMemcpyAsync(slot.d_tma, slot.h_tma, tma_batch_desc_bytes() * n_tma,
-                        cudaMemcpyHostToDevice, stream);
+    e = param_upload(slot.h_tma, slot.d_tma, tma_batch_desc_bytes() * n_tma, nullptr, stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
+  h->launches += 1 + (n_lane ? (sizeof(ImageDesc) * n_lane - 1) / kParamChunk : 0) +
+                 (n_tma ? (tma_batch_desc_bytes() * n_tma + kParamChunk - 1) / kParamChunk : 0);
   for (int g = 0; g < 2; ++g) {
     if (!n_grp[g]) continue;
     const int64_t want = (total_grp[g] + kWarpsPerCta - 1) / kWarpsPerCta;
