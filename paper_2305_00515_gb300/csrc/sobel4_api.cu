@@ -652,12 +652,14 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
     return SOBEL4_ERR_UNSUPPORTED;
   // The descriptors reach the device in kernel parameters (param_upload), not
   // by a host-to-device copy, which would queue behind the caller's uploads.
-  e = param_upload(slot.h_desc, slot.d_desc, sizeof(ImageDesc) * n_lane, slot.d_queue, stream);
+  // (n >= 1, so at least one of the two uploads runs and zeroes the queue.)
+  const size_t lane_bytes = sizeof(ImageDesc) * n_lane, tma_bytes = tma_batch_desc_bytes() * n_tma;
+  if (n_lane) e = param_upload(slot.h_desc, slot.d_desc, lane_bytes, slot.d_queue, stream);
   if (e == cudaSuccess && n_tma)
-    e = param_upload(slot.h_tma, slot.d_tma, tma_batch_desc_bytes() * n_tma, nullptr, stream);
+    e = param_upload(slot.h_tma, slot.d_tma, tma_bytes, n_lane ? nullptr : slot.d_queue, stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
-  h->launches += 1 + (n_lane ? (sizeof(ImageDesc) * n_lane - 1) / kParamChunk : 0) +
-                 (n_tma ? (tma_batch_desc_bytes() * n_tma + kParamChunk - 1) / kParamChunk : 0);
+  h->launches += (lane_bytes + kParamChunk - 1) / kParamChunk +
+                 (tma_bytes + kParamChunk - 1) / kParamChunk;
   for (int g = 0; g < 2; ++g) {
     if (!n_grp[g]) continue;
     const int64_t want = (total_grp[g] + kWarpsPerCta - 1) / kWarpsPerCta;
