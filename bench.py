@@ -266,6 +266,45 @@ def bench_batched(torch, pkg, synth, reps: int = 5):
             "batch_equals_single_runs": bool(same)}
 
 
+def bench_ablation(torch, pkg, synth):
+    """The paper's kernel ladder (Table 2, 5x5 four-directional) re-measured
+    here: GM = the direct 25-tap kernel, RG = the factored register-window
+    scheme with per-lane copies and with TMA staging, plus the tensor-core
+    variant; F32 VALID, mean CUDA-event time per launch (images up to 2048^2
+    stay in L2 between launches, as in the paper's repeated runs)."""
+    variants = (("GM_direct", "direct"), ("RG_lanecopy", "rg_lanecopy"), ("RG_tma", "rg"),
+                ("TC_tensor_core", "tc"))
+    res = {}
+    stream = torch.cuda.Stream()
+    for side in (512, 1024, 2048, 8192):
+        img = synth.rects_noise(side, side, side)
+        src = torch.from_numpy(img).cuda()
+        out = torch.empty((side, side), dtype=torch.float32, device="cuda")
+        row = {}
+        for name, variant in variants:
+            st, h = pkg.sobel4_create(0, pkg.VARIANTS[variant])
+            assert st == 0
+
+            def launch():
+                assert pkg.sobel4_run(h, src.data_ptr(), side, out.data_ptr(), 4 * side, side, side,
+                                      0, 0, stream.cuda_stream) == 0
+            for _ in range(5):
+                launch()
+            n = 50 if side <= 2048 else 20
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                a.record(stream)
+                for _ in range(n):
+                    launch()
+                b.record(stream)
+            stream.synchronize()
+            row[name] = round(a.elapsed_time(b) * 1e3 / n, 2)
+            pkg.sobel4_destroy(h)
+        res[f"{side}x{side}"] = row
+    return {"workload": "one rects+noise image per size, F32 VALID; microseconds per launch",
+            **res}
+
+
 def bench_video(torch, pkg, synth, frames: int, slots: int = 4):
     """3840x2160 frames through the graph-captured pipeline (H2D + kernel + D2H
     per frame, `slots` frame slots); the slot buffers hold pre-generated frames
@@ -567,6 +606,7 @@ def run_ours(args, world, rank, local):
         del srcs, outs
         torch.cuda.empty_cache()
         extras["batched"] = bench_batched(torch, pkg, synth)
+        extras["ablation_us"] = bench_ablation(torch, pkg, synth)
         torch.cuda.empty_cache()
         extras["video"] = bench_video(torch, pkg, synth, args.video_frames)
         extras["serving"] = bench_serving(torch, pkg, synth, args.serve_seconds)
