@@ -204,6 +204,23 @@ sobel4_status sobel4_device_status(sobel4_handle h);
  */
 sobel4_status sobel4_inject_stage_loss(sobel4_handle h, int32_t stage);
 
+/*
+ * Runtime weights: the generalised operator of Eq. (5) (Section 3.2),
+ *   K_x = a (1 n m n 1)^T (-1 -b 0 b 1),  K_y = its transpose,
+ *   K_d, K_dt the matching diagonal masks of Eq. (5),
+ * replaces the Eq. (3) masks for this handle's later runs (a = 1, b = 2,
+ * n = 4, m = 6 restores Eq. 3 and the register-window kernels).  With other
+ * weights, single images run on the tensor-core kernel where it applies
+ * (VALID, F32, aligned rows, width a multiple of 4) and on the DIRECT kernel
+ * otherwise; batches run image by image.  Every weight must be an integer
+ * (a a positive integer, b, n, m positive reals).
+ * Errors: INVALID_ARG (h == NULL, a weight that is not an integer or exceeds
+ * 16 bits, a non-positive parameter), UNSUPPORTED (the largest S = sum of the
+ * four squared responses would not fit in int32); later S16X4 runs return
+ * UNSUPPORTED when a response can exceed the int16 range.
+ */
+sobel4_status sobel4_set_weights(sobel4_handle h, double a, double b, double n, double m);
+
 /* Number of kernels this handle has launched so far (for launch accounting). */
 uint64_t sobel4_launch_count(sobel4_handle h);
 

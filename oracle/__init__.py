@@ -6,7 +6,8 @@ package.  The product path (``paper_2305_00515_gb300``) never imports it, and it
 imports nothing from there: the two share no code, tables or helpers.
 
 The arithmetic lives in ``sobel4_oracle.c`` (a direct 25-tap correlation per
-mask, Eq. (3) and Eq. (4) of Section 3.1, written out with no factoring); this
+mask, Eq. (3) and Eq. (4) of Section 3.1, written out with no factoring; the
+generalised masks of Eq. (5) written out entry by entry); this
 module only compiles it with gcc and marshals numpy arrays through ctypes.
 Every function here is pinned by ``tests/test_oracle_pins.py`` against the
 paper's other statements of the operator (Eq. (5), (10), (18)), closed forms,
@@ -63,6 +64,14 @@ class Oracle:
         lib.sobel4_oracle_responses.restype = ctypes.c_int
         lib.sobel4_oracle_masks.argtypes = [ctypes.POINTER(ctypes.c_int32)]
         lib.sobel4_oracle_masks.restype = ctypes.c_int
+        lib.sobel4_oracle_eq5_masks.argtypes = [ctypes.c_double] * 4 + [
+            ctypes.POINTER(ctypes.c_int32)]
+        lib.sobel4_oracle_eq5_masks.restype = ctypes.c_int
+        lib.sobel4_oracle_run_masks.argtypes = [ctypes.POINTER(ctypes.c_int32), u8p,
+                                                ctypes.c_size_t, ctypes.c_int32, ctypes.c_int32,
+                                                ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                                ctypes.c_size_t, ctypes.c_int32]
+        lib.sobel4_oracle_run_masks.restype = ctypes.c_int
         lib.sobel4_oracle_magnitude_f32.argtypes = [ctypes.c_int32]
         lib.sobel4_oracle_magnitude_f32.restype = ctypes.c_float
         lib.sobel4_oracle_magnitude_u8.argtypes = [ctypes.c_int32]
@@ -100,24 +109,40 @@ class Oracle:
         return out
 
     def run_into(self, img: np.ndarray, out: np.ndarray, border: str = "valid",
-                 fmt: str = "f32", threads: int = 1) -> None:
-        """Gradient output of Eq. (4) written into a caller array (rows may be padded)."""
+                 fmt: str = "f32", threads: int = 1, masks=None) -> None:
+        """Gradient output of Eq. (4) written into a caller array (rows may be padded);
+        `masks` (4, 5, 5) integers replace the Eq. (3) masks when given."""
         img, sp = self._src(img)
         H, W = img.shape
-        rc = self.lib.sobel4_oracle_run(
-            img.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), sp, H, W, BORDERS[border],
-            FORMATS[fmt], out.ctypes.data, out.strides[-2], int(threads))
+        u8 = img.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        if masks is None:
+            rc = self.lib.sobel4_oracle_run(u8, sp, H, W, BORDERS[border], FORMATS[fmt],
+                                            out.ctypes.data, out.strides[-2], int(threads))
+        else:
+            m = np.ascontiguousarray(masks, dtype=np.int32).reshape(100)
+            rc = self.lib.sobel4_oracle_run_masks(
+                m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), u8, sp, H, W, BORDERS[border],
+                FORMATS[fmt], out.ctypes.data, out.strides[-2], int(threads))
         if rc != 0:
             raise ValueError(f"oracle rejected arguments (H={H}, W={W}, border={border})")
 
     def sobel4(self, img: np.ndarray, border: str = "valid", fmt: str = "f32",
-               threads: int = 1) -> np.ndarray:
+               threads: int = 1, masks=None) -> np.ndarray:
         """Gradient output of Eq. (4): (H, W) f32/u8, or (4, H, W) int16 for s16x4."""
         H, W = img.shape
         shape = (4, H, W) if fmt == "s16x4" else (H, W)
         out = np.zeros(shape, dtype=_OUT_DTYPE[fmt])
-        self.run_into(img, out, border, fmt, threads)
+        self.run_into(img, out, border, fmt, threads, masks)
         return out
+
+    def eq5_masks(self, a: float, b: float, n: float, m: float) -> np.ndarray:
+        """The generalised masks of Eq. (5) as (4, 5, 5) int32 (x, y, d, dt)."""
+        out = np.zeros(100, dtype=np.int32)
+        rc = self.lib.sobel4_oracle_eq5_masks(float(a), float(b), float(n), float(m),
+                                              out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        if rc != 0:
+            raise ValueError(f"Eq. (5) weights are not integers for {(a, b, n, m)}")
+        return out.reshape(4, 5, 5)
 
     def magnitude_f32(self, s: int) -> np.float32:
         return np.float32(self.lib.sobel4_oracle_magnitude_f32(int(s)))
@@ -143,8 +168,13 @@ def responses(img: np.ndarray, border: str = "valid") -> np.ndarray:
     return default().responses(img, border)
 
 
-def sobel4(img: np.ndarray, border: str = "valid", fmt: str = "f32", threads: int = 1):
-    return default().sobel4(img, border, fmt, threads)
+def sobel4(img: np.ndarray, border: str = "valid", fmt: str = "f32", threads: int = 1,
+           masks=None):
+    return default().sobel4(img, border, fmt, threads, masks)
+
+
+def eq5_masks(a: float, b: float, n: float, m: float) -> np.ndarray:
+    return default().eq5_masks(a, b, n, m)
 
 
 def cpu_count() -> int:

@@ -109,15 +109,15 @@ static int32_t read_pixel(const uint8_t *src, size_t sp, int H, int W, int y, in
   return (int32_t)src[(size_t)yy * sp + (size_t)xx];
 }
 
-/* R_k(y, x) for the four masks, straight from the definition. */
-static void responses_at(const uint8_t *src, size_t sp, int H, int W, int border, int y,
-                         int x, int32_t r[4]) {
+/* R_k(y, x) for the four masks (k, i, j order), straight from the definition. */
+static void responses_at(const int32_t masks[4][5][5], const uint8_t *src, size_t sp, int H,
+                         int W, int border, int y, int x, int32_t r[4]) {
   int k, i, j;
   for (k = 0; k < 4; ++k) r[k] = 0;
   for (i = 0; i < 5; ++i) {
     for (j = 0; j < 5; ++j) {
       int32_t v = read_pixel(src, sp, H, W, y + i - 2, x + j - 2, border);
-      for (k = 0; k < 4; ++k) r[k] += ORACLE_MASKS[k][i][j] * v;
+      for (k = 0; k < 4; ++k) r[k] += masks[k][i][j] * v;
     }
   }
 }
@@ -152,6 +152,7 @@ static uint8_t magnitude_u8(int32_t s) {
 }
 
 typedef struct {
+  const int32_t (*masks)[5][5];
   const uint8_t *src;
   size_t sp;
   int H, W, border, fmt;
@@ -166,7 +167,7 @@ static void run_band(const band_job *jb) {
     for (x = 0; x < jb->W; ++x) {
       int32_t r[4] = {0, 0, 0, 0};
       if (is_computed(jb->H, jb->W, jb->border, y, x))
-        responses_at(jb->src, jb->sp, jb->H, jb->W, jb->border, y, x, r);
+        responses_at(jb->masks, jb->src, jb->sp, jb->H, jb->W, jb->border, y, x, r);
       int32_t s = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3];
       uint8_t *row = (uint8_t *)jb->dst + (size_t)y * jb->dp;
       if (jb->fmt == OR_F32) {
@@ -202,8 +203,28 @@ static int check_args(int H, int W, int border) {
  * nthreads contiguous bands run on POSIX threads (nthreads <= 1: the calling
  * thread only).
  */
+static int run_with(const int32_t masks[4][5][5], const uint8_t *src, size_t sp, int32_t H,
+                    int32_t W, int32_t border, int32_t fmt, void *dst, size_t dp,
+                    int32_t nthreads);
+
 int sobel4_oracle_run(const uint8_t *src, size_t sp, int32_t H, int32_t W, int32_t border,
                       int32_t fmt, void *dst, size_t dp, int32_t nthreads) {
+  return run_with(ORACLE_MASKS, src, sp, H, W, border, fmt, dst, dp, nthreads);
+}
+
+/* The same with caller-supplied masks (k, i, j order, e.g. from
+ * sobel4_oracle_eq5_masks).  The caller keeps S = sum R_k^2 inside int32. */
+int sobel4_oracle_run_masks(const int32_t *masks100, const uint8_t *src, size_t sp, int32_t H,
+                            int32_t W, int32_t border, int32_t fmt, void *dst, size_t dp,
+                            int32_t nthreads) {
+  if (!masks100) return OR_ERR_INVALID;
+  return run_with((const int32_t(*)[5][5])masks100, src, sp, H, W, border, fmt, dst, dp,
+                  nthreads);
+}
+
+static int run_with(const int32_t masks[4][5][5], const uint8_t *src, size_t sp, int32_t H,
+                    int32_t W, int32_t border, int32_t fmt, void *dst, size_t dp,
+                    int32_t nthreads) {
   int rc = check_args(H, W, border);
   if (rc) return rc;
   if (!src || !dst || fmt < OR_F32 || fmt > OR_S16X4) return OR_ERR_INVALID;
@@ -218,7 +239,7 @@ int sobel4_oracle_run(const uint8_t *src, size_t sp, int32_t H, int32_t W, int32
   }
   int t;
   for (t = 0; t < nthreads; ++t) {
-    band_job j = {src, sp, H, W, border, fmt, dst, dp,
+    band_job j = {masks, src, sp, H, W, border, fmt, dst, dp,
                   (int)((int64_t)H * t / nthreads), (int)((int64_t)H * (t + 1) / nthreads)};
     jobs[t] = j;
   }
@@ -243,10 +264,61 @@ int sobel4_oracle_responses(const uint8_t *src, size_t sp, int32_t H, int32_t W,
   for (y = 0; y < H; ++y) {
     for (x = 0; x < W; ++x) {
       int32_t r[4] = {0, 0, 0, 0};
-      if (is_computed(H, W, border, y, x)) responses_at(src, sp, H, W, border, y, x, r);
+      if (is_computed(H, W, border, y, x))
+        responses_at(ORACLE_MASKS, src, sp, H, W, border, y, x, r);
       for (k = 0; k < 4; ++k) out[(size_t)k * H * W + (size_t)y * W + x] = r[k];
     }
   }
+  return OR_OK;
+}
+
+/*
+ * The generalised masks of Eq. (5) (Section 3.2), written out entry by entry
+ * as the four matrices are displayed there, scaled by a, each entry rounded
+ * to the nearest integer.  Returns OR_ERR_INVALID when a parameter is not
+ * positive, a is not an integer, or an entry is not an integer (the
+ * operator requires every k_ij to be one).  (1, 2, 4, 6) gives Eq. (3).
+ */
+int sobel4_oracle_eq5_masks(double a, double b, double n, double m, int32_t *out100) {
+  if (!out100 || !(a > 0) || !(b > 0) || !(n > 0) || !(m > 0) || a != floor(a))
+    return OR_ERR_INVALID;
+  const double nb = n * b, mb = m * b;
+  const double K[4][5][5] = {
+      {/* K_x */
+       {-1, -b, 0, b, 1},
+       {-n, -nb, 0, nb, n},
+       {-m, -mb, 0, mb, m},
+       {-n, -nb, 0, nb, n},
+       {-1, -b, 0, b, 1}},
+      {/* K_y */
+       {-1, -n, -m, -n, -1},
+       {-b, -nb, -mb, -nb, -b},
+       {0, 0, 0, 0, 0},
+       {b, nb, mb, nb, b},
+       {1, n, m, n, 1}},
+      {/* K_d */
+       {-m, -n, -1, -b, 0},
+       {-n, -mb, -nb, 0, b},
+       {-1, -nb, 0, nb, 1},
+       {-b, 0, nb, mb, n},
+       {0, b, 1, n, m}},
+      {/* K_dt */
+       {0, -b, -1, -n, -m},
+       {b, 0, -nb, -mb, -n},
+       {1, nb, 0, -nb, -1},
+       {n, mb, nb, 0, -b},
+       {m, n, 1, b, 0}},
+  };
+  int k, i, j;
+  for (k = 0; k < 4; ++k)
+    for (i = 0; i < 5; ++i)
+      for (j = 0; j < 5; ++j) {
+        const double w = a * K[k][i][j];
+        const double r = floor(w + 0.5);
+        if (fabs(w - r) > 1e-9 * (fabs(w) > 1.0 ? fabs(w) : 1.0) || fabs(r) > 1e6)
+          return OR_ERR_INVALID;
+        out100[(k * 5 + i) * 5 + j] = (int32_t)r;
+      }
   return OR_OK;
 }
 

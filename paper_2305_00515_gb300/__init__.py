@@ -20,7 +20,7 @@ __all__ = [
     "BORDERS", "FORMATS", "VARIANTS", "Sobel4", "Sobel4Error", "Image", "Options",
     "library_path", "load", "sobel4_create", "sobel4_destroy", "sobel4_run",
     "sobel4_run_batched", "sobel4_run_host", "sobel4_status_string", "sobel4_last_cuda_error",
-    "sobel4_device_status", "sobel4_inject_stage_loss", "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
+    "sobel4_device_status", "sobel4_inject_stage_loss", "sobel4_set_weights", "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
     "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched", "sobel4_tune_entries",
     "sobel4_tune_config", "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create",
     "sobel4_pipeline_buffers", "sobel4_pipeline_submit", "sobel4_pipeline_wait",
@@ -40,7 +40,7 @@ STATUS = {0: "SOBEL4_OK", 1: "SOBEL4_ERR_INVALID_ARG", 2: "SOBEL4_ERR_UNSUPPORTE
 EXPORTED_SYMBOLS = (
     "sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_batched", "sobel4_run_host",
     "sobel4_status_string", "sobel4_last_cuda_error", "sobel4_device_status",
-    "sobel4_inject_stage_loss",
+    "sobel4_inject_stage_loss", "sobel4_set_weights",
     "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
     "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched", "sobel4_tune_entries",
     "sobel4_tune_config", "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create",
@@ -113,6 +113,8 @@ def load() -> ctypes.CDLL:
         lib.sobel4_last_cuda_error.restype = i32
         lib.sobel4_device_status.argtypes = [vp]
         lib.sobel4_inject_stage_loss.argtypes = [vp, i32]
+        lib.sobel4_set_weights.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double]
         lib.sobel4_launch_count.argtypes = [vp]
         lib.sobel4_launch_count.restype = ctypes.c_uint64
         lib.sobel4_set_variant.argtypes = [vp, i32]
@@ -144,6 +146,7 @@ def load() -> ctypes.CDLL:
         for name in ("sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_batched",
                      "sobel4_run_host", "sobel4_set_variant", "sobel4_check_magnitude",
                      "sobel4_device_status", "sobel4_inject_stage_loss", "sobel4_tune_config",
+                     "sobel4_set_weights",
                      "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched",
                      "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create",
                      "sobel4_pipeline_buffers", "sobel4_pipeline_submit", "sobel4_pipeline_wait",
@@ -200,6 +203,11 @@ def sobel4_last_cuda_error(h) -> int:
 
 def sobel4_device_status(h) -> int:
     return load().sobel4_device_status(h)
+
+
+def sobel4_set_weights(h, a: float, b: float, n: float, m: float) -> int:
+    """Eq. (5) weights for the handle's later runs (1, 2, 4, 6 = Eq. 3)."""
+    return load().sobel4_set_weights(h, a, b, n, m)
 
 
 def sobel4_inject_stage_loss(h, stage: int) -> int:
@@ -403,6 +411,10 @@ class Sobel4:
 
     def set_variant(self, variant: str):
         _check(sobel4_set_variant(self.handle, VARIANTS[variant]), "sobel4_set_variant")
+
+    def set_weights(self, a: float = 1, b: float = 2, n: float = 4, m: float = 6):
+        """The generalised operator of Eq. (5); the defaults restore Eq. (3)."""
+        _check(sobel4_set_weights(self.handle, a, b, n, m), "sobel4_set_weights")
 
     @staticmethod
     def _stream(stream) -> int:

@@ -166,6 +166,9 @@ struct sobel4_ctx {
   uint32_t next_pair = 0;
   unsigned int *d_err = nullptr;  // bit 0: a bounded wait in a kernel ran out (inside d_pairs)
   int lose_stage = -1;            // failure injection for the next TMA-staged launch
+  bool custom = false;            // runtime weights (Eq. 5) replace Eq. (3)
+  bool custom_s16_ok = true;      // every response fits the S16X4 planes
+  Masks4 masks{};
   cudaStream_t own_stream = nullptr;
   uint8_t *d_in = nullptr;
   size_t d_in_bytes = 0;
@@ -321,9 +324,20 @@ sobel4_status launch_one(sobel4_ctx *h, const uint8_t *src, size_t sp, void *dst
                          int32_t H, int32_t W, int border, int fmt, cudaStream_t stream,
                          unsigned int *pair = nullptr) {
   cudaError_t e;
-  if (h->variant == SOBEL4_VARIANT_DIRECT) {
+  if (h->custom) {
+    // Runtime weights: the tensor-core kernel where it applies, else DIRECT.
+    if (fmt == kS16x4 && !h->custom_s16_ok) return SOBEL4_ERR_UNSUPPORTED;
+    if (h->variant != SOBEL4_VARIANT_DIRECT && tc_eligible(src, sp, dst, dp, H, W, border, fmt)) {
+      e = launch_tc_single(src, sp, dst, dp, H, W, border, fmt, h->sm_count, h->d_err, stream,
+                           h->lose_stage, &h->masks);
+      h->lose_stage = -1;
+    } else {
+      const ImageDesc im = make_desc(src, sp, dst, dp, H, W, 1, h->nc);
+      e = launch_direct(im, border, fmt, &h->masks, stream);
+    }
+  } else if (h->variant == SOBEL4_VARIANT_DIRECT) {
     const ImageDesc im = make_desc(src, sp, dst, dp, H, W, 1, h->nc);
-    e = launch_direct(im, border, fmt, stream);
+    e = launch_direct(im, border, fmt, nullptr, stream);
   } else if (use_tc(h, src, sp, dst, dp, H, W, border, fmt)) {
     e = launch_tc_single(src, sp, dst, dp, H, W, border, fmt, h->sm_count, h->d_err, stream,
                          h->lose_stage);
@@ -488,6 +502,35 @@ sobel4_status sobel4_inject_stage_loss(sobel4_handle h, int32_t stage) {
   return SOBEL4_OK;
 }
 
+sobel4_status sobel4_set_weights(sobel4_handle h, double a, double b, double n, double m) {
+  if (!h) return SOBEL4_ERR_INVALID_ARG;
+  Masks4 mk;
+  if (!eq5_masks(a, b, n, m, &mk)) return SOBEL4_ERR_INVALID_ARG;
+  // Largest |R_k| = 255 x (sum of the positive weights of mask k) (every mask
+  // sums to zero); S must stay exact in int32 (and G's conversion exact).
+  double s_max = 0.0;
+  bool s16 = true;
+  for (int k = 0; k < 4; ++k) {
+    int64_t pos = 0, sum = 0;
+    for (int i = 0; i < 5; ++i)
+      for (int j = 0; j < 5; ++j) {
+        pos += mk.w[k][i][j] > 0 ? mk.w[k][i][j] : 0;
+        sum += mk.w[k][i][j];
+      }
+    if (sum != 0) return SOBEL4_ERR_INVALID_ARG;
+    const double r = 255.0 * (double)pos;
+    s_max += r * r;
+    s16 = s16 && r <= 32767.0;
+  }
+  if (s_max >= 2147483648.0) return SOBEL4_ERR_UNSUPPORTED;
+  Masks4 eq3;
+  eq5_masks(1, 2, 4, 6, &eq3);
+  h->custom = memcmp(&mk, &eq3, sizeof(mk)) != 0;
+  h->custom_s16_ok = s16;
+  h->masks = mk;
+  return SOBEL4_OK;
+}
+
 sobel4_status sobel4_device_status(sobel4_handle h) {
   if (!h) return SOBEL4_ERR_INVALID_ARG;
   DeviceGuard g(h->device);
@@ -565,7 +608,7 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
     else end_in = std::max(end_in, v.e);
   }
   DeviceGuard g(h->device);
-  if (h->variant == SOBEL4_VARIANT_DIRECT) {
+  if (h->variant == SOBEL4_VARIANT_DIRECT || h->custom) {
     for (int32_t i = 0; i < n; ++i) {
       const sobel4_image &m = imgs[i];
       sobel4_status s = launch_one(h, m.src, m.src_pitch, m.dst, m.dst_pitch, m.height, m.width,

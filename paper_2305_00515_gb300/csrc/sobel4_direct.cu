@@ -1,11 +1,15 @@
 // sobel4_direct.cu — the DIRECT kernel: Eq. (3) summed tap by tap per output
 // pixel straight from global memory (the paper's "GM" baseline, Section 5.2).
+#include <cstring>
+
 #include "sobel4_launch.h"
 
 namespace sobel4 {
 
-template <int FMT>
-__global__ void __launch_bounds__(256) direct_kernel(ImageDesc im, int border) {
+// CUSTOM: the masks come from `m` (runtime weights, Eq. 5) instead of the
+// Eq. (3) table.
+template <int FMT, bool CUSTOM>
+__global__ void __launch_bounds__(256) direct_kernel(ImageDesc im, int border, Masks4 m) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int H = im.H, W = im.W;
@@ -24,7 +28,8 @@ __global__ void __launch_bounds__(256) direct_kernel(ImageDesc im, int border) {
         const int xx = map_index(x + j - 2, W, border, &zc);
         const int32_t v = (zr || zc) ? 0 : (int32_t)__ldg(row + xx);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) r[k] += (int32_t)kMasks[k][i][j] * v;
+        for (int k = 0; k < 4; ++k)
+          r[k] += (CUSTOM ? (int32_t)m.w[k][i][j] : (int32_t)kMasks[k][i][j]) * v;
       }
     }
   }
@@ -41,15 +46,23 @@ __global__ void __launch_bounds__(256) direct_kernel(ImageDesc im, int border) {
   }
 }
 
-cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, cudaStream_t st) {
+cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, const Masks4 *masks,
+                          cudaStream_t st) {
   const dim3 block(32, 8);
   const dim3 grid((im.W + 31) / 32, (im.H + 7) / 8);
+  Masks4 m;
+  if (masks) m = *masks;
+  else memset(&m, 0, sizeof(m));
   (void)cudaGetLastError();  // report this launch only, not an earlier failed call
+#define SOBEL4_DIRECT(F)                                                          \
+  (masks ? direct_kernel<F, true><<<grid, block, 0, st>>>(im, border, m)          \
+         : direct_kernel<F, false><<<grid, block, 0, st>>>(im, border, m))
   switch (fmt) {
-    case kF32: direct_kernel<kF32><<<grid, block, 0, st>>>(im, border); break;
-    case kU8: direct_kernel<kU8><<<grid, block, 0, st>>>(im, border); break;
-    default: direct_kernel<kS16x4><<<grid, block, 0, st>>>(im, border); break;
+    case kF32: SOBEL4_DIRECT(kF32); break;
+    case kU8: SOBEL4_DIRECT(kU8); break;
+    default: SOBEL4_DIRECT(kS16x4); break;
   }
+#undef SOBEL4_DIRECT
   return cudaGetLastError();
 }
 

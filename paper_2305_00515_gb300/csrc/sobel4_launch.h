@@ -72,12 +72,19 @@ cudaError_t tma_encode_2d(void *map, const void *base, bool f32, size_t pitch, i
 // CTA-local tile so that the waits run out.
 bool tc_eligible(const uint8_t *src, size_t sp, const void *dst, size_t dp, int32_t H, int32_t W,
                  int border, int fmt);
+// masks = nullptr: Eq. (3).
 cudaError_t launch_tc_single(const uint8_t *src, size_t sp, void *dst, size_t dp, int32_t H,
                              int32_t W, int border, int fmt, int sm_count, unsigned int *err,
-                             cudaStream_t st, int lose_tile = -1);
+                             cudaStream_t st, int lose_tile = -1, const Masks4 *masks = nullptr);
 
-// DIRECT kernel (one thread per output pixel).
-cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, cudaStream_t st);
+// DIRECT kernel (one thread per output pixel); masks = nullptr: Eq. (3).
+cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, const Masks4 *masks,
+                          cudaStream_t st);
+
+// The four masks of the generalised operator (Eq. 5) for parameters a, b, n,
+// m, built from its factored rows; false if a weight is not an integer or
+// does not fit in 16 bits.  (a, b, n, m) = (1, 2, 4, 6) gives Eq. (3).
+bool eq5_masks(double a, double b, double n, double m, Masks4 *out);
 
 // Self-check of the magnitude step over S in [s0, s1); mismatches added to *d_bad.
 cudaError_t launch_check_magnitude(int64_t s0, int64_t s1, unsigned long long *d_bad, int grid,

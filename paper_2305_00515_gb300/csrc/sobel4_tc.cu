@@ -2,6 +2,8 @@
 // maps (source: uint8 box 96 x 132; destination: float32 box 32 x 128 with the
 // 128-byte swizzle), the tile grid and the launch.
 #include <algorithm>
+#include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "sobel4_launch.h"
@@ -16,9 +18,40 @@ bool tc_eligible(const uint8_t *src, size_t sp, const void *dst, size_t dp, int3
          tma_eligible(src, sp) && (uintptr_t)dst % 16 == 0 && dp % 16 == 0;
 }
 
+bool eq5_masks(double a, double b, double n, double m, Masks4 *out) {
+  if (!(a > 0) || !(b > 0) || !(n > 0) || !(m > 0) || a != std::floor(a)) return false;
+  // Factored rows: K_x = a (v x h), K_y = a (h x v) with v = (1 n m n 1),
+  // h = (-1 -b 0 b 1); the diagonal pair through K_d+ = K_d + K_dt (rows
+  // -q0, -q1, 0, q1, q0) and K_d- = K_d - K_dt (rows r0, r1, r2, r1, r0), so
+  // that K_d = a (K_d+ + K_d-) / 2 and K_dt = a (K_d+ - K_d-) / 2.
+  const double v[5] = {1, n, m, n, 1}, h[5] = {-1, -b, 0, b, 1};
+  const double q0[5] = {m, n + b, 2, n + b, m};
+  const double q1[5] = {n - b, m * b, 2 * n * b, m * b, n - b};
+  const double r0[5] = {-m, b - n, 0, n - b, m};
+  const double r1[5] = {-(n + b), -m * b, 0, m * b, n + b};
+  const double r2[5] = {-2, -2 * n * b, 0, 2 * n * b, 2};
+  const double *dp_rows[5] = {q0, q1, nullptr, q1, q0};
+  const double dp_sign[5] = {-1, -1, 0, 1, 1};
+  const double *dm_rows[5] = {r0, r1, r2, r1, r0};
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) {
+      const double kdp = dp_rows[i] ? dp_sign[i] * dp_rows[i][j] : 0.0;
+      const double kdm = dm_rows[i][j];
+      const double w[4] = {a * v[i] * h[j], a * h[i] * v[j], a * (kdp + kdm) / 2,
+                           a * (kdp - kdm) / 2};
+      for (int k = 0; k < 4; ++k) {
+        const double r = std::nearbyint(w[k]);
+        if (std::fabs(w[k] - r) > 1e-9 * std::max(1.0, std::fabs(w[k])) || std::fabs(r) > 32767)
+          return false;
+        out->w[k][i][j] = (int16_t)r;
+      }
+    }
+  return true;
+}
+
 cudaError_t launch_tc_single(const uint8_t *src, size_t sp, void *dst, size_t dp, int32_t H,
                              int32_t W, int border, int fmt, int sm_count, unsigned int *err,
-                             cudaStream_t st, int lose_tile) {
+                             cudaStream_t st, int lose_tile, const Masks4 *masks) {
   if (!tc_eligible(src, sp, dst, dp, H, W, border, fmt)) return cudaErrorInvalidValue;
   alignas(64) CUtensorMap in_map, out_map;
   memset(&in_map, 0, sizeof(in_map));
@@ -41,7 +74,17 @@ cudaError_t launch_tc_single(const uint8_t *src, size_t sp, void *dst, size_t dp
   im.lose_tile = lose_tile;
   const int grid = (int)std::min<int64_t>(n_tiles, std::max(sm_count, 1));
   (void)cudaGetLastError();  // report this launch only, not an earlier failed call
-  tc::tc_single_kernel<kF32><<<grid, tc::kThreads, tc::kSmemBytes, st>>>(in_map, out_map, im, err);
+  static const Masks4 eq3 = [] {
+    Masks4 m;
+    eq5_masks(1, 2, 4, 6, &m);
+    return m;
+  }();
+  for (int k = 0; k < 4; ++k)  // the products hold weights up to 2048 exactly (f16)
+    for (int i = 0; i < 5; ++i)
+      for (int j = 0; j < 5; ++j)
+        if (masks && std::abs((int)masks->w[k][i][j]) > 2048) return cudaErrorInvalidValue;
+  tc::tc_single_kernel<kF32><<<grid, tc::kThreads, tc::kSmemBytes, st>>>(
+      in_map, out_map, im, masks ? *masks : eq3, err);
   return cudaGetLastError();
 }
 

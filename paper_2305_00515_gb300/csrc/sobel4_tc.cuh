@@ -18,7 +18,8 @@
 // row), so a view dy rows down is the same descriptor 16*dy bytes later.
 //
 // Exactness.  Inputs are staged as the f16 value 1024 + p (exact; the bias
-// cancels because every mask sums to zero), weights are small integers, and
+// cancels because every mask sums to zero: true of Eq. 3 and of every
+// operator of Eq. 5), weights are integers of at most 2048 in magnitude, and
 // each accumulator is preset to 1.5 * 2^23 (a tensor-memory store of the bit
 // pattern 0x4B400000), so every partial sum is an integer in [2^23, 2^24),
 // exact in fp32, and the final bits are 0x4B400000 + R.  The squares are
@@ -266,34 +267,18 @@ __device__ __forceinline__ void drain(uint32_t bar, uint32_t parity) {
   }
 }
 
-// The factored rows of the passes (Eq. 6-7, 12, 15, 18-19): smoothing,
-// derivative, q0', q1', r0', r2'.
-__constant__ int8_t kRows1x5[6][5] = {{1, 4, 6, 4, 1},  {-1, -2, 0, 2, 1}, {3, 3, 1, 3, 3},
-                                      {1, 6, 8, 6, 1},  {-3, -1, 0, 1, 3}, {-1, -8, 0, 8, 1}};
-
-// Weight of mask r (0: R_x, 1: R_y, 2: R_d, 3: R_dt) at row i, column j, built
-// from those rows (R_d = P' + M', R_dt = P' - M').
-__device__ __forceinline__ int mask_weight(int r, int i, int j) {
-  const int8_t *sm = kRows1x5[0], *df = kRows1x5[1], *q0 = kRows1x5[2], *q1 = kRows1x5[3];
-  const int8_t *r0 = kRows1x5[4], *r2 = kRows1x5[5];
-  if (r == 0) return sm[i] * df[j];
-  if (r == 1) return df[i] * sm[j];
-  const int p = i == 0 ? -q0[j] : i == 1 ? -q1[j] : i == 2 ? 0 : i == 3 ? q1[j] : q0[j];
-  const int m = (i == 0 || i == 4) ? r0[j] : (i == 2 ? r2[j] : 3 * df[j]);
-  return r == 2 ? p + m : p - m;
-}
-
 // Byte offset of element (row, k) in a K-major no-swizzle operand whose rows
 // are 16 bytes apart and whose 8-column groups are `lbo` bytes apart.
 __device__ __forceinline__ uint32_t op_off(int row, int k, uint32_t lbo) {
   return (uint32_t)(k >> 3) * lbo + (uint32_t)row * 16u + (uint32_t)(k & 7) * 2u;
 }
 
-__device__ __forceinline__ void fill_weights(uint8_t *smem) {
+// The five banded weight matrices B_dy[n = 4j + r][k] = K_r[dy][k - j].
+__device__ __forceinline__ void fill_weights(uint8_t *smem, const Masks4 &m) {
   for (int e = threadIdx.x; e < 5 * kN * 16; e += blockDim.x) {
     const int dy = e / (kN * 16), n = (e / 16) % kN, k = e % 16;
     const int j = n >> 2, r = n & 3, dx = k - j;
-    const float w = (dx >= 0 && dx <= 4) ? (float)mask_weight(r, dy, dx) : 0.0f;
+    const float w = (dx >= 0 && dx <= 4) ? (float)m.w[r][dy][dx] : 0.0f;
     *(__half *)(smem + kOffB + dy * kBMat + op_off(n, k, kN * 16)) = __float2half_rn(w);
   }
 }
@@ -349,7 +334,8 @@ __device__ __forceinline__ void stage_xtile(uint8_t *box, int row, int c, bool f
 template <int FMT>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_single_kernel(const __grid_constant__ CUtensorMap in_map,
-                     const __grid_constant__ CUtensorMap out_map, TcImage im, unsigned int *err) {
+                     const __grid_constant__ CUtensorMap out_map, TcImage im,
+                     const __grid_constant__ Masks4 masks, unsigned int *err) {
   static_assert(FMT == kF32, "tensor-core kernel: F32 output");
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned base (the swizzled staging boxes need it).
@@ -363,7 +349,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile uint32_t *abort = misc + 1;
   auto bar = [&](int which, int b) { return bar0 + 8u * (uint32_t)(which + b); };
 
-  fill_weights(smem);
+  fill_weights(smem, masks);
   if (tid == 0) {
     for (int u = 0; u < kUStages; ++u) {
       tma::mbar_init(bar(kUFull, u), 1);

@@ -1,0 +1,104 @@
+"""Runtime weights (the generalised operator of Eq. 5) through the C ABI,
+against the oracle's Eq. (5) masks, bit for bit.
+
+With weights other than Eq. (3), F32 VALID images with aligned rows run on the
+tensor-core kernel and everything else on the DIRECT kernel; batches run image
+by image.  Every border, format and a batch are covered for four weight sets,
+and (1, 2, 4, 6) must restore the register-window path and the Eq. (3)
+results.  Tolerance: zero mismatched elements, no write outside the payload.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2305_00515_gb300 as pkg
+import synth
+from gpu_util import run_placed
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+BORDERS = ("valid", "replicate", "reflect101", "constant0")
+FORMATS = ("f32", "u8", "s16x4")
+PARAMS = [(2, 0.5, 3, 4), (3, 1, 2, 5), (1, 3, 1, 1), (2, 1.5, 2, 2)]
+SHAPES = [(37, 61), (130, 256), (257, 300)]
+
+
+def ceil16(v):
+    return (v + 15) // 16 * 16
+
+
+def assert_same(got, want, what):
+    if not np.array_equal(got, want):
+        bad = np.argwhere(got != want)
+        raise AssertionError(f"{what}: {len(bad)} mismatches, first at {bad[:4].tolist()}")
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2305_00515_gb300 import build
+    build.build()
+
+
+@pytest.mark.parametrize("abnm", PARAMS, ids=lambda p: "a{}b{}n{}m{}".format(*p))
+@pytest.mark.parametrize("variant", ("auto", "direct"))
+def test_runtime_weights_match_oracle(built, abnm, variant):
+    K = oracle.eq5_masks(*abnm)
+    st, h = pkg.sobel4_create(0, pkg.VARIANTS[variant])
+    assert st == 0
+    try:
+        assert pkg.sobel4_set_weights(h, *abnm) == 0
+        for (H, W) in SHAPES:
+            img = synth.rects_noise(H, W, H * W)
+            for border in BORDERS:
+                for fmt in FORMATS:
+                    want = oracle.sobel4(img, border, fmt, masks=K)
+                    e = {"f32": 4, "u8": 1, "s16x4": 2}[fmt]
+                    for sp, dp in ((W, W * e), (ceil16(W), ceil16(W * e))):
+                        got, guards = run_placed(torch, h, img, border, fmt, src_pitch=sp,
+                                                 dst_pitch=dp)
+                        assert guards, f"{abnm} {H}x{W} {border} {fmt}: outside the payload"
+                        assert_same(got, want, f"{abnm} {variant} {H}x{W} {border} {fmt} sp {sp}")
+        assert pkg.sobel4_device_status(h) == 0
+    finally:
+        pkg.sobel4_destroy(h)
+
+
+def test_runtime_weights_batched_and_restore(built):
+    abnm = (2, 0.5, 3, 4)
+    K = oracle.eq5_masks(*abnm)
+    with pkg.Sobel4(0) as s:
+        s.set_weights(*abnm)
+        batch = [torch.from_numpy(synth.rects_noise(H, W, 3 + H)).cuda()
+                 for (H, W) in ((40, 64), (129, 300), (300, 512))]
+        outs = s.run_batched(batch, border="reflect101", fmt="f32")
+        big = torch.from_numpy(synth.rects_noise(1024, 2048, 5)).cuda()
+        out_big = s.run(big)  # VALID F32, aligned rows: the tensor-core kernel
+        torch.cuda.synchronize()
+        for b, o in zip(batch, outs):
+            assert_same(o.cpu().numpy(), oracle.sobel4(b.cpu().numpy(), "reflect101", "f32",
+                                                       masks=K), "batch")
+        assert_same(out_big.cpu().numpy(),
+                    oracle.sobel4(big.cpu().numpy(), "valid", "f32", masks=K,
+                                  threads=oracle.cpu_count()), "1024x2048")
+        s.set_weights()  # (1, 2, 4, 6): Eq. (3) again
+        out = s.run(big)
+        torch.cuda.synchronize()
+        assert_same(out.cpu().numpy(), oracle.sobel4(big.cpu().numpy(), "valid", "f32",
+                                                     threads=oracle.cpu_count()), "restored")
+
+
+def test_runtime_weights_rejected(built):
+    st, h = pkg.sobel4_create(0)
+    assert st == 0
+    try:
+        assert pkg.sobel4_set_weights(h, 1, 0.3, 4, 6) == 1      # k_ij not integers
+        assert pkg.sobel4_set_weights(h, 1.5, 2, 4, 6) == 1      # a not an integer
+        assert pkg.sobel4_set_weights(h, 1, 2, 0, 6) == 1        # n not positive
+        assert pkg.sobel4_set_weights(h, 8, 2, 4, 6) == 2        # S would overflow int32
+        # a rejected call leaves the weights as they were (Eq. 3)
+        img = synth.rects_noise(64, 64, 1)
+        got, _ = run_placed(torch, h, img, "valid", "f32")
+        assert_same(got, oracle.sobel4(img, "valid", "f32"), "unchanged")
+    finally:
+        pkg.sobel4_destroy(h)

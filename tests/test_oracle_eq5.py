@@ -1,0 +1,81 @@
+"""The oracle's generalised operator (Eq. 5, Section 3.2) against the paper's
+other statements of it and against a library correlation.
+
+Pins: (1, 2, 4, 6) gives the Eq. (3) tables; for general weights the sum and
+difference of the diagonal masks equal the K_d+ and K_d- matrices printed in
+Eq. (10), and K_d- equals the two outer products of Eq. (18) — different
+printed matrices, so a wrong entry in the Eq. (5) transcription fails them;
+K_y is the transpose of K_x and K_dt the left-right mirror of K_d; a linear
+ramp gives the closed form a (2 + 2n + m)(4 + 2b); and runs with the
+generated masks equal scipy.ndimage.correlate under every border rule.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import oracle_checks as oc
+
+PARAMS = [(1, 2, 4, 6), (2, 0.5, 3, 4), (3, 1, 2, 5), (1, 3, 1, 1), (2, 1.5, 2, 2)]
+
+
+@pytest.fixture(scope="module")
+def o():
+    return oracle.default()
+
+
+def test_defaults_are_eq3(o):
+    assert np.array_equal(o.eq5_masks(1, 2, 4, 6), o.masks())
+
+
+@pytest.mark.parametrize("abnm", PARAMS)
+def test_eq10_and_eq18_identities(o, abnm):
+    a, b, n, m = abnm
+    K = o.eq5_masks(a, b, n, m).astype(np.float64)
+    kp, km = oc.eq10_kd_plus_minus(a, b, m, n)
+    assert np.allclose(K[2] + K[3], kp), "K_d + K_dt must be the printed K_d+"
+    assert np.allclose(K[2] - K[3], km), "K_d - K_dt must be the printed K_d-"
+    assert np.allclose(K[2] - K[3], oc.eq18_kd_minus(a, b, m, n))
+    assert np.array_equal(K[1], K[0].T)
+    assert np.array_equal(K[3], K[2][:, ::-1])
+    assert all(K[k].sum() == 0 for k in range(4))
+
+
+@pytest.mark.parametrize("abnm", PARAMS)
+def test_ramp_closed_form(o, abnm):
+    a, b, n, m = abnm
+    K = o.eq5_masks(a, b, n, m)
+    H, W = 9, 12
+    ramp = np.tile(np.arange(W, dtype=np.uint8) * 3, (H, 1))
+    R = oc.scipy_responses(ramp, "valid", K)
+    want = 3 * a * (2 + 2 * n + m) * (4 + 2 * b)
+    assert (R[0][2:H - 2, 2:W - 2] == want).all()
+    assert (R[1][2:H - 2, 2:W - 2] == 0).all()
+
+
+@pytest.mark.parametrize("abnm", PARAMS[1:])
+def test_run_with_masks_matches_scipy(o, abnm):
+    K = o.eq5_masks(*abnm)
+    img = oc.rng_image(7, 23, 31)
+    for border in oc.BORDERS:
+        R = oc.scipy_responses(img, border, K).astype(np.int64)
+        S = (R ** 2).sum(axis=0)
+        assert S.max() < 2 ** 31
+        got = o.sobel4(img, border, "f32", masks=K)
+        assert np.array_equal(got, np.sqrt(S.astype(np.float32)).astype(np.float32)), border
+        s16 = o.sobel4(img, border, "s16x4", masks=K)
+        if np.abs(R).max() <= 32767:
+            assert np.array_equal(s16.astype(np.int64), R), border
+
+
+def test_eq3_masks_through_both_entry_points(o):
+    img = oc.rng_image(3, 17, 19)
+    for border in oc.BORDERS:
+        for fmt in ("f32", "u8", "s16x4"):
+            assert np.array_equal(o.sobel4(img, border, fmt),
+                                  o.sobel4(img, border, fmt, masks=o.masks()))
+
+
+def test_rejects_non_integer_weights(o):
+    for bad in ((1, 0.3, 4, 6), (1.5, 2, 4, 6), (0, 2, 4, 6), (1, -2, 4, 6), (1, 2, 4.5, 6)):
+        with pytest.raises(ValueError):
+            o.eq5_masks(*bad)

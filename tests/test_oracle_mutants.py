@@ -40,7 +40,7 @@ MUTANTS = {
     "gd_sign_flip": ("{-2, 0, 8, 12, 4},", "{-2, 0, 8, 12, -4},"),
     "gx_swapped_taps": ("{-4, -8, 0, 8, 4},\n     {-6", "{-8, -4, 0, 8, 4},\n     {-6"),
     "gdt_row_swap": ("{2, 0, -8, -12, -4},", "{0, 2, -8, -12, -4},"),
-    "transposed_mask": ("ORACLE_MASKS[k][i][j] * v", "ORACLE_MASKS[k][j][i] * v"),
+    "transposed_mask": ("r[k] += masks[k][i][j] * v", "r[k] += masks[k][j][i] * v"),
     "convolution_order": ("read_pixel(src, sp, H, W, y + i - 2, x + j - 2, border)",
                           "read_pixel(src, sp, H, W, y - i + 2, x - j + 2, border)"),
     "row_offset": ("sp, H, W, y + i - 2, x + j - 2, border);", "sp, H, W, y + i - 1, x + j - 2, border);"),
