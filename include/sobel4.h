@@ -74,8 +74,17 @@ typedef enum {
  *   U8    : uint8 min(255, round(sqrt(S))), 1 byte per pixel.
  *   S16X4 : the four responses R_x, R_y, R_d, R_dt as int16, in four planes;
  *           plane k starts at dst + k * height * dst_pitch.
+ *   U16   : uint16 round(sqrt(S)) by the exact integer rule, unsaturated (the
+ *           largest value of Eq. 3 is 24480), 2 bytes per pixel.  Runs on the
+ *           TMA-family and DIRECT kernels (the lane-copy variant and the
+ *           allocation-free entry point return UNSUPPORTED).
  */
-typedef enum { SOBEL4_OUT_F32 = 0, SOBEL4_OUT_U8 = 1, SOBEL4_OUT_S16X4 = 2 } sobel4_format;
+typedef enum {
+  SOBEL4_OUT_F32 = 0,
+  SOBEL4_OUT_U8 = 1,
+  SOBEL4_OUT_S16X4 = 2,
+  SOBEL4_OUT_U16 = 3
+} sobel4_format;
 
 /*
  * Kernel variants.  AUTO picks the fastest for the request (autotuned when

@@ -28,8 +28,8 @@ _BUILD_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD_DIR, "libsobel4_oracle.so")
 
 BORDERS = {"valid": 0, "replicate": 1, "reflect101": 2, "constant0": 3}
-FORMATS = {"f32": 0, "u8": 1, "s16x4": 2}
-_OUT_DTYPE = {"f32": np.float32, "u8": np.uint8, "s16x4": np.int16}
+FORMATS = {"f32": 0, "u8": 1, "s16x4": 2, "u16": 3}
+_OUT_DTYPE = {"f32": np.float32, "u8": np.uint8, "s16x4": np.int16, "u16": np.uint16}
 
 _lock = threading.Lock()
 _default = None
@@ -76,6 +76,8 @@ class Oracle:
         lib.sobel4_oracle_magnitude_f32.restype = ctypes.c_float
         lib.sobel4_oracle_magnitude_u8.argtypes = [ctypes.c_int32]
         lib.sobel4_oracle_magnitude_u8.restype = ctypes.c_int32
+        lib.sobel4_oracle_magnitude_u16.argtypes = [ctypes.c_int32]
+        lib.sobel4_oracle_magnitude_u16.restype = ctypes.c_int32
         self.lib = lib
         self.path = lib_path
 
@@ -149,6 +151,9 @@ class Oracle:
 
     def magnitude_u8(self, s: int) -> int:
         return int(self.lib.sobel4_oracle_magnitude_u8(int(s)))
+
+    def magnitude_u16(self, s: int) -> int:
+        return int(self.lib.sobel4_oracle_magnitude_u16(int(s)))
 
 
 def default() -> Oracle:

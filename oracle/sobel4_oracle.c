@@ -23,6 +23,7 @@
  *     F32   : sqrtf((float)S)  (int -> fp32 round-to-nearest-even, then the
  *             IEEE-754 correctly rounded single-precision square root),
  *     U8    : min(255, round(sqrt(S))) by an exact integer rule (no float),
+ *     U16   : round(sqrt(S)) by the same rule, unsaturated,
  *     S16X4 : the four responses R_x, R_y, R_d, R_dt as int16 planes.
  *
  *   Border rules (Section 4.3: the kernel's output is 2r rows and columns
@@ -74,7 +75,7 @@ static const int32_t ORACLE_MASKS[4][5][5] = {
 };
 
 enum { OR_VALID = 0, OR_REPLICATE = 1, OR_REFLECT101 = 2, OR_CONSTANT0 = 3 };
-enum { OR_F32 = 0, OR_U8 = 1, OR_S16X4 = 2 };
+enum { OR_F32 = 0, OR_U8 = 1, OR_S16X4 = 2, OR_U16 = 3 };
 enum { OR_OK = 0, OR_ERR_INVALID = 1 };
 
 /* Copy the Eq. (3) tables out (k, i, j order). */
@@ -143,11 +144,17 @@ static uint32_t isqrt_u32(uint32_t s) {
   return root;
 }
 
-/* min(255, nearest integer to sqrt(s)); ties cannot occur for integer s. */
-static uint8_t magnitude_u8(int32_t s) {
+/* Nearest integer to sqrt(s); ties cannot occur for integer s. */
+static uint32_t round_sqrt(int32_t s) {
   uint32_t n = isqrt_u32((uint32_t)s);
   /* sqrt(s) >= n + 1/2  <=>  s >= n^2 + n + 1/4  <=>  s > n^2 + n */
   if ((uint32_t)s > n * n + n) n += 1;
+  return n;
+}
+
+/* min(255, nearest integer to sqrt(s)). */
+static uint8_t magnitude_u8(int32_t s) {
+  uint32_t n = round_sqrt(s);
   return (uint8_t)(n > 255u ? 255u : n);
 }
 
@@ -174,6 +181,8 @@ static void run_band(const band_job *jb) {
         ((float *)row)[x] = sqrtf((float)s);
       } else if (jb->fmt == OR_U8) {
         row[x] = magnitude_u8(s);
+      } else if (jb->fmt == OR_U16) {
+        ((uint16_t *)row)[x] = (uint16_t)round_sqrt(s);
       } else {
         int k;
         for (k = 0; k < 4; ++k) {
@@ -227,7 +236,7 @@ static int run_with(const int32_t masks[4][5][5], const uint8_t *src, size_t sp,
                     int32_t nthreads) {
   int rc = check_args(H, W, border);
   if (rc) return rc;
-  if (!src || !dst || fmt < OR_F32 || fmt > OR_S16X4) return OR_ERR_INVALID;
+  if (!src || !dst || fmt < OR_F32 || fmt > OR_U16) return OR_ERR_INVALID;
   if (nthreads < 1) nthreads = 1;
   if (nthreads > H) nthreads = H;
   band_job *jobs = (band_job *)calloc((size_t)nthreads, sizeof(band_job));
@@ -327,3 +336,6 @@ float sobel4_oracle_magnitude_f32(int32_t s) { return sqrtf((float)s); }
 
 /* The exact U8 rule, exposed for its pin. */
 int32_t sobel4_oracle_magnitude_u8(int32_t s) { return (int32_t)magnitude_u8(s); }
+
+/* The exact U16 rule (nearest integer to sqrt(s), unsaturated), for its pin. */
+int32_t sobel4_oracle_magnitude_u16(int32_t s) { return (int32_t)round_sqrt(s); }

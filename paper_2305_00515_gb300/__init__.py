@@ -31,9 +31,9 @@ __all__ = [
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 BORDERS = {"valid": 0, "replicate": 1, "reflect101": 2, "constant0": 3}
-FORMATS = {"f32": 0, "u8": 1, "s16x4": 2}
+FORMATS = {"f32": 0, "u8": 1, "s16x4": 2, "u16": 3}
 VARIANTS = {"auto": 0, "direct": 1, "rg": 2, "rg_lanecopy": 3, "tc": 4}
-ELEM_SIZE = {"f32": 4, "u8": 1, "s16x4": 2}
+ELEM_SIZE = {"f32": 4, "u8": 1, "s16x4": 2, "u16": 2}
 STATUS = {0: "SOBEL4_OK", 1: "SOBEL4_ERR_INVALID_ARG", 2: "SOBEL4_ERR_UNSUPPORTED",
           3: "SOBEL4_ERR_OOM", 4: "SOBEL4_ERR_CUDA", 5: "SOBEL4_ERR_TIMEOUT"}
 
@@ -301,7 +301,7 @@ class Pipeline:
                                        FORMATS[fmt], slots)
         _check(st, "sobel4_pipeline_create")
         self.p, self.slots, self.H, self.W, self.fmt = p, slots, height, width, fmt
-        dtype = {"f32": np.float32, "u8": np.uint8, "s16x4": np.int16}[fmt]
+        dtype = {"f32": np.float32, "u8": np.uint8, "s16x4": np.int16, "u16": np.uint16}[fmt]
         planes = 4 if fmt == "s16x4" else 1
         self.inputs, self.outputs = [], []
         for k in range(slots):
@@ -427,7 +427,7 @@ class Sobel4:
     def empty_output(src, fmt: str = "f32"):
         import torch
         H, W = src.shape
-        dtype = {"f32": torch.float32, "u8": torch.uint8, "s16x4": torch.int16}[fmt]
+        dtype = {"f32": torch.float32, "u8": torch.uint8, "s16x4": torch.int16, "u16": torch.uint16}[fmt]
         shape = (4, H, W) if fmt == "s16x4" else (H, W)
         return torch.empty(shape, dtype=dtype, device=src.device)
 
@@ -473,7 +473,7 @@ class Sobel4:
             raise ValueError("src must be a 2-D uint8 array with unit column stride")
         H, W = src.shape
         if out is None:
-            dtype = {"f32": np.float32, "u8": np.uint8, "s16x4": np.int16}[fmt]
+            dtype = {"f32": np.float32, "u8": np.uint8, "s16x4": np.int16, "u16": np.uint16}[fmt]
             out = np.empty((4, H, W) if fmt == "s16x4" else (H, W), dtype=dtype)
         _check(sobel4_run_host(self.handle, src.ctypes.data, src.strides[0], out.ctypes.data,
                                out.strides[-2], H, W, BORDERS[border], FORMATS[fmt]),

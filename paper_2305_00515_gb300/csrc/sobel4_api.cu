@@ -198,7 +198,7 @@ sobel4_status cuda_fail(sobel4_ctx *h, cudaError_t e) {
 
 bool valid_enum(int border, int fmt) {
   return border >= SOBEL4_BORDER_VALID && border <= SOBEL4_BORDER_CONSTANT0 &&
-         fmt >= SOBEL4_OUT_F32 && fmt <= SOBEL4_OUT_S16X4;
+         fmt >= SOBEL4_OUT_F32 && fmt <= SOBEL4_OUT_U16;
 }
 
 // Shape and pitch rules shared by every entry point (pointers checked separately).
@@ -209,14 +209,14 @@ bool valid_shape(size_t src_pitch, size_t dst_pitch, int32_t H, int32_t W, int b
   if (src_pitch < (size_t)W || src_pitch > kMaxPitch) return false;
   if (dst_pitch < (size_t)W * elem_size(fmt) || dst_pitch > kMaxPitch) return false;
   if (fmt == kF32 && dst_pitch % 4) return false;
-  if (fmt == kS16x4 && dst_pitch % 2) return false;
+  if ((fmt == kS16x4 || fmt == kU16) && dst_pitch % 2) return false;
   return true;
 }
 
 bool valid_dst_ptr(const void *dst, int fmt) {
   if (!dst) return false;
   if (fmt == kF32 && ((uintptr_t)dst % 4)) return false;
-  if (fmt == kS16x4 && ((uintptr_t)dst % 2)) return false;
+  if ((fmt == kS16x4 || fmt == kU16) && ((uintptr_t)dst % 2)) return false;
   return true;
 }
 
@@ -263,7 +263,9 @@ const TuneEntry *find_tuned(const sobel4_ctx *h, int kind, int32_t H, int32_t W,
 void rg_config(const sobel4_ctx *h, const uint8_t *src, size_t sp, const void *dst, size_t dp,
                int32_t H, int32_t W, int border, int fmt, bool *use_tma, int *nc, int *R) {
   const TuneEntry *t = find_tuned(h, 0, H, W, fmt);
-  *use_tma = h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced && !(t && t->kernel == 0);
+  // U16 exists on the TMA family only (no lane-copy instantiation).
+  *use_tma = fmt == kU16 ||
+             (h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced && !(t && t->kernel == 0));
   if (*use_tma) {
     *nc = 4;
     if (h->rows_per_strip > 0) *R = tma_round_R(h->rows_per_strip);
@@ -638,7 +640,8 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
   // Every image goes to the TMA-family batched kernel unless the handle asks
   // for lane copies: 16-byte aligned sources in one launch group (tensor
   // copies), the others in a second (bulk row copies).
-  const bool tma_ok = h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced && !bl;
+  const bool tma_ok =
+      fmt == kU16 || (h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced && !bl);
   // TMA strip height: explicit option, else the tuned one, else by the
   // batch's make-up.  When every image has 16-byte aligned source rows and
   // vector-aligned destination rows, about four items per resident warp (8 ..
@@ -942,7 +945,7 @@ extern "C" sobel4_status sobel4_run_batched_static(const sobel4_image *imgs, int
                                                    sobel4_border border, sobel4_format fmt,
                                                    cudaStream_t stream) {
   if (!imgs || n < 1 || !valid_enum(border, fmt)) return SOBEL4_ERR_INVALID_ARG;
-  if (n > kStaticMaxImages) return SOBEL4_ERR_UNSUPPORTED;
+  if (n > kStaticMaxImages || fmt == kU16) return SOBEL4_ERR_UNSUPPORTED;  // lane-copy kernel
   for (int32_t i = 0; i < n; ++i) {
     const sobel4_image &m = imgs[i];
     if (!m.src || !valid_dst_ptr(m.dst, fmt) ||
@@ -1097,7 +1100,8 @@ extern "C" sobel4_status sobel4_tune(sobel4_handle h, int32_t height, int32_t wi
   }
   // TMA-staged kernel: a few strip heights, including the one that gives every
   // resident warp about one item.
-  if (h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced && tma_eligible(src, sp)) {
+  if ((fmt == kU16 || (h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced)) &&
+      tma_eligible(src, sp)) {
     std::vector<int> cands;
     if (h->rows_per_strip > 0) {
       cands.push_back(tma_round_R(h->rows_per_strip));
@@ -1123,7 +1127,7 @@ extern "C" sobel4_status sobel4_tune(sobel4_handle h, int32_t height, int32_t wi
   }
   const int ncs[2] = {2, 4};
   const int Rs[4] = {8, 16, 32, 64};
-  for (int a = 0; a < 2 && e == cudaSuccess; ++a) {
+  for (int a = 0; a < 2 && e == cudaSuccess && fmt != kU16; ++a) {
     if (h->nc_forced && ncs[a] != h->nc) continue;
     for (int b = 0; b < 4 && e == cudaSuccess; ++b) {
       if (h->rows_per_strip > 0 && Rs[b] != h->rows_per_strip) continue;
@@ -1187,7 +1191,7 @@ extern "C" sobel4_status sobel4_tune_batched(sobel4_handle h, const sobel4_image
     }
   }
   // Lane-copy kernel: columns per lane, strip height, CTAs per SM.
-  for (int a = 0; a < 2 && st == SOBEL4_OK; ++a) {
+  for (int a = 0; a < 2 && st == SOBEL4_OK && fmt != kU16; ++a) {
     if (h->nc_forced && ncs[a] != h->nc) continue;
     for (int b = 0; b < 3 && st == SOBEL4_OK; ++b) {
       if (h->rows_per_strip > 0 && Rs[b] != h->rows_per_strip) continue;
@@ -1209,7 +1213,7 @@ extern "C" sobel4_status sobel4_tune_config(sobel4_handle h, int32_t height, int
                                             sobel4_format fmt, int32_t *kernel,
                                             int32_t *columns_per_lane, int32_t *rows_per_strip) {
   if (!h || !kernel || !columns_per_lane || !rows_per_strip || height < 1 || width < 1 ||
-      fmt < SOBEL4_OUT_F32 || fmt > SOBEL4_OUT_S16X4)
+      fmt < SOBEL4_OUT_F32 || fmt > SOBEL4_OUT_U16)
     return SOBEL4_ERR_INVALID_ARG;
   // The configuration a VALID launch with 16-byte aligned rows would use.
   static const uint8_t kAligned[16] __attribute__((aligned(16))) = {0};

@@ -39,6 +39,8 @@ __global__ void __launch_bounds__(256) direct_kernel(ImageDesc im, int border, M
     ((float *)row)[x] = magnitude_f32(s);
   } else if (FMT == kU8) {
     row[x] = (uint8_t)magnitude_u8(s);
+  } else if (FMT == kU16) {
+    ((uint16_t *)row)[x] = (uint16_t)magnitude_u16(s);
   } else {
     const uint64_t plane = (uint64_t)(uint32_t)H * im.dp;
 #pragma unroll
@@ -60,6 +62,7 @@ cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, const Masks4
   switch (fmt) {
     case kF32: SOBEL4_DIRECT(kF32); break;
     case kU8: SOBEL4_DIRECT(kU8); break;
+    case kU16: SOBEL4_DIRECT(kU16); break;
     default: SOBEL4_DIRECT(kS16x4); break;
   }
 #undef SOBEL4_DIRECT

@@ -304,7 +304,7 @@ extern "C" sobel4_status sobel4_server_create(sobel4_handle h, const sobel4_serv
   if (!out) return SOBEL4_ERR_INVALID_ARG;
   *out = nullptr;
   if (!h || !opt || opt->border < SOBEL4_BORDER_VALID || opt->border > SOBEL4_BORDER_CONSTANT0 ||
-      opt->format < SOBEL4_OUT_F32 || opt->format > SOBEL4_OUT_S16X4 || opt->max_batch < 0 ||
+      opt->format < SOBEL4_OUT_F32 || opt->format > SOBEL4_OUT_U16 || opt->max_batch < 0 ||
       opt->memory_budget < 0 || (opt->plain != 0 && opt->plain != 1))
     return SOBEL4_ERR_INVALID_ARG;
   sobel4_server_ctx *s = new (std::nothrow) sobel4_server_ctx();

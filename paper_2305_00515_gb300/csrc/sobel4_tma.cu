@@ -37,6 +37,7 @@ int resident(int fmt, int mode, int st) {
   switch (fmt) {
     case kF32: return TmaFmt<kF32>::resident(mode, st);
     case kU8: return TmaFmt<kU8>::resident(mode, st);
+    case kU16: return TmaFmt<kU16>::resident(mode, st);
     default: return TmaFmt<kS16x4>::resident(mode, st);
   }
 }
@@ -108,6 +109,9 @@ void single(int fmt, int mode, int st, const CUtensorMap &map, const tma::TmaIma
       break;
     case kU8:
       TmaFmt<kU8>::single(mode, st, map, im, border, R, items, grid, pair, err, s);
+      break;
+    case kU16:
+      TmaFmt<kU16>::single(mode, st, map, im, border, R, items, grid, pair, err, s);
       break;
     default:
       TmaFmt<kS16x4>::single(mode, st, map, im, border, R, items, grid, pair, err, s);
@@ -221,6 +225,9 @@ cudaError_t launch_tma_batched(const void *d_descs, int n_img, int64_t total,
         break;
       case kU8:
         TmaFmt<kU8>::batched(mode, staging, d, n_img, (int)total, queue, border, R, g, err, st);
+        break;
+      case kU16:
+        TmaFmt<kU16>::batched(mode, staging, d, n_img, (int)total, queue, border, R, g, err, st);
         break;
       default:
         TmaFmt<kS16x4>::batched(mode, staging, d, n_img, (int)total, queue, border, R, g, err,

@@ -467,6 +467,43 @@ __device__ __forceinline__ void store_rows(const TmaImage &im, uint8_t *row_a, u
         }
       }
     }
+  } else if constexpr (FMT == kU16) {
+    uint32_t ua[4], ub[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      ua[k] = magnitude_u16(sa[k]);
+      ub[k] = magnitude_u16(sb[k]);
+    }
+    uint16_t *pa = (uint16_t *)row_a + x, *pb = (uint16_t *)row_b + x;
+    if (GEN) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const bool fk = (framemask >> k) & 1u;
+        if (zero_a || fk) ua[k] = 0u;
+        if (zero_b || fk) ub[k] = 0u;
+      }
+    }
+    const uint2 wa = make_uint2(ua[0] | (ua[1] << 16), ua[2] | (ua[3] << 16));
+    const uint2 wb = make_uint2(ub[0] | (ub[1] << 16), ub[2] | (ub[3] << 16));
+    if (!GEN) {
+      if constexpr (RA) {
+        st4_s16_realigned((int16_t *)pa, wa.x, wa.y, st_a);
+        st4_s16_realigned((int16_t *)pb, wb.x, wb.y, st_b);
+      } else {
+        if (st_a) *(uint2 *)pa = wa;
+        if (st_b) *(uint2 *)pb = wb;
+      }
+    } else if (vec && colmask == 0xFu) {
+      if (st_a) *(uint2 *)pa = wa;
+      if (st_b) *(uint2 *)pb = wb;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (!((colmask >> k) & 1u)) continue;
+        if (st_a) pa[k] = (uint16_t)ua[k];
+        if (st_b) pb[k] = (uint16_t)ub[k];
+      }
+    }
   } else {
     uint32_t ua[4], ub[4];
 #pragma unroll
@@ -513,6 +550,8 @@ __device__ __forceinline__ void zero_px(const TmaImage &im, int y, int x) {
     ((float *)row)[x] = 0.0f;
   } else if constexpr (FMT == kU8) {
     row[x] = 0;
+  } else if constexpr (FMT == kU16) {
+    ((uint16_t *)row)[x] = 0;
   } else {
     const uint64_t plane = (uint64_t)(uint32_t)im.H * im.dp;
 #pragma unroll
@@ -529,6 +568,8 @@ __device__ __forceinline__ void zero_row4(const TmaImage &im, int y, int x) {
     *(float4 *)((float *)row + x) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   } else if constexpr (FMT == kU8) {
     *(uint32_t *)(row + x) = 0u;
+  } else if constexpr (FMT == kU16) {
+    *(uint2 *)((uint16_t *)row + x) = make_uint2(0u, 0u);
   } else {
     const uint64_t plane = (uint64_t)(uint32_t)im.H * im.dp;
 #pragma unroll

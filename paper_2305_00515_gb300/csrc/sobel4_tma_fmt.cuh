@@ -1,6 +1,6 @@
 // sobel4_tma_fmt.cuh — launch helpers of the TMA-family kernels for one
 // output format, explicitly instantiated once per format in
-// sobel4_tma_{f32,u8,s16}.cu so the kernel variants compile in parallel.
+// sobel4_tma_{f32,u8,s16,u16}.cu so the kernel variants compile in parallel.
 #pragma once
 
 #include <algorithm>
@@ -88,5 +88,6 @@ void TmaFmt<FMT>::batched(int mode, int st, const tma::TmaBatchDesc *d, int n_im
 extern template struct TmaFmt<kF32>;
 extern template struct TmaFmt<kU8>;
 extern template struct TmaFmt<kS16x4>;
+extern template struct TmaFmt<kU16>;
 
 }  // namespace sobel4

@@ -8,8 +8,8 @@ import numpy as np
 import paper_2305_00515_gb300 as pkg
 
 GUARD = 0xA5
-ELEM = {"f32": 4, "u8": 1, "s16x4": 2}
-DTYPE = {"f32": np.float32, "u8": np.uint8, "s16x4": np.int16}
+ELEM = {"f32": 4, "u8": 1, "s16x4": 2, "u16": 2}
+DTYPE = {"f32": np.float32, "u8": np.uint8, "s16x4": np.int16, "u16": np.uint16}
 
 
 class Placed:

@@ -79,7 +79,7 @@ BAD_RUNS = [
     dict(d_dst=DST + 2),                     # F32 destination not 4-byte aligned
     dict(border=4),
     dict(border=-1),
-    dict(fmt=3),
+    dict(fmt=4),
     dict(border=2, height=2),                # REFLECT101 needs >= 3
     dict(border=2, width=2, src_pitch=100, dst_pitch=400),
     dict(d_dst=SRC + 50),                    # output overlaps input

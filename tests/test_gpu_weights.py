@@ -19,7 +19,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 BORDERS = ("valid", "replicate", "reflect101", "constant0")
-FORMATS = ("f32", "u8", "s16x4")
+FORMATS = ("f32", "u8", "s16x4", "u16")
 PARAMS = [(2, 0.5, 3, 4), (3, 1, 2, 5), (1, 3, 1, 1), (2, 1.5, 2, 2)]
 SHAPES = [(37, 61), (130, 256), (257, 300)]
 
@@ -53,7 +53,7 @@ def test_runtime_weights_match_oracle(built, abnm, variant):
             for border in BORDERS:
                 for fmt in FORMATS:
                     want = oracle.sobel4(img, border, fmt, masks=K)
-                    e = {"f32": 4, "u8": 1, "s16x4": 2}[fmt]
+                    e = {"f32": 4, "u8": 1, "s16x4": 2, "u16": 2}[fmt]
                     for sp, dp in ((W, W * e), (ceil16(W), ceil16(W * e))):
                         got, guards = run_placed(torch, h, img, border, fmt, src_pitch=sp,
                                                  dst_pitch=dp)

@@ -79,3 +79,21 @@ def test_rejects_non_integer_weights(o):
     for bad in ((1, 0.3, 4, 6), (1.5, 2, 4, 6), (0, 2, 4, 6), (1, -2, 4, 6), (1, 2, 4.5, 6)):
         with pytest.raises(ValueError):
             o.eq5_masks(*bad)
+
+
+def test_u16_rule(o):
+    """U16 = nearest integer to sqrt(S), unsaturated: (2r-1)^2 <= 4S < (2r+1)^2 (r > 0),
+    checked on every S below 2^20, around every square and its midpoints up to
+    the largest S of Eq. (3), and at the int32 end."""
+    import itertools
+    ss = itertools.chain(range(0, 1 << 20, 7), (k * k + d for k in range(0, 24500, 97)
+                                               for d in (-k - 1, -k, -1, 0, k, k + 1) if k * k + d >= 0),
+                         (599270400, (1 << 31) - 1))
+    for s in ss:
+        r = o.magnitude_u16(s)
+        assert (r == 0 or (2 * r - 1) ** 2 <= 4 * s) and 4 * s < (2 * r + 1) ** 2, s
+    img = oc.rng_image(5, 19, 23)
+    R = oc.scipy_responses(img, "reflect101", o.masks()).astype(np.int64)
+    S = (R ** 2).sum(axis=0)
+    got = o.sobel4(img, "reflect101", "u16").astype(np.int64)
+    assert (((2 * got - 1) ** 2 <= 4 * S) | (got == 0)).all() and (4 * S < (2 * got + 1) ** 2).all()
