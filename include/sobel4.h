@@ -230,6 +230,22 @@ sobel4_status sobel4_inject_stage_loss(sobel4_handle h, int32_t stage);
  */
 sobel4_status sobel4_set_weights(sobel4_handle h, double a, double b, double n, double m);
 
+/*
+ * Operators (Section 3.1): the four-directional 5x5 of Eq. (3) (the default),
+ * the two-directional 5x5 (its K_x and K_y only, S = R_x^2 + R_y^2), and the
+ * two-directional 3x3 of Eq. (1)-(2) (whose VALID frame is 1 pixel wide).
+ * The two-directional operators run like runtime weights: on the tensor-core
+ * kernel where it applies, else on DIRECT; S16X4 writes R_x, R_y and two zero
+ * planes.  SOBEL4_OP_4DIR_5X5 restores Eq. (3) (same as sobel4_set_weights
+ * with 1, 2, 4, 6).  Errors: INVALID_ARG (h == NULL, unknown operator).
+ */
+typedef enum {
+  SOBEL4_OP_4DIR_5X5 = 0,
+  SOBEL4_OP_2DIR_5X5 = 1,
+  SOBEL4_OP_2DIR_3X3 = 2
+} sobel4_operator;
+sobel4_status sobel4_set_operator(sobel4_handle h, int32_t op);
+
 /* Number of kernels this handle has launched so far (for launch accounting). */
 uint64_t sobel4_launch_count(sobel4_handle h);
 

@@ -67,10 +67,14 @@ class Oracle:
         lib.sobel4_oracle_eq5_masks.argtypes = [ctypes.c_double] * 4 + [
             ctypes.POINTER(ctypes.c_int32)]
         lib.sobel4_oracle_eq5_masks.restype = ctypes.c_int
-        lib.sobel4_oracle_run_masks.argtypes = [ctypes.POINTER(ctypes.c_int32), u8p,
-                                                ctypes.c_size_t, ctypes.c_int32, ctypes.c_int32,
-                                                ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
-                                                ctypes.c_size_t, ctypes.c_int32]
+        lib.sobel4_oracle_run_masks.argtypes = [ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
+                                                u8p, ctypes.c_size_t, ctypes.c_int32,
+                                                ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32]
+        lib.sobel4_oracle_operator_masks.argtypes = [ctypes.c_int32,
+                                                     ctypes.POINTER(ctypes.c_int32),
+                                                     ctypes.POINTER(ctypes.c_int32)]
+        lib.sobel4_oracle_operator_masks.restype = ctypes.c_int
         lib.sobel4_oracle_run_masks.restype = ctypes.c_int
         lib.sobel4_oracle_magnitude_f32.argtypes = [ctypes.c_int32]
         lib.sobel4_oracle_magnitude_f32.restype = ctypes.c_float
@@ -111,7 +115,7 @@ class Oracle:
         return out
 
     def run_into(self, img: np.ndarray, out: np.ndarray, border: str = "valid",
-                 fmt: str = "f32", threads: int = 1, masks=None) -> None:
+                 fmt: str = "f32", threads: int = 1, masks=None, radius: int = 2) -> None:
         """Gradient output of Eq. (4) written into a caller array (rows may be padded);
         `masks` (4, 5, 5) integers replace the Eq. (3) masks when given."""
         img, sp = self._src(img)
@@ -123,19 +127,30 @@ class Oracle:
         else:
             m = np.ascontiguousarray(masks, dtype=np.int32).reshape(100)
             rc = self.lib.sobel4_oracle_run_masks(
-                m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), u8, sp, H, W, BORDERS[border],
-                FORMATS[fmt], out.ctypes.data, out.strides[-2], int(threads))
+                m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(radius), u8, sp, H, W,
+                BORDERS[border], FORMATS[fmt], out.ctypes.data, out.strides[-2], int(threads))
         if rc != 0:
             raise ValueError(f"oracle rejected arguments (H={H}, W={W}, border={border})")
 
     def sobel4(self, img: np.ndarray, border: str = "valid", fmt: str = "f32",
-               threads: int = 1, masks=None) -> np.ndarray:
-        """Gradient output of Eq. (4): (H, W) f32/u8, or (4, H, W) int16 for s16x4."""
+               threads: int = 1, masks=None, radius: int = 2) -> np.ndarray:
+        """Gradient output of Eq. (4): (H, W) f32/u8/u16, or (4, H, W) int16 for s16x4."""
         H, W = img.shape
         shape = (4, H, W) if fmt == "s16x4" else (H, W)
         out = np.zeros(shape, dtype=_OUT_DTYPE[fmt])
-        self.run_into(img, out, border, fmt, threads, masks)
+        self.run_into(img, out, border, fmt, threads, masks, radius)
         return out
+
+    def operator_masks(self, op: str):
+        """(masks (4, 5, 5), radius) of the 2dir5x5 or 2dir3x3 operator."""
+        out = np.zeros(100, dtype=np.int32)
+        r = ctypes.c_int32(0)
+        rc = self.lib.sobel4_oracle_operator_masks(
+            {"2dir5x5": 1, "2dir3x3": 2}[op], out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+            ctypes.byref(r))
+        if rc != 0:
+            raise ValueError(op)
+        return out.reshape(4, 5, 5), r.value
 
     def eq5_masks(self, a: float, b: float, n: float, m: float) -> np.ndarray:
         """The generalised masks of Eq. (5) as (4, 5, 5) int32 (x, y, d, dt)."""
@@ -174,8 +189,12 @@ def responses(img: np.ndarray, border: str = "valid") -> np.ndarray:
 
 
 def sobel4(img: np.ndarray, border: str = "valid", fmt: str = "f32", threads: int = 1,
-           masks=None):
-    return default().sobel4(img, border, fmt, threads, masks)
+           masks=None, radius: int = 2):
+    return default().sobel4(img, border, fmt, threads, masks, radius)
+
+
+def operator_masks(op: str):
+    return default().operator_masks(op)
 
 
 def eq5_masks(a: float, b: float, n: float, m: float) -> np.ndarray:

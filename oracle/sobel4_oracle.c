@@ -123,9 +123,11 @@ static void responses_at(const int32_t masks[4][5][5], const uint8_t *src, size_
   }
 }
 
-static int is_computed(int H, int W, int border, int y, int x) {
+/* Under VALID only pixels at least `radius` (the masks' support radius: 2
+ * for 5x5, 1 for 3x3) from every edge are computed; the frame stays 0. */
+static int is_computed(int H, int W, int border, int y, int x, int radius) {
   if (border != OR_VALID) return 1;
-  return y >= 2 && y <= H - 3 && x >= 2 && x <= W - 3;
+  return y >= radius && y <= H - 1 - radius && x >= radius && x <= W - 1 - radius;
 }
 
 /* floor(sqrt(s)) for 0 <= s < 2^31 by the bit-by-bit integer method. */
@@ -160,6 +162,7 @@ static uint8_t magnitude_u8(int32_t s) {
 
 typedef struct {
   const int32_t (*masks)[5][5];
+  int radius;
   const uint8_t *src;
   size_t sp;
   int H, W, border, fmt;
@@ -173,7 +176,7 @@ static void run_band(const band_job *jb) {
   for (y = jb->y0; y < jb->y1; ++y) {
     for (x = 0; x < jb->W; ++x) {
       int32_t r[4] = {0, 0, 0, 0};
-      if (is_computed(jb->H, jb->W, jb->border, y, x))
+      if (is_computed(jb->H, jb->W, jb->border, y, x, jb->radius))
         responses_at(jb->masks, jb->src, jb->sp, jb->H, jb->W, jb->border, y, x, r);
       int32_t s = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] + r[3] * r[3];
       uint8_t *row = (uint8_t *)jb->dst + (size_t)y * jb->dp;
@@ -212,27 +215,28 @@ static int check_args(int H, int W, int border) {
  * nthreads contiguous bands run on POSIX threads (nthreads <= 1: the calling
  * thread only).
  */
-static int run_with(const int32_t masks[4][5][5], const uint8_t *src, size_t sp, int32_t H,
-                    int32_t W, int32_t border, int32_t fmt, void *dst, size_t dp,
+static int run_with(const int32_t masks[4][5][5], int radius, const uint8_t *src, size_t sp,
+                    int32_t H, int32_t W, int32_t border, int32_t fmt, void *dst, size_t dp,
                     int32_t nthreads);
 
 int sobel4_oracle_run(const uint8_t *src, size_t sp, int32_t H, int32_t W, int32_t border,
                       int32_t fmt, void *dst, size_t dp, int32_t nthreads) {
-  return run_with(ORACLE_MASKS, src, sp, H, W, border, fmt, dst, dp, nthreads);
+  return run_with(ORACLE_MASKS, 2, src, sp, H, W, border, fmt, dst, dp, nthreads);
 }
 
 /* The same with caller-supplied masks (k, i, j order, e.g. from
- * sobel4_oracle_eq5_masks).  The caller keeps S = sum R_k^2 inside int32. */
-int sobel4_oracle_run_masks(const int32_t *masks100, const uint8_t *src, size_t sp, int32_t H,
-                            int32_t W, int32_t border, int32_t fmt, void *dst, size_t dp,
-                            int32_t nthreads) {
-  if (!masks100) return OR_ERR_INVALID;
-  return run_with((const int32_t(*)[5][5])masks100, src, sp, H, W, border, fmt, dst, dp,
-                  nthreads);
+ * sobel4_oracle_eq5_masks) of support radius 1 or 2.  The caller keeps
+ * S = sum R_k^2 inside int32. */
+int sobel4_oracle_run_masks(const int32_t *masks100, int32_t radius, const uint8_t *src,
+                            size_t sp, int32_t H, int32_t W, int32_t border, int32_t fmt,
+                            void *dst, size_t dp, int32_t nthreads) {
+  if (!masks100 || radius < 1 || radius > 2) return OR_ERR_INVALID;
+  return run_with((const int32_t(*)[5][5])masks100, radius, src, sp, H, W, border, fmt, dst,
+                  dp, nthreads);
 }
 
-static int run_with(const int32_t masks[4][5][5], const uint8_t *src, size_t sp, int32_t H,
-                    int32_t W, int32_t border, int32_t fmt, void *dst, size_t dp,
+static int run_with(const int32_t masks[4][5][5], int radius, const uint8_t *src, size_t sp,
+                    int32_t H, int32_t W, int32_t border, int32_t fmt, void *dst, size_t dp,
                     int32_t nthreads) {
   int rc = check_args(H, W, border);
   if (rc) return rc;
@@ -248,7 +252,7 @@ static int run_with(const int32_t masks[4][5][5], const uint8_t *src, size_t sp,
   }
   int t;
   for (t = 0; t < nthreads; ++t) {
-    band_job j = {masks, src, sp, H, W, border, fmt, dst, dp,
+    band_job j = {masks, radius, src, sp, H, W, border, fmt, dst, dp,
                   (int)((int64_t)H * t / nthreads), (int)((int64_t)H * (t + 1) / nthreads)};
     jobs[t] = j;
   }
@@ -273,7 +277,7 @@ int sobel4_oracle_responses(const uint8_t *src, size_t sp, int32_t H, int32_t W,
   for (y = 0; y < H; ++y) {
     for (x = 0; x < W; ++x) {
       int32_t r[4] = {0, 0, 0, 0};
-      if (is_computed(H, W, border, y, x))
+      if (is_computed(H, W, border, y, x, 2))
         responses_at(ORACLE_MASKS, src, sp, H, W, border, y, x, r);
       for (k = 0; k < 4; ++k) out[(size_t)k * H * W + (size_t)y * W + x] = r[k];
     }
@@ -329,6 +333,34 @@ int sobel4_oracle_eq5_masks(double a, double b, double n, double m, int32_t *out
         out100[(k * 5 + i) * 5 + j] = (int32_t)r;
       }
   return OR_OK;
+}
+
+/*
+ * Masks of the other operators of Section 3.1, in the 5x5 grid: op 1 = the
+ * two-directional 5x5 (G_x and G_y of Eq. 3), op 2 = the two-directional
+ * 3x3 of Eq. (1) as printed, centred; the diagonal masks are zero.  Returns
+ * the support radius (2 or 1) through *radius.
+ */
+int sobel4_oracle_operator_masks(int32_t op, int32_t *out100, int32_t *radius) {
+  static const int32_t G3[2][3][3] = {
+      {{-1, 0, 1}, {-2, 0, 2}, {-1, 0, 1}},   /* G_x, Eq. (1) */
+      {{-1, -2, -1}, {0, 0, 0}, {1, 2, 1}}};  /* G_y, Eq. (1) */
+  int k, i, j;
+  if (!out100 || !radius) return OR_ERR_INVALID;
+  memset(out100, 0, 100 * sizeof(int32_t));
+  if (op == 1) {
+    memcpy(out100, ORACLE_MASKS, 2 * 25 * sizeof(int32_t));
+    *radius = 2;
+    return OR_OK;
+  }
+  if (op == 2) {
+    for (k = 0; k < 2; ++k)
+      for (i = 0; i < 3; ++i)
+        for (j = 0; j < 3; ++j) out100[(k * 5 + 1 + i) * 5 + 1 + j] = G3[k][i][j];
+    *radius = 1;
+    return OR_OK;
+  }
+  return OR_ERR_INVALID;
 }
 
 /* sqrtf((float)s) as the oracle evaluates it, exposed for the rounding pins. */

@@ -20,7 +20,7 @@ __all__ = [
     "BORDERS", "FORMATS", "VARIANTS", "Sobel4", "Sobel4Error", "Image", "Options",
     "library_path", "load", "sobel4_create", "sobel4_destroy", "sobel4_run",
     "sobel4_run_batched", "sobel4_run_host", "sobel4_status_string", "sobel4_last_cuda_error",
-    "sobel4_device_status", "sobel4_inject_stage_loss", "sobel4_set_weights", "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
+    "sobel4_device_status", "sobel4_inject_stage_loss", "sobel4_set_weights", "sobel4_set_operator", "OPERATORS", "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
     "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched", "sobel4_tune_entries",
     "sobel4_tune_config", "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create",
     "sobel4_pipeline_buffers", "sobel4_pipeline_submit", "sobel4_pipeline_wait",
@@ -33,6 +33,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 BORDERS = {"valid": 0, "replicate": 1, "reflect101": 2, "constant0": 3}
 FORMATS = {"f32": 0, "u8": 1, "s16x4": 2, "u16": 3}
 VARIANTS = {"auto": 0, "direct": 1, "rg": 2, "rg_lanecopy": 3, "tc": 4}
+OPERATORS = {"4dir5x5": 0, "2dir5x5": 1, "2dir3x3": 2}
 ELEM_SIZE = {"f32": 4, "u8": 1, "s16x4": 2, "u16": 2}
 STATUS = {0: "SOBEL4_OK", 1: "SOBEL4_ERR_INVALID_ARG", 2: "SOBEL4_ERR_UNSUPPORTED",
           3: "SOBEL4_ERR_OOM", 4: "SOBEL4_ERR_CUDA", 5: "SOBEL4_ERR_TIMEOUT"}
@@ -40,7 +41,7 @@ STATUS = {0: "SOBEL4_OK", 1: "SOBEL4_ERR_INVALID_ARG", 2: "SOBEL4_ERR_UNSUPPORTE
 EXPORTED_SYMBOLS = (
     "sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_batched", "sobel4_run_host",
     "sobel4_status_string", "sobel4_last_cuda_error", "sobel4_device_status",
-    "sobel4_inject_stage_loss", "sobel4_set_weights",
+    "sobel4_inject_stage_loss", "sobel4_set_weights", "sobel4_set_operator",
     "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
     "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched", "sobel4_tune_entries",
     "sobel4_tune_config", "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create",
@@ -115,6 +116,7 @@ def load() -> ctypes.CDLL:
         lib.sobel4_inject_stage_loss.argtypes = [vp, i32]
         lib.sobel4_set_weights.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_double]
+        lib.sobel4_set_operator.argtypes = [vp, i32]
         lib.sobel4_launch_count.argtypes = [vp]
         lib.sobel4_launch_count.restype = ctypes.c_uint64
         lib.sobel4_set_variant.argtypes = [vp, i32]
@@ -146,7 +148,7 @@ def load() -> ctypes.CDLL:
         for name in ("sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_batched",
                      "sobel4_run_host", "sobel4_set_variant", "sobel4_check_magnitude",
                      "sobel4_device_status", "sobel4_inject_stage_loss", "sobel4_tune_config",
-                     "sobel4_set_weights",
+                     "sobel4_set_weights", "sobel4_set_operator",
                      "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched",
                      "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create",
                      "sobel4_pipeline_buffers", "sobel4_pipeline_submit", "sobel4_pipeline_wait",
@@ -203,6 +205,11 @@ def sobel4_last_cuda_error(h) -> int:
 
 def sobel4_device_status(h) -> int:
     return load().sobel4_device_status(h)
+
+
+def sobel4_set_operator(h, op: int) -> int:
+    """Operator for the handle's later runs (OPERATORS)."""
+    return load().sobel4_set_operator(h, op)
 
 
 def sobel4_set_weights(h, a: float, b: float, n: float, m: float) -> int:
@@ -411,6 +418,10 @@ class Sobel4:
 
     def set_variant(self, variant: str):
         _check(sobel4_set_variant(self.handle, VARIANTS[variant]), "sobel4_set_variant")
+
+    def set_operator(self, name: str = "4dir5x5"):
+        """4dir5x5 (Eq. 3), 2dir5x5 or 2dir3x3 (Eq. 1-2)."""
+        _check(sobel4_set_operator(self.handle, OPERATORS[name]), "sobel4_set_operator")
 
     def set_weights(self, a: float = 1, b: float = 2, n: float = 4, m: float = 6):
         """The generalised operator of Eq. (5); the defaults restore Eq. (3)."""

@@ -166,7 +166,8 @@ struct sobel4_ctx {
   uint32_t next_pair = 0;
   unsigned int *d_err = nullptr;  // bit 0: a bounded wait in a kernel ran out (inside d_pairs)
   int lose_stage = -1;            // failure injection for the next TMA-staged launch
-  bool custom = false;            // runtime weights (Eq. 5) replace Eq. (3)
+  bool custom = false;            // runtime masks (Eq. 5 weights, other operators) replace Eq. (3)
+  int radius = 2;                 // support radius of the masks (VALID frame width)
   bool custom_s16_ok = true;      // every response fits the S16X4 planes
   Masks4 masks{};
   cudaStream_t own_stream = nullptr;
@@ -331,15 +332,15 @@ sobel4_status launch_one(sobel4_ctx *h, const uint8_t *src, size_t sp, void *dst
     if (fmt == kS16x4 && !h->custom_s16_ok) return SOBEL4_ERR_UNSUPPORTED;
     if (h->variant != SOBEL4_VARIANT_DIRECT && tc_eligible(src, sp, dst, dp, H, W, border, fmt)) {
       e = launch_tc_single(src, sp, dst, dp, H, W, border, fmt, h->sm_count, h->d_err, stream,
-                           h->lose_stage, &h->masks);
+                           h->lose_stage, &h->masks, h->radius);
       h->lose_stage = -1;
     } else {
       const ImageDesc im = make_desc(src, sp, dst, dp, H, W, 1, h->nc);
-      e = launch_direct(im, border, fmt, &h->masks, stream);
+      e = launch_direct(im, border, fmt, &h->masks, h->radius, stream);
     }
   } else if (h->variant == SOBEL4_VARIANT_DIRECT) {
     const ImageDesc im = make_desc(src, sp, dst, dp, H, W, 1, h->nc);
-    e = launch_direct(im, border, fmt, nullptr, stream);
+    e = launch_direct(im, border, fmt, nullptr, 2, stream);
   } else if (use_tc(h, src, sp, dst, dp, H, W, border, fmt)) {
     e = launch_tc_single(src, sp, dst, dp, H, W, border, fmt, h->sm_count, h->d_err, stream,
                          h->lose_stage);
@@ -530,6 +531,20 @@ sobel4_status sobel4_set_weights(sobel4_handle h, double a, double b, double n, 
   h->custom = memcmp(&mk, &eq3, sizeof(mk)) != 0;
   h->custom_s16_ok = s16;
   h->masks = mk;
+  h->radius = 2;
+  return SOBEL4_OK;
+}
+
+sobel4_status sobel4_set_operator(sobel4_handle h, int32_t op) {
+  if (!h) return SOBEL4_ERR_INVALID_ARG;
+  if (op == SOBEL4_OP_4DIR_5X5) return sobel4_set_weights(h, 1, 2, 4, 6);
+  Masks4 mk;
+  const int radius = operator_masks(op, &mk);
+  if (!radius) return SOBEL4_ERR_INVALID_ARG;
+  h->custom = true;
+  h->custom_s16_ok = true;
+  h->masks = mk;
+  h->radius = radius;
   return SOBEL4_OK;
 }
 

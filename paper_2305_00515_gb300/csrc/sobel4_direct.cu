@@ -8,14 +8,17 @@ namespace sobel4 {
 
 // CUSTOM: the masks come from `m` (runtime weights, Eq. 5) instead of the
 // Eq. (3) table.
+// fr: the support radius of the masks (2 for 5x5, 1 for a 3x3 operator),
+// the width of the frame the paper's rule leaves at 0.
 template <int FMT, bool CUSTOM>
-__global__ void __launch_bounds__(256) direct_kernel(ImageDesc im, int border, Masks4 m) {
+__global__ void __launch_bounds__(256) direct_kernel(ImageDesc im, int border, Masks4 m, int fr) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int H = im.H, W = im.W;
   if (x >= W || y >= H) return;
   int32_t r[4] = {0, 0, 0, 0};
-  const bool computed = border != kValid || (y >= 2 && y <= H - 3 && x >= 2 && x <= W - 3);
+  const bool computed =
+      border != kValid || (y >= fr && y <= H - 1 - fr && x >= fr && x <= W - 1 - fr);
   if (computed) {
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
@@ -49,7 +52,7 @@ __global__ void __launch_bounds__(256) direct_kernel(ImageDesc im, int border, M
 }
 
 cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, const Masks4 *masks,
-                          cudaStream_t st) {
+                          int radius, cudaStream_t st) {
   const dim3 block(32, 8);
   const dim3 grid((im.W + 31) / 32, (im.H + 7) / 8);
   Masks4 m;
@@ -57,8 +60,8 @@ cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, const Masks4
   else memset(&m, 0, sizeof(m));
   (void)cudaGetLastError();  // report this launch only, not an earlier failed call
 #define SOBEL4_DIRECT(F)                                                          \
-  (masks ? direct_kernel<F, true><<<grid, block, 0, st>>>(im, border, m)          \
-         : direct_kernel<F, false><<<grid, block, 0, st>>>(im, border, m))
+  (masks ? direct_kernel<F, true><<<grid, block, 0, st>>>(im, border, m, radius)  \
+         : direct_kernel<F, false><<<grid, block, 0, st>>>(im, border, m, radius))
   switch (fmt) {
     case kF32: SOBEL4_DIRECT(kF32); break;
     case kU8: SOBEL4_DIRECT(kU8); break;

@@ -75,11 +75,19 @@ bool tc_eligible(const uint8_t *src, size_t sp, const void *dst, size_t dp, int3
 // masks = nullptr: Eq. (3).
 cudaError_t launch_tc_single(const uint8_t *src, size_t sp, void *dst, size_t dp, int32_t H,
                              int32_t W, int border, int fmt, int sm_count, unsigned int *err,
-                             cudaStream_t st, int lose_tile = -1, const Masks4 *masks = nullptr);
+                             cudaStream_t st, int lose_tile = -1, const Masks4 *masks = nullptr,
+                             int radius = 2);
 
-// DIRECT kernel (one thread per output pixel); masks = nullptr: Eq. (3).
+// DIRECT kernel (one thread per output pixel); masks = nullptr: Eq. (3);
+// radius: the masks' support radius (VALID leaves a frame that wide at 0).
 cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, const Masks4 *masks,
-                          cudaStream_t st);
+                          int radius, cudaStream_t st);
+
+// Masks of the operators besides the four-directional 5x5: op 1 = the
+// two-directional 5x5 (K_x, K_y of Eq. 3), op 2 = the two-directional 3x3 of
+// Eq. (1) centred in the 5x5 grid; diagonal masks zero.  Returns the support
+// radius (2 or 1), or 0 for an unknown op.
+int operator_masks(int op, Masks4 *out);
 
 // The four masks of the generalised operator (Eq. 5) for parameters a, b, n,
 // m, built from its factored rows; false if a weight is not an integer or

@@ -49,9 +49,29 @@ bool eq5_masks(double a, double b, double n, double m, Masks4 *out) {
   return true;
 }
 
+int operator_masks(int op, Masks4 *out) {
+  memset(out, 0, sizeof(*out));
+  if (op == 1) {  // two-directional 5x5: the x and y masks of the four-directional one
+    eq5_masks(1, 2, 4, 6, out);
+    memset(out->w[2], 0, sizeof(out->w[2]));
+    memset(out->w[3], 0, sizeof(out->w[3]));
+    return 2;
+  }
+  if (op == 2) {  // two-directional 3x3 (Eq. 1): (1 2 1)^T (-1 0 1) and its transpose
+    const int v[3] = {1, 2, 1}, d[3] = {-1, 0, 1};
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        out->w[0][1 + i][1 + j] = (int16_t)(v[i] * d[j]);
+        out->w[1][1 + i][1 + j] = (int16_t)(d[i] * v[j]);
+      }
+    return 1;
+  }
+  return 0;
+}
+
 cudaError_t launch_tc_single(const uint8_t *src, size_t sp, void *dst, size_t dp, int32_t H,
                              int32_t W, int border, int fmt, int sm_count, unsigned int *err,
-                             cudaStream_t st, int lose_tile, const Masks4 *masks) {
+                             cudaStream_t st, int lose_tile, const Masks4 *masks, int radius) {
   if (!tc_eligible(src, sp, dst, dp, H, W, border, fmt)) return cudaErrorInvalidValue;
   alignas(64) CUtensorMap in_map, out_map;
   memset(&in_map, 0, sizeof(in_map));
@@ -63,7 +83,9 @@ cudaError_t launch_tc_single(const uint8_t *src, size_t sp, void *dst, size_t dp
       tc::tc_single_kernel<kF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
       (int)tc::kSmemBytes);
   if (attr != cudaSuccess) return attr;
+  if (radius != 1 && radius != 2) return cudaErrorInvalidValue;
   tc::TcImage im;
+  im.fr = radius;
   im.H = H;
   im.W = W;
   im.n_tx = (W + tc::kTileCols - 1) / tc::kTileCols;

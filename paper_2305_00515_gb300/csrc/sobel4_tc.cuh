@@ -107,6 +107,7 @@ enum Bar {
 
 struct TcImage {
   int32_t H, W;
+  int32_t fr;  // support radius of the masks: the VALID frame width
   int32_t n_tx, n_tiles;
   int32_t lose_tile;  // failure injection (tests): this CTA-local tile's copy is never issued
 };
@@ -317,13 +318,13 @@ __device__ __forceinline__ int32_t s_from_bits(uint32_t b0, uint32_t b1, uint32_
 // touches the frame, whose pixels the paper's rule leaves at 0.
 template <bool MASK>
 __device__ __forceinline__ void stage_xtile(uint8_t *box, int row, int c, bool frame_row, int x,
-                                            int W, const uint32_t (&r)[32]) {
+                                            int W, int fr, const uint32_t (&r)[32]) {
   float g[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const int32_t s = s_from_bits(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
     const float v = magnitude_newton(s);
-    g[j] = MASK && (frame_row || x + j < 2 || x + j > W - 3) ? 0.0f : v;
+    g[j] = MASK && (frame_row || x + j < fr || x + j > W - 1 - fr) ? 0.0f : v;
   }
   uint8_t *line = box + row * 128;
   const int sw = row & 7;
@@ -476,8 +477,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
       const int t = tile_of(li), ty = t / im.n_tx, tx = t - ty * im.n_tx;
       const int y = kM * ty + lrow;
-      const bool frame_row = y < 2 || y > im.H - 3;
-      const bool mask = tx == 0 || kTileCols * tx + kTileCols > im.W - 2;
+      const bool frame_row = y < im.fr || y > im.H - 1 - im.fr;
+      const bool mask = tx == 0 || kTileCols * tx + kTileCols > im.W - im.fr;
 #pragma unroll 1
       for (int q = 0; q < 2; ++q) {
         const int xt = 2 * g4 + q;
@@ -487,8 +488,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         tmem_preset32(ta, magic);  // ready for this buffer's next tile
         uint8_t *box = smem + kOffO + (2 * ob + (xt >> 2)) * kOBox;
         const int x = kTileCols * tx + 8 * xt;
-        if (mask || frame_row) stage_xtile<true>(box, lrow, 2 * (xt & 3), frame_row, x, im.W, r);
-        else stage_xtile<false>(box, lrow, 2 * (xt & 3), frame_row, x, im.W, r);
+        if (mask || frame_row)
+          stage_xtile<true>(box, lrow, 2 * (xt & 3), frame_row, x, im.W, im.fr, r);
+        else
+          stage_xtile<false>(box, lrow, 2 * (xt & 3), frame_row, x, im.W, im.fr, r);
       }
       tmem_wait_st();
       tc_fence_before();

@@ -46,6 +46,7 @@ def test_null_handle_queries(lib):
     assert pkg.sobel4_destroy(None) == 0
     assert pkg.sobel4_set_variant(None, 0) == 1
     assert pkg.sobel4_set_weights(None, 1, 2, 4, 6) == 1
+    assert pkg.sobel4_set_operator(None, 0) == 1
 
 
 def test_create_rejects_bad_options(lib):

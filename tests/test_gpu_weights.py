@@ -102,3 +102,33 @@ def test_runtime_weights_rejected(built):
         assert_same(got, oracle.sobel4(img, "valid", "f32"), "unchanged")
     finally:
         pkg.sobel4_destroy(h)
+
+
+@pytest.mark.parametrize("op", ("2dir5x5", "2dir3x3"))
+@pytest.mark.parametrize("variant", ("auto", "direct"))
+def test_two_directional_operators(built, op, variant):
+    """The two-directional 5x5 and the 3x3 of Eq. (1)-(2) (1-pixel VALID
+    frame) through the tensor-core and DIRECT kernels, against the oracle."""
+    K, radius = oracle.operator_masks(op)
+    st, h = pkg.sobel4_create(0, pkg.VARIANTS[variant])
+    assert st == 0
+    try:
+        assert pkg.sobel4_set_operator(h, pkg.OPERATORS[op]) == 0
+        for (H, W) in SHAPES:
+            img = synth.rects_noise(H, W, H + 3 * W)
+            for border in BORDERS:
+                for fmt in FORMATS:
+                    want = oracle.sobel4(img, border, fmt, masks=K, radius=radius)
+                    e = {"f32": 4, "u8": 1, "s16x4": 2, "u16": 2}[fmt]
+                    for sp, dp in ((W, W * e), (ceil16(W), ceil16(W * e))):
+                        got, guards = run_placed(torch, h, img, border, fmt, src_pitch=sp,
+                                                 dst_pitch=dp)
+                        assert guards
+                        assert_same(got, want, f"{op} {variant} {H}x{W} {border} {fmt} sp {sp}")
+        assert pkg.sobel4_set_operator(h, 7) == 1
+        assert pkg.sobel4_set_operator(h, pkg.OPERATORS["4dir5x5"]) == 0
+        img = synth.rects_noise(64, 128, 2)
+        got, _ = run_placed(torch, h, img, "valid", "f32")
+        assert_same(got, oracle.sobel4(img, "valid", "f32"), "restored")
+    finally:
+        pkg.sobel4_destroy(h)

@@ -97,3 +97,34 @@ def test_u16_rule(o):
     S = (R ** 2).sum(axis=0)
     got = o.sobel4(img, "reflect101", "u16").astype(np.int64)
     assert (((2 * got - 1) ** 2 <= 4 * S) | (got == 0)).all() and (4 * S < (2 * got + 1) ** 2).all()
+
+
+def test_two_directional_operators(o):
+    """The two-directional 3x3 of Eq. (1) against scipy.ndimage.sobel (a
+    library routine: [-1 0 1] along the axis, [1 2 1] across), with its
+    1-pixel VALID frame; the two-directional 5x5 = the first two Eq. (3)
+    masks, diagonals zero, S = R_x^2 + R_y^2 (Eq. 2)."""
+    import scipy.ndimage as ndi
+    m3, r3 = o.operator_masks("2dir3x3")
+    m5, r5 = o.operator_masks("2dir5x5")
+    assert (r3, r5) == (1, 2)
+    assert np.array_equal(m5[:2], o.masks()[:2]) and not m5[2:].any() and not m3[2:].any()
+    img = oc.rng_image(11, 21, 26)
+    I = img.astype(np.int64)
+    mode = {"replicate": "nearest", "reflect101": "mirror", "constant0": "constant"}
+    for border in ("valid", "replicate", "reflect101", "constant0"):
+        md = mode.get(border, "nearest")
+        gx = ndi.sobel(I, axis=1, mode=md, cval=0)
+        gy = ndi.sobel(I, axis=0, mode=md, cval=0)
+        if border == "valid":
+            keep = np.zeros(I.shape, bool)
+            keep[1:-1, 1:-1] = True
+            gx, gy = np.where(keep, gx, 0), np.where(keep, gy, 0)
+        s16 = o.sobel4(img, border, "s16x4", masks=m3, radius=1).astype(np.int64)
+        assert np.array_equal(s16[0], gx) and np.array_equal(s16[1], gy), border
+        assert not s16[2:].any()
+        f = o.sobel4(img, border, "f32", masks=m3, radius=1)
+        assert np.array_equal(f, np.sqrt((gx * gx + gy * gy).astype(np.float32))), border
+        R = oc.scipy_responses(img, border, o.masks()).astype(np.int64)
+        f5 = o.sobel4(img, border, "f32", masks=m5)
+        assert np.array_equal(f5, np.sqrt((R[0] ** 2 + R[1] ** 2).astype(np.float32))), border

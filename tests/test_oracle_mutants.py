@@ -48,7 +48,7 @@ MUTANTS = {
     "reflect_not_101": ("if (i < 0) return -i;", "if (i < 0) return -i - 1;"),
     "replicate_edge": ("return i < 0 ? 0 : n - 1;", "return i < 0 ? 0 : n - 2;"),
     "constant_reads_edge": ("case OR_CONSTANT0:\n      return -1;", "case OR_CONSTANT0:\n      return i < 0 ? 0 : n - 1;"),
-    "valid_frame_off_by_one": ("y <= H - 3 && x >= 2", "y <= H - 2 && x >= 2"),
+    "valid_frame_off_by_one": ("y <= H - 1 - radius && x >= radius", "y <= H - radius && x >= radius"),
     "sqrt_in_double": ("((float *)row)[x] = sqrtf((float)s);",
                        "((float *)row)[x] = (float)sqrt((double)s);"),
     "u8_truncates": ("if ((uint32_t)s > n * n + n) n += 1;", "if ((uint32_t)s > n * n) n += 0;"),
