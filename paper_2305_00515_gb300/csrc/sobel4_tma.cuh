@@ -1,5 +1,5 @@
-// sobel4_tma.cuh — TMA-staged register-window kernel for single images whose
-// rows start on 16-byte boundaries (sm_103a).
+// sobel4_tma.cuh — TMA-family register-window kernels (sm_103a): single
+// images and batches, any row alignment.
 //
 // The operator is that of sobel4_device.cuh (Section 3.1, Eq. 3 and Eq. 4);
 // the schedule is the paper's register-window design (Section 4.3) rebuilt
@@ -8,24 +8,28 @@
 //  * Work item = one warp: a 128-column segment and a band of 2R rows, split
 //    into two strips of R rows that travel together in the two 16-bit halves
 //    of every register (v = lo + 65536 * hi, lo = strip a, hi = strip b).  The
-//    host sizes R so that the items fill every resident warp about once, which
-//    keeps the 4-row window fill of each strip (Section 4.3.2) near 3 % of
-//    the rows.
-//  * Staging: lane 0 of each warp issues 2-D tensor copies (cp.async.bulk.tensor,
-//    TMA) of 8 rows x 160 bytes per strip into a 3-slot shared-memory ring,
-//    completing on one mbarrier per slot; rows and columns outside the image
-//    arrive as zeros from the copy engine, which is the CONSTANT0 rule and
-//    harmless under VALID.  Under REPLICATE / REFLECT101 the lanes whose
-//    columns cross the left or right edge read their bytes from the staged row
-//    at the mapped columns, and rows outside the image are gathered from the
-//    mapped rows in global memory.  This is the prefetch of Section 4.3.4, two
-//    stages (16 rows) ahead.
+//    host sizes R (about two items per resident warp for images whose items
+//    all take the fast path, more otherwise; or the tuned value); a last band
+//    with fewer than 2R rows is split evenly between its strips.  Items are
+//    handed out edge items first (item_coords).
+//  * Staging into a 3-slot per-warp shared-memory ring completed by one
+//    mbarrier per slot, two stages (16 rows) ahead: the prefetch of Section
+//    4.3.4.  Tensor staging (rows on 16-byte boundaries): lane 0 issues 2-D
+//    tensor copies (cp.async.bulk.tensor, TMA) of 8 rows x 160 bytes per
+//    strip; rows and columns outside the image arrive as zeros.  Bulk staging
+//    (any other source): 16 lanes each copy the 16-byte granules of one row
+//    (cp.async.bulk) and record that row's byte offset.
 //  * Per new row each column runs the packed passes of sobel4_arith.cuh
-//    (Eq. 6-19), then the squares (Eq. 4) and the square root, and each lane
-//    stores four results per strip row with one vector store.
-//  * Border rules on the fast path: the copy engine's zero fill is the
-//    CONSTANT0 rule; under VALID the lane that stored a frame element
-//    overwrites it with 0 after the row loop.
+//    (Eq. 6-19), then the squares (Eq. 4) and the magnitude, and each lane
+//    stores four results per strip row with one vector store (lane-shifted
+//    aligned stores when the destination rows are not vector-aligned).
+//  * Border rules: on the fast path the zero fill is the CONSTANT0 rule and,
+//    under VALID, the lane that stored a frame element overwrites it with 0
+//    after the row loop; edge items of REPLICATE / REFLECT101 (and of bulk
+//    staging) read the mapped columns from the staged row and gather rows
+//    outside the image from their mapped rows.
+//  * Kernel modes: fast items only (the lean kernel), general items only, or
+//    both in one kernel.
 #pragma once
 
 #include <cuda.h>
