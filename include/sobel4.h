@@ -78,12 +78,17 @@ typedef enum {
  *           largest value of Eq. 3 is 24480), 2 bytes per pixel.  Runs on the
  *           TMA-family and DIRECT kernels (the lane-copy variant and the
  *           allocation-free entry point return UNSUPPORTED).
+ *   EDGE8 : uint8 edge map, 255 where sqrt(S) >= T (exactly: S >= ceil(T^2))
+ *           and 0 elsewhere (the VALID frame is 0); T is the handle's
+ *           threshold (sobel4_set_threshold, 128 by default); 1 byte per
+ *           pixel.  Same kernels as U16.
  */
 typedef enum {
   SOBEL4_OUT_F32 = 0,
   SOBEL4_OUT_U8 = 1,
   SOBEL4_OUT_S16X4 = 2,
-  SOBEL4_OUT_U16 = 3
+  SOBEL4_OUT_U16 = 3,
+  SOBEL4_OUT_EDGE8 = 4
 } sobel4_format;
 
 /*
@@ -245,6 +250,13 @@ typedef enum {
   SOBEL4_OP_2DIR_3X3 = 2
 } sobel4_operator;
 sobel4_status sobel4_set_operator(sobel4_handle h, int32_t op);
+
+/*
+ * Threshold T >= 0 of the EDGE8 output for this handle's later runs
+ * (default 128): a pixel is 255 where sqrt(S) >= T.
+ * Errors: INVALID_ARG (h == NULL, T negative, not a number, or above 46341).
+ */
+sobel4_status sobel4_set_threshold(sobel4_handle h, double t);
 
 /* Number of kernels this handle has launched so far (for launch accounting). */
 uint64_t sobel4_launch_count(sobel4_handle h);

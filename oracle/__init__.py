@@ -28,8 +28,10 @@ _BUILD_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD_DIR, "libsobel4_oracle.so")
 
 BORDERS = {"valid": 0, "replicate": 1, "reflect101": 2, "constant0": 3}
-FORMATS = {"f32": 0, "u8": 1, "s16x4": 2, "u16": 3}
-_OUT_DTYPE = {"f32": np.float32, "u8": np.uint8, "s16x4": np.int16, "u16": np.uint16}
+FORMATS = {"f32": 0, "u8": 1, "s16x4": 2, "u16": 3, "edge8": 4}
+_OUT_DTYPE = {"f32": np.float32, "u8": np.uint8, "s16x4": np.int16, "u16": np.uint16,
+              "edge8": np.uint8}
+DEFAULT_THRESHOLD = 128
 
 _lock = threading.Lock()
 _default = None
@@ -68,7 +70,8 @@ class Oracle:
             ctypes.POINTER(ctypes.c_int32)]
         lib.sobel4_oracle_eq5_masks.restype = ctypes.c_int
         lib.sobel4_oracle_run_masks.argtypes = [ctypes.POINTER(ctypes.c_int32), ctypes.c_int32,
-                                                u8p, ctypes.c_size_t, ctypes.c_int32,
+                                                ctypes.c_int64, u8p, ctypes.c_size_t,
+                                                ctypes.c_int32,
                                                 ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                 ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32]
         lib.sobel4_oracle_operator_masks.argtypes = [ctypes.c_int32,
@@ -115,30 +118,35 @@ class Oracle:
         return out
 
     def run_into(self, img: np.ndarray, out: np.ndarray, border: str = "valid",
-                 fmt: str = "f32", threads: int = 1, masks=None, radius: int = 2) -> None:
+                 fmt: str = "f32", threads: int = 1, masks=None, radius: int = 2,
+                 threshold=None) -> None:
         """Gradient output of Eq. (4) written into a caller array (rows may be padded);
         `masks` (4, 5, 5) integers replace the Eq. (3) masks when given."""
         img, sp = self._src(img)
         H, W = img.shape
         u8 = img.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        if masks is None and fmt == "edge8":
+            masks = self.masks()
         if masks is None:
             rc = self.lib.sobel4_oracle_run(u8, sp, H, W, BORDERS[border], FORMATS[fmt],
                                             out.ctypes.data, out.strides[-2], int(threads))
         else:
             m = np.ascontiguousarray(masks, dtype=np.int32).reshape(100)
             rc = self.lib.sobel4_oracle_run_masks(
-                m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(radius), u8, sp, H, W,
-                BORDERS[border], FORMATS[fmt], out.ctypes.data, out.strides[-2], int(threads))
+                m.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(radius),
+                edge_threshold(DEFAULT_THRESHOLD if threshold is None else threshold), u8, sp,
+                H, W, BORDERS[border], FORMATS[fmt], out.ctypes.data, out.strides[-2],
+                int(threads))
         if rc != 0:
             raise ValueError(f"oracle rejected arguments (H={H}, W={W}, border={border})")
 
     def sobel4(self, img: np.ndarray, border: str = "valid", fmt: str = "f32",
-               threads: int = 1, masks=None, radius: int = 2) -> np.ndarray:
+               threads: int = 1, masks=None, radius: int = 2, threshold=None) -> np.ndarray:
         """Gradient output of Eq. (4): (H, W) f32/u8/u16, or (4, H, W) int16 for s16x4."""
         H, W = img.shape
         shape = (4, H, W) if fmt == "s16x4" else (H, W)
         out = np.zeros(shape, dtype=_OUT_DTYPE[fmt])
-        self.run_into(img, out, border, fmt, threads, masks, radius)
+        self.run_into(img, out, border, fmt, threads, masks, radius, threshold)
         return out
 
     def operator_masks(self, op: str):
@@ -189,8 +197,16 @@ def responses(img: np.ndarray, border: str = "valid") -> np.ndarray:
 
 
 def sobel4(img: np.ndarray, border: str = "valid", fmt: str = "f32", threads: int = 1,
-           masks=None, radius: int = 2):
-    return default().sobel4(img, border, fmt, threads, masks, radius)
+           masks=None, radius: int = 2, threshold=None):
+    return default().sobel4(img, border, fmt, threads, masks, radius, threshold)
+
+
+def edge_threshold(t) -> int:
+    """ceil(t^2) for the EDGE8 rule sqrt(S) >= t, in exact rational arithmetic."""
+    from fractions import Fraction
+    import math
+    q = Fraction(t) ** 2
+    return math.ceil(q)
 
 
 def operator_masks(op: str):

@@ -24,6 +24,7 @@
  *             IEEE-754 correctly rounded single-precision square root),
  *     U8    : min(255, round(sqrt(S))) by an exact integer rule (no float),
  *     U16   : round(sqrt(S)) by the same rule, unsaturated,
+ *     EDGE8 : 255 where S >= thr (thr = ceil(T^2) for a threshold T), else 0,
  *     S16X4 : the four responses R_x, R_y, R_d, R_dt as int16 planes.
  *
  *   Border rules (Section 4.3: the kernel's output is 2r rows and columns
@@ -75,7 +76,7 @@ static const int32_t ORACLE_MASKS[4][5][5] = {
 };
 
 enum { OR_VALID = 0, OR_REPLICATE = 1, OR_REFLECT101 = 2, OR_CONSTANT0 = 3 };
-enum { OR_F32 = 0, OR_U8 = 1, OR_S16X4 = 2, OR_U16 = 3 };
+enum { OR_F32 = 0, OR_U8 = 1, OR_S16X4 = 2, OR_U16 = 3, OR_EDGE8 = 4 };
 enum { OR_OK = 0, OR_ERR_INVALID = 1 };
 
 /* Copy the Eq. (3) tables out (k, i, j order). */
@@ -163,6 +164,7 @@ static uint8_t magnitude_u8(int32_t s) {
 typedef struct {
   const int32_t (*masks)[5][5];
   int radius;
+  int64_t thr;
   const uint8_t *src;
   size_t sp;
   int H, W, border, fmt;
@@ -186,6 +188,10 @@ static void run_band(const band_job *jb) {
         row[x] = magnitude_u8(s);
       } else if (jb->fmt == OR_U16) {
         ((uint16_t *)row)[x] = (uint16_t)round_sqrt(s);
+      } else if (jb->fmt == OR_EDGE8) {
+        /* sqrt(S) >= T  <=>  S >= T^2  <=>  S >= thr = ceil(T^2); frame 0 */
+        row[x] = (is_computed(jb->H, jb->W, jb->border, y, x, jb->radius) && s >= jb->thr)
+                     ? 255 : 0;
       } else {
         int k;
         for (k = 0; k < 4; ++k) {
@@ -215,32 +221,33 @@ static int check_args(int H, int W, int border) {
  * nthreads contiguous bands run on POSIX threads (nthreads <= 1: the calling
  * thread only).
  */
-static int run_with(const int32_t masks[4][5][5], int radius, const uint8_t *src, size_t sp,
-                    int32_t H, int32_t W, int32_t border, int32_t fmt, void *dst, size_t dp,
-                    int32_t nthreads);
+static int run_with(const int32_t masks[4][5][5], int radius, int64_t thr, const uint8_t *src,
+                    size_t sp, int32_t H, int32_t W, int32_t border, int32_t fmt, void *dst,
+                    size_t dp, int32_t nthreads);
 
 int sobel4_oracle_run(const uint8_t *src, size_t sp, int32_t H, int32_t W, int32_t border,
                       int32_t fmt, void *dst, size_t dp, int32_t nthreads) {
-  return run_with(ORACLE_MASKS, 2, src, sp, H, W, border, fmt, dst, dp, nthreads);
+  if (fmt == OR_EDGE8) return OR_ERR_INVALID; /* needs a threshold: run_masks */
+  return run_with(ORACLE_MASKS, 2, 0, src, sp, H, W, border, fmt, dst, dp, nthreads);
 }
 
 /* The same with caller-supplied masks (k, i, j order, e.g. from
- * sobel4_oracle_eq5_masks) of support radius 1 or 2.  The caller keeps
- * S = sum R_k^2 inside int32. */
-int sobel4_oracle_run_masks(const int32_t *masks100, int32_t radius, const uint8_t *src,
-                            size_t sp, int32_t H, int32_t W, int32_t border, int32_t fmt,
-                            void *dst, size_t dp, int32_t nthreads) {
+ * sobel4_oracle_eq5_masks) of support radius 1 or 2, and for EDGE8 the
+ * threshold thr on S.  The caller keeps S = sum R_k^2 inside int32. */
+int sobel4_oracle_run_masks(const int32_t *masks100, int32_t radius, int64_t thr,
+                            const uint8_t *src, size_t sp, int32_t H, int32_t W, int32_t border,
+                            int32_t fmt, void *dst, size_t dp, int32_t nthreads) {
   if (!masks100 || radius < 1 || radius > 2) return OR_ERR_INVALID;
-  return run_with((const int32_t(*)[5][5])masks100, radius, src, sp, H, W, border, fmt, dst,
-                  dp, nthreads);
+  return run_with((const int32_t(*)[5][5])masks100, radius, thr, src, sp, H, W, border, fmt,
+                  dst, dp, nthreads);
 }
 
-static int run_with(const int32_t masks[4][5][5], int radius, const uint8_t *src, size_t sp,
-                    int32_t H, int32_t W, int32_t border, int32_t fmt, void *dst, size_t dp,
-                    int32_t nthreads) {
+static int run_with(const int32_t masks[4][5][5], int radius, int64_t thr, const uint8_t *src,
+                    size_t sp, int32_t H, int32_t W, int32_t border, int32_t fmt, void *dst,
+                    size_t dp, int32_t nthreads) {
   int rc = check_args(H, W, border);
   if (rc) return rc;
-  if (!src || !dst || fmt < OR_F32 || fmt > OR_U16) return OR_ERR_INVALID;
+  if (!src || !dst || fmt < OR_F32 || fmt > OR_EDGE8) return OR_ERR_INVALID;
   if (nthreads < 1) nthreads = 1;
   if (nthreads > H) nthreads = H;
   band_job *jobs = (band_job *)calloc((size_t)nthreads, sizeof(band_job));
@@ -252,7 +259,7 @@ static int run_with(const int32_t masks[4][5][5], int radius, const uint8_t *src
   }
   int t;
   for (t = 0; t < nthreads; ++t) {
-    band_job j = {masks, radius, src, sp, H, W, border, fmt, dst, dp,
+    band_job j = {masks, radius, thr, src, sp, H, W, border, fmt, dst, dp,
                   (int)((int64_t)H * t / nthreads), (int)((int64_t)H * (t + 1) / nthreads)};
     jobs[t] = j;
   }

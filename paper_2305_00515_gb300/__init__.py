@@ -20,7 +20,7 @@ __all__ = [
     "BORDERS", "FORMATS", "VARIANTS", "Sobel4", "Sobel4Error", "Image", "Options",
     "library_path", "load", "sobel4_create", "sobel4_destroy", "sobel4_run",
     "sobel4_run_batched", "sobel4_run_host", "sobel4_status_string", "sobel4_last_cuda_error",
-    "sobel4_device_status", "sobel4_inject_stage_loss", "sobel4_set_weights", "sobel4_set_operator", "OPERATORS", "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
+    "sobel4_device_status", "sobel4_inject_stage_loss", "sobel4_set_weights", "sobel4_set_operator", "sobel4_set_threshold", "OPERATORS", "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
     "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched", "sobel4_tune_entries",
     "sobel4_tune_config", "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create",
     "sobel4_pipeline_buffers", "sobel4_pipeline_submit", "sobel4_pipeline_wait",
@@ -31,10 +31,10 @@ __all__ = [
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 BORDERS = {"valid": 0, "replicate": 1, "reflect101": 2, "constant0": 3}
-FORMATS = {"f32": 0, "u8": 1, "s16x4": 2, "u16": 3}
+FORMATS = {"f32": 0, "u8": 1, "s16x4": 2, "u16": 3, "edge8": 4}
 VARIANTS = {"auto": 0, "direct": 1, "rg": 2, "rg_lanecopy": 3, "tc": 4}
 OPERATORS = {"4dir5x5": 0, "2dir5x5": 1, "2dir3x3": 2}
-ELEM_SIZE = {"f32": 4, "u8": 1, "s16x4": 2, "u16": 2}
+ELEM_SIZE = {"f32": 4, "u8": 1, "s16x4": 2, "u16": 2, "edge8": 1}
 STATUS = {0: "SOBEL4_OK", 1: "SOBEL4_ERR_INVALID_ARG", 2: "SOBEL4_ERR_UNSUPPORTED",
           3: "SOBEL4_ERR_OOM", 4: "SOBEL4_ERR_CUDA", 5: "SOBEL4_ERR_TIMEOUT"}
 
@@ -42,7 +42,7 @@ EXPORTED_SYMBOLS = (
     "sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_batched", "sobel4_run_host",
     "sobel4_status_string", "sobel4_last_cuda_error", "sobel4_device_status",
     "sobel4_inject_stage_loss", "sobel4_set_weights", "sobel4_set_operator",
-    "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
+    "sobel4_set_threshold", "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
     "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched", "sobel4_tune_entries",
     "sobel4_tune_config", "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create",
     "sobel4_pipeline_buffers", "sobel4_pipeline_submit", "sobel4_pipeline_wait",
@@ -117,6 +117,7 @@ def load() -> ctypes.CDLL:
         lib.sobel4_set_weights.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                            ctypes.c_double]
         lib.sobel4_set_operator.argtypes = [vp, i32]
+        lib.sobel4_set_threshold.argtypes = [vp, ctypes.c_double]
         lib.sobel4_launch_count.argtypes = [vp]
         lib.sobel4_launch_count.restype = ctypes.c_uint64
         lib.sobel4_set_variant.argtypes = [vp, i32]
@@ -148,7 +149,7 @@ def load() -> ctypes.CDLL:
         for name in ("sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_batched",
                      "sobel4_run_host", "sobel4_set_variant", "sobel4_check_magnitude",
                      "sobel4_device_status", "sobel4_inject_stage_loss", "sobel4_tune_config",
-                     "sobel4_set_weights", "sobel4_set_operator",
+                     "sobel4_set_weights", "sobel4_set_operator", "sobel4_set_threshold",
                      "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched",
                      "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create",
                      "sobel4_pipeline_buffers", "sobel4_pipeline_submit", "sobel4_pipeline_wait",
@@ -205,6 +206,11 @@ def sobel4_last_cuda_error(h) -> int:
 
 def sobel4_device_status(h) -> int:
     return load().sobel4_device_status(h)
+
+
+def sobel4_set_threshold(h, t: float) -> int:
+    """EDGE8 threshold T for the handle's later runs (255 where sqrt(S) >= T)."""
+    return load().sobel4_set_threshold(h, t)
 
 
 def sobel4_set_operator(h, op: int) -> int:
@@ -308,7 +314,7 @@ class Pipeline:
                                        FORMATS[fmt], slots)
         _check(st, "sobel4_pipeline_create")
         self.p, self.slots, self.H, self.W, self.fmt = p, slots, height, width, fmt
-        dtype = {"f32": np.float32, "u8": np.uint8, "s16x4": np.int16, "u16": np.uint16}[fmt]
+        dtype = {"f32": np.float32, "u8": np.uint8, "s16x4": np.int16, "u16": np.uint16, "edge8": np.uint8}[fmt]
         planes = 4 if fmt == "s16x4" else 1
         self.inputs, self.outputs = [], []
         for k in range(slots):
@@ -419,6 +425,10 @@ class Sobel4:
     def set_variant(self, variant: str):
         _check(sobel4_set_variant(self.handle, VARIANTS[variant]), "sobel4_set_variant")
 
+    def set_threshold(self, t: float = 128.0):
+        """EDGE8 threshold (255 where sqrt(S) >= t)."""
+        _check(sobel4_set_threshold(self.handle, t), "sobel4_set_threshold")
+
     def set_operator(self, name: str = "4dir5x5"):
         """4dir5x5 (Eq. 3), 2dir5x5 or 2dir3x3 (Eq. 1-2)."""
         _check(sobel4_set_operator(self.handle, OPERATORS[name]), "sobel4_set_operator")
@@ -438,7 +448,7 @@ class Sobel4:
     def empty_output(src, fmt: str = "f32"):
         import torch
         H, W = src.shape
-        dtype = {"f32": torch.float32, "u8": torch.uint8, "s16x4": torch.int16, "u16": torch.uint16}[fmt]
+        dtype = {"f32": torch.float32, "u8": torch.uint8, "s16x4": torch.int16, "u16": torch.uint16, "edge8": torch.uint8}[fmt]
         shape = (4, H, W) if fmt == "s16x4" else (H, W)
         return torch.empty(shape, dtype=dtype, device=src.device)
 
@@ -484,7 +494,7 @@ class Sobel4:
             raise ValueError("src must be a 2-D uint8 array with unit column stride")
         H, W = src.shape
         if out is None:
-            dtype = {"f32": np.float32, "u8": np.uint8, "s16x4": np.int16, "u16": np.uint16}[fmt]
+            dtype = {"f32": np.float32, "u8": np.uint8, "s16x4": np.int16, "u16": np.uint16, "edge8": np.uint8}[fmt]
             out = np.empty((4, H, W) if fmt == "s16x4" else (H, W), dtype=dtype)
         _check(sobel4_run_host(self.handle, src.ctypes.data, src.strides[0], out.ctypes.data,
                                out.strides[-2], H, W, BORDERS[border], FORMATS[fmt]),

@@ -9,6 +9,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <new>
 #include <string>
@@ -119,7 +120,7 @@ cudaError_t param_upload(const void *src, void *dst, size_t bytes, unsigned int 
   return cudaSuccess;
 }
 
-size_t elem_size(int fmt) { return fmt == kF32 ? 4 : (fmt == kU8 ? 1 : 2); }
+size_t elem_size(int fmt) { return fmt == kF32 ? 4 : ((fmt == kU8 || fmt == kEdge8) ? 1 : 2); }
 int planes(int fmt) { return fmt == kS16x4 ? 4 : 1; }
 
 class DeviceGuard {
@@ -168,6 +169,7 @@ struct sobel4_ctx {
   int lose_stage = -1;            // failure injection for the next TMA-staged launch
   bool custom = false;            // runtime masks (Eq. 5 weights, other operators) replace Eq. (3)
   int radius = 2;                 // support radius of the masks (VALID frame width)
+  int32_t thr = 16384;            // EDGE8 threshold on S (T = 128 by default)
   bool custom_s16_ok = true;      // every response fits the S16X4 planes
   Masks4 masks{};
   cudaStream_t own_stream = nullptr;
@@ -199,7 +201,7 @@ sobel4_status cuda_fail(sobel4_ctx *h, cudaError_t e) {
 
 bool valid_enum(int border, int fmt) {
   return border >= SOBEL4_BORDER_VALID && border <= SOBEL4_BORDER_CONSTANT0 &&
-         fmt >= SOBEL4_OUT_F32 && fmt <= SOBEL4_OUT_U16;
+         fmt >= SOBEL4_OUT_F32 && fmt <= SOBEL4_OUT_EDGE8;
 }
 
 // Shape and pitch rules shared by every entry point (pointers checked separately).
@@ -264,8 +266,8 @@ const TuneEntry *find_tuned(const sobel4_ctx *h, int kind, int32_t H, int32_t W,
 void rg_config(const sobel4_ctx *h, const uint8_t *src, size_t sp, const void *dst, size_t dp,
                int32_t H, int32_t W, int border, int fmt, bool *use_tma, int *nc, int *R) {
   const TuneEntry *t = find_tuned(h, 0, H, W, fmt);
-  // U16 exists on the TMA family only (no lane-copy instantiation).
-  *use_tma = fmt == kU16 ||
+  // U16 and EDGE8 exist on the TMA family only (no lane-copy instantiation).
+  *use_tma = fmt == kU16 || fmt == kEdge8 ||
              (h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced && !(t && t->kernel == 0));
   if (*use_tma) {
     *nc = 4;
@@ -336,11 +338,11 @@ sobel4_status launch_one(sobel4_ctx *h, const uint8_t *src, size_t sp, void *dst
       h->lose_stage = -1;
     } else {
       const ImageDesc im = make_desc(src, sp, dst, dp, H, W, 1, h->nc);
-      e = launch_direct(im, border, fmt, &h->masks, h->radius, stream);
+      e = launch_direct(im, border, fmt, &h->masks, h->radius, h->thr, stream);
     }
   } else if (h->variant == SOBEL4_VARIANT_DIRECT) {
     const ImageDesc im = make_desc(src, sp, dst, dp, H, W, 1, h->nc);
-    e = launch_direct(im, border, fmt, nullptr, 2, stream);
+    e = launch_direct(im, border, fmt, nullptr, 2, h->thr, stream);
   } else if (use_tc(h, src, sp, dst, dp, H, W, border, fmt)) {
     e = launch_tc_single(src, sp, dst, dp, H, W, border, fmt, h->sm_count, h->d_err, stream,
                          h->lose_stage);
@@ -351,7 +353,7 @@ sobel4_status launch_one(sobel4_ctx *h, const uint8_t *src, size_t sp, void *dst
     rg_config(h, src, sp, dst, dp, H, W, border, fmt, &use_tma, &nc, &R);
     if (use_tma) {
       e = launch_tma_single(src, sp, dst, dp, H, W, border, fmt, R, h->sm_count,
-                            pair ? pair : next_pair(h), h->d_err, stream, h->lose_stage);
+                            pair ? pair : next_pair(h), h->d_err, stream, h->lose_stage, h->thr);
       h->lose_stage = -1;
     } else {
       const ImageDesc im = make_desc(src, sp, dst, dp, H, W, R, nc);
@@ -535,6 +537,17 @@ sobel4_status sobel4_set_weights(sobel4_handle h, double a, double b, double n, 
   return SOBEL4_OK;
 }
 
+sobel4_status sobel4_set_threshold(sobel4_handle h, double t) {
+  if (!h || !(t >= 0.0) || t > 46341.0) return SOBEL4_ERR_INVALID_ARG;
+  // Smallest integer k with k >= t^2, decided exactly: fma(t, t, -k) has the
+  // sign of t^2 - k (a nonzero difference never rounds to zero here).
+  int64_t k = (int64_t)std::ceil(t * t);
+  while (k > 0 && std::fma(t, t, -(double)(k - 1)) <= 0.0) --k;
+  while (std::fma(t, t, -(double)k) > 0.0) ++k;
+  h->thr = (int32_t)std::min<int64_t>(k, INT32_MAX);
+  return SOBEL4_OK;
+}
+
 sobel4_status sobel4_set_operator(sobel4_handle h, int32_t op) {
   if (!h) return SOBEL4_ERR_INVALID_ARG;
   if (op == SOBEL4_OP_4DIR_5X5) return sobel4_set_weights(h, 1, 2, 4, 6);
@@ -655,8 +668,8 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
   // Every image goes to the TMA-family batched kernel unless the handle asks
   // for lane copies: 16-byte aligned sources in one launch group (tensor
   // copies), the others in a second (bulk row copies).
-  const bool tma_ok =
-      fmt == kU16 || (h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced && !bl);
+  const bool tma_ok = fmt == kU16 || fmt == kEdge8 ||
+                      (h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced && !bl);
   // TMA strip height: explicit option, else the tuned one, else by the
   // batch's make-up.  When every image has 16-byte aligned source rows and
   // vector-aligned destination rows, about four items per resident warp (8 ..
@@ -674,7 +687,7 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
       for (int32_t i = 0; i < n; ++i) {
         const sobel4_image &m = imgs[i];
         seg_rows += (int64_t)((m.width + 127) / 128) * m.height;
-        const int vec = fmt == kF32 ? 16 : (fmt == kU8 ? 4 : 8);
+        const int vec = vec_bytes(fmt);
         every_aligned = every_aligned && tma_eligible(m.src, m.src_pitch) &&
                      pow2_align((uintptr_t)m.dst | (uintptr_t)m.dst_pitch) >= vec;
       }
@@ -694,7 +707,8 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
         if (tma_eligible(m.src, m.src_pitch) != (g == 0)) continue;
         int64_t items = 0;
         e = tma_fill_batch_desc(slot.h_tma + tma_batch_desc_bytes() * n_tma, m.src, m.src_pitch,
-                                m.dst, m.dst_pitch, m.height, m.width, Rt, total_grp[g], &items);
+                                m.dst, m.dst_pitch, m.height, m.width, Rt, total_grp[g], &items,
+                                h->thr);
         if (e != cudaSuccess) return cuda_fail(h, e);
         total_grp[g] += items;
         ++n_grp[g];
@@ -960,7 +974,8 @@ extern "C" sobel4_status sobel4_run_batched_static(const sobel4_image *imgs, int
                                                    sobel4_border border, sobel4_format fmt,
                                                    cudaStream_t stream) {
   if (!imgs || n < 1 || !valid_enum(border, fmt)) return SOBEL4_ERR_INVALID_ARG;
-  if (n > kStaticMaxImages || fmt == kU16) return SOBEL4_ERR_UNSUPPORTED;  // lane-copy kernel
+  if (n > kStaticMaxImages || fmt == kU16 || fmt == kEdge8)
+    return SOBEL4_ERR_UNSUPPORTED;  // the lane-copy kernel has no such output
   for (int32_t i = 0; i < n; ++i) {
     const sobel4_image &m = imgs[i];
     if (!m.src || !valid_dst_ptr(m.dst, fmt) ||
@@ -1115,7 +1130,8 @@ extern "C" sobel4_status sobel4_tune(sobel4_handle h, int32_t height, int32_t wi
   }
   // TMA-staged kernel: a few strip heights, including the one that gives every
   // resident warp about one item.
-  if ((fmt == kU16 || (h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced)) &&
+  if ((fmt == kU16 || fmt == kEdge8 ||
+       (h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced)) &&
       tma_eligible(src, sp)) {
     std::vector<int> cands;
     if (h->rows_per_strip > 0) {
@@ -1142,7 +1158,7 @@ extern "C" sobel4_status sobel4_tune(sobel4_handle h, int32_t height, int32_t wi
   }
   const int ncs[2] = {2, 4};
   const int Rs[4] = {8, 16, 32, 64};
-  for (int a = 0; a < 2 && e == cudaSuccess && fmt != kU16; ++a) {
+  for (int a = 0; a < 2 && e == cudaSuccess && fmt != kU16 && fmt != kEdge8; ++a) {
     if (h->nc_forced && ncs[a] != h->nc) continue;
     for (int b = 0; b < 4 && e == cudaSuccess; ++b) {
       if (h->rows_per_strip > 0 && Rs[b] != h->rows_per_strip) continue;
@@ -1206,7 +1222,7 @@ extern "C" sobel4_status sobel4_tune_batched(sobel4_handle h, const sobel4_image
     }
   }
   // Lane-copy kernel: columns per lane, strip height, CTAs per SM.
-  for (int a = 0; a < 2 && st == SOBEL4_OK && fmt != kU16; ++a) {
+  for (int a = 0; a < 2 && st == SOBEL4_OK && fmt != kU16 && fmt != kEdge8; ++a) {
     if (h->nc_forced && ncs[a] != h->nc) continue;
     for (int b = 0; b < 3 && st == SOBEL4_OK; ++b) {
       if (h->rows_per_strip > 0 && Rs[b] != h->rows_per_strip) continue;
@@ -1228,7 +1244,7 @@ extern "C" sobel4_status sobel4_tune_config(sobel4_handle h, int32_t height, int
                                             sobel4_format fmt, int32_t *kernel,
                                             int32_t *columns_per_lane, int32_t *rows_per_strip) {
   if (!h || !kernel || !columns_per_lane || !rows_per_strip || height < 1 || width < 1 ||
-      fmt < SOBEL4_OUT_F32 || fmt > SOBEL4_OUT_U16)
+      fmt < SOBEL4_OUT_F32 || fmt > SOBEL4_OUT_EDGE8)
     return SOBEL4_ERR_INVALID_ARG;
   // The configuration a VALID launch with 16-byte aligned rows would use.
   static const uint8_t kAligned[16] __attribute__((aligned(16))) = {0};

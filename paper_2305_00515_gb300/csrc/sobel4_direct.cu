@@ -11,7 +11,8 @@ namespace sobel4 {
 // fr: the support radius of the masks (2 for 5x5, 1 for a 3x3 operator),
 // the width of the frame the paper's rule leaves at 0.
 template <int FMT, bool CUSTOM>
-__global__ void __launch_bounds__(256) direct_kernel(ImageDesc im, int border, Masks4 m, int fr) {
+__global__ void __launch_bounds__(256) direct_kernel(ImageDesc im, int border, Masks4 m, int fr,
+                                                     int32_t thr) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int H = im.H, W = im.W;
@@ -44,6 +45,8 @@ __global__ void __launch_bounds__(256) direct_kernel(ImageDesc im, int border, M
     row[x] = (uint8_t)magnitude_u8(s);
   } else if (FMT == kU16) {
     ((uint16_t *)row)[x] = (uint16_t)magnitude_u16(s);
+  } else if (FMT == kEdge8) {
+    row[x] = (computed && s >= thr) ? 255 : 0;
   } else {
     const uint64_t plane = (uint64_t)(uint32_t)H * im.dp;
 #pragma unroll
@@ -52,7 +55,7 @@ __global__ void __launch_bounds__(256) direct_kernel(ImageDesc im, int border, M
 }
 
 cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, const Masks4 *masks,
-                          int radius, cudaStream_t st) {
+                          int radius, int32_t thr, cudaStream_t st) {
   const dim3 block(32, 8);
   const dim3 grid((im.W + 31) / 32, (im.H + 7) / 8);
   Masks4 m;
@@ -60,12 +63,13 @@ cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, const Masks4
   else memset(&m, 0, sizeof(m));
   (void)cudaGetLastError();  // report this launch only, not an earlier failed call
 #define SOBEL4_DIRECT(F)                                                          \
-  (masks ? direct_kernel<F, true><<<grid, block, 0, st>>>(im, border, m, radius)  \
-         : direct_kernel<F, false><<<grid, block, 0, st>>>(im, border, m, radius))
+  (masks ? direct_kernel<F, true><<<grid, block, 0, st>>>(im, border, m, radius, thr)  \
+         : direct_kernel<F, false><<<grid, block, 0, st>>>(im, border, m, radius, thr))
   switch (fmt) {
     case kF32: SOBEL4_DIRECT(kF32); break;
     case kU8: SOBEL4_DIRECT(kU8); break;
     case kU16: SOBEL4_DIRECT(kU16); break;
+    case kEdge8: SOBEL4_DIRECT(kEdge8); break;
     default: SOBEL4_DIRECT(kS16x4); break;
   }
 #undef SOBEL4_DIRECT

@@ -40,7 +40,7 @@ int tma_round_R(int R);
 cudaError_t launch_tma_single(const uint8_t *src, size_t sp, void *dst, size_t dp, int32_t H,
                               int32_t W, int border, int fmt, int R, int sm_count,
                               unsigned int *pair, unsigned int *err, cudaStream_t st,
-                              int lose_stage = -1);
+                              int lose_stage = -1, int32_t thr = 0);
 
 // TMA-family batches: the host fills one descriptor (tma_batch_desc_bytes
 // bytes, 64-byte aligned) per image, copies them to the device and launches
@@ -48,8 +48,10 @@ cudaError_t launch_tma_single(const uint8_t *src, size_t sp, void *dst, size_t d
 // the launch).  One launch takes images of one staging: all tma_eligible
 // (bulk = false) or all not (bulk = true); R as for launch_tma_single.
 size_t tma_batch_desc_bytes();
+// thr: the EDGE8 threshold on S.
 cudaError_t tma_fill_batch_desc(void *out, const uint8_t *src, size_t sp, void *dst, size_t dp,
-                                int32_t H, int32_t W, int R, int64_t item0, int64_t *items);
+                                int32_t H, int32_t W, int R, int64_t item0, int64_t *items,
+                                int32_t thr = 0);
 // d_queue: one zeroed counter; all_fast (every image's items on the fast
 // path with vector stores, see tma_all_fast) selects the lean kernel.
 cudaError_t launch_tma_batched(const void *d_descs, int n_img, int64_t total,
@@ -81,7 +83,7 @@ cudaError_t launch_tc_single(const uint8_t *src, size_t sp, void *dst, size_t dp
 // DIRECT kernel (one thread per output pixel); masks = nullptr: Eq. (3);
 // radius: the masks' support radius (VALID leaves a frame that wide at 0).
 cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, const Masks4 *masks,
-                          int radius, cudaStream_t st);
+                          int radius, int32_t thr, cudaStream_t st);
 
 // Masks of the operators besides the four-directional 5x5: op 1 = the
 // two-directional 5x5 (K_x, K_y of Eq. 3), op 2 = the two-directional 3x3 of

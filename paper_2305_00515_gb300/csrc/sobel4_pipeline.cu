@@ -26,7 +26,9 @@ struct Slot {
   bool pending = false;
 };
 
-size_t elem_bytes(int fmt) { return fmt == SOBEL4_OUT_F32 ? 4 : (fmt == SOBEL4_OUT_U8 ? 1 : 2); }
+size_t elem_bytes(int fmt) {
+  return fmt == SOBEL4_OUT_F32 ? 4 : ((fmt == SOBEL4_OUT_U8 || fmt == SOBEL4_OUT_EDGE8) ? 1 : 2);
+}
 
 }  // namespace
 

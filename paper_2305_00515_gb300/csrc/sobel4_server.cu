@@ -30,7 +30,9 @@ constexpr int kMaxInFlight = 2;
 constexpr size_t kAlign = 256;
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-size_t elem_bytes(int fmt) { return fmt == SOBEL4_OUT_F32 ? 4 : (fmt == SOBEL4_OUT_U8 ? 1 : 2); }
+size_t elem_bytes(int fmt) {
+  return fmt == SOBEL4_OUT_F32 ? 4 : ((fmt == SOBEL4_OUT_U8 || fmt == SOBEL4_OUT_EDGE8) ? 1 : 2);
+}
 
 // First-fit allocator over one device buffer; offsets only, no device calls.
 class Arena {
@@ -304,7 +306,7 @@ extern "C" sobel4_status sobel4_server_create(sobel4_handle h, const sobel4_serv
   if (!out) return SOBEL4_ERR_INVALID_ARG;
   *out = nullptr;
   if (!h || !opt || opt->border < SOBEL4_BORDER_VALID || opt->border > SOBEL4_BORDER_CONSTANT0 ||
-      opt->format < SOBEL4_OUT_F32 || opt->format > SOBEL4_OUT_U16 || opt->max_batch < 0 ||
+      opt->format < SOBEL4_OUT_F32 || opt->format > SOBEL4_OUT_EDGE8 || opt->max_batch < 0 ||
       opt->memory_budget < 0 || (opt->plain != 0 && opt->plain != 1))
     return SOBEL4_ERR_INVALID_ARG;
   sobel4_server_ctx *s = new (std::nothrow) sobel4_server_ctx();

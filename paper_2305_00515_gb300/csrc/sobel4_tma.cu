@@ -38,6 +38,7 @@ int resident(int fmt, int mode, int st) {
     case kF32: return TmaFmt<kF32>::resident(mode, st);
     case kU8: return TmaFmt<kU8>::resident(mode, st);
     case kU16: return TmaFmt<kU16>::resident(mode, st);
+    case kEdge8: return TmaFmt<kEdge8>::resident(mode, st);
     default: return TmaFmt<kS16x4>::resident(mode, st);
   }
 }
@@ -57,7 +58,7 @@ bool tensor_ok(const uint8_t *src, size_t sp) {
 enum Plan { kPlanFast, kPlanGeneral, kPlanAll };
 
 Plan plan_for(int32_t W, int border, int fmt, int dst_align, int st) {
-  const int vec_need = fmt == kF32 ? 16 : (fmt == kU8 ? 4 : 8);
+  const int vec_need = vec_bytes(fmt);
   if (W < tma::kCols) return kPlanGeneral;
   if (dst_align >= vec_need && W % tma::kCols == 0 &&
       (border == kValid || (st == tma::kTensor && border == kConstant0)))
@@ -95,6 +96,7 @@ tma::TmaImage make_image(const uint8_t *src, size_t sp, void *dst, size_t dp, in
   while (a < 16 && (((uintptr_t)dst | (uintptr_t)dp) % (uintptr_t)(2 * a)) == 0) a *= 2;
   im.dst_align = a;
   im.lose_stage = -1;
+  im.thr = 0;
   return im;
 }
 
@@ -112,6 +114,9 @@ void single(int fmt, int mode, int st, const CUtensorMap &map, const tma::TmaIma
       break;
     case kU16:
       TmaFmt<kU16>::single(mode, st, map, im, border, R, items, grid, pair, err, s);
+      break;
+    case kEdge8:
+      TmaFmt<kEdge8>::single(mode, st, map, im, border, R, items, grid, pair, err, s);
       break;
     default:
       TmaFmt<kS16x4>::single(mode, st, map, im, border, R, items, grid, pair, err, s);
@@ -163,7 +168,7 @@ int tma_pick_R(int fmt, int sm_count, int32_t H, int32_t W, bool all_fast) {
 cudaError_t launch_tma_single(const uint8_t *src, size_t sp, void *dst, size_t dp, int32_t H,
                               int32_t W, int border, int fmt, int R, int sm_count,
                               unsigned int *pair, unsigned int *err, cudaStream_t st,
-                              int lose_stage) {
+                              int lose_stage, int32_t thr) {
   if (R < tma::kUnroll || R % tma::kUnroll) return cudaErrorInvalidValue;
   const int staging = tensor_ok(src, sp) ? tma::kTensor : tma::kBulk;
   CUtensorMap map;
@@ -174,6 +179,7 @@ cudaError_t launch_tma_single(const uint8_t *src, size_t sp, void *dst, size_t d
   }
   tma::TmaImage im = make_image(src, sp, dst, dp, H, W, R);
   im.lose_stage = lose_stage;
+  im.thr = thr;
   const int64_t items = (int64_t)im.n_seg * im.n_band;
   if (items >= (1ll << 31)) return cudaErrorInvalidValue;
   const Plan plan = plan_for(W, border, fmt, im.dst_align, staging);
@@ -187,7 +193,8 @@ cudaError_t launch_tma_single(const uint8_t *src, size_t sp, void *dst, size_t d
 size_t tma_batch_desc_bytes() { return sizeof(tma::TmaBatchDesc); }
 
 cudaError_t tma_fill_batch_desc(void *out, const uint8_t *src, size_t sp, void *dst, size_t dp,
-                                int32_t H, int32_t W, int R, int64_t item0, int64_t *items) {
+                                int32_t H, int32_t W, int R, int64_t item0, int64_t *items,
+                                int32_t thr) {
   tma::TmaBatchDesc *d = (tma::TmaBatchDesc *)out;
   memset(&d->map, 0, sizeof(d->map));
   if (tensor_ok(src, sp)) {
@@ -195,6 +202,7 @@ cudaError_t tma_fill_batch_desc(void *out, const uint8_t *src, size_t sp, void *
     if (e != cudaSuccess) return e;
   }
   d->im = make_image(src, sp, dst, dp, H, W, R);
+  d->im.thr = thr;
   d->item0 = item0;
   *items = (int64_t)d->im.n_seg * d->im.n_band;
   return cudaSuccess;
@@ -228,6 +236,10 @@ cudaError_t launch_tma_batched(const void *d_descs, int n_img, int64_t total,
         break;
       case kU16:
         TmaFmt<kU16>::batched(mode, staging, d, n_img, (int)total, queue, border, R, g, err, st);
+        break;
+      case kEdge8:
+        TmaFmt<kEdge8>::batched(mode, staging, d, n_img, (int)total, queue, border, R, g, err,
+                                st);
         break;
       default:
         TmaFmt<kS16x4>::batched(mode, staging, d, n_img, (int)total, queue, border, R, g, err,

@@ -109,6 +109,7 @@ struct TmaImage {
   int32_t n_seg, n_band;
   int32_t dst_align;  // largest power of two (<= 16) dividing dst and dp
   int32_t lose_stage; // failure injection (tests): stage of item 0 never copied; -1 = off
+  int32_t thr;        // EDGE8: an output pixel is 255 where S >= thr, else 0
 };
 
 // One image of a TMA-staged batch: its tensor map (written by the host before
@@ -510,8 +511,16 @@ __device__ __forceinline__ void store_rows(const TmaImage &im, uint8_t *row_a, u
     }
   } else {
     uint32_t ua[4], ub[4];
+    if constexpr (FMT == kEdge8) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) magnitude_u8x2(sa[k], sb[k], ua[k], ub[k]);
+      for (int k = 0; k < 4; ++k) {
+        ua[k] = sa[k] >= im.thr ? 255u : 0u;
+        ub[k] = sb[k] >= im.thr ? 255u : 0u;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) magnitude_u8x2(sa[k], sb[k], ua[k], ub[k]);
+    }
     uint8_t *pa = row_a + x, *pb = row_b + x;
     if (GEN) {
 #pragma unroll
@@ -552,7 +561,7 @@ __device__ __forceinline__ void zero_px(const TmaImage &im, int y, int x) {
   uint8_t *row = (uint8_t *)im.dst + (uint64_t)(uint32_t)y * im.dp;
   if constexpr (FMT == kF32) {
     ((float *)row)[x] = 0.0f;
-  } else if constexpr (FMT == kU8) {
+  } else if constexpr (FMT == kU8 || FMT == kEdge8) {
     row[x] = 0;
   } else if constexpr (FMT == kU16) {
     ((uint16_t *)row)[x] = 0;
@@ -570,7 +579,7 @@ __device__ __forceinline__ void zero_row4(const TmaImage &im, int y, int x) {
   uint8_t *row = (uint8_t *)im.dst + (uint64_t)(uint32_t)y * im.dp;
   if constexpr (FMT == kF32) {
     *(float4 *)((float *)row + x) = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-  } else if constexpr (FMT == kU8) {
+  } else if constexpr (FMT == kU8 || FMT == kEdge8) {
     *(uint32_t *)(row + x) = 0u;
   } else if constexpr (FMT == kU16) {
     *(uint2 *)((uint16_t *)row + x) = make_uint2(0u, 0u);
@@ -724,7 +733,7 @@ __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg
     // bulk staging also for CONSTANT0, whose outside columns read 0).
     edge_lane = (mapped_rule || (ST == kBulk && border == kConstant0)) &&
                 (x - 2 < 0 || x + 5 >= W);
-    const int vec_need = FMT == kF32 ? 16 : (FMT == kU8 ? 4 : 8);
+    const int vec_need = vec_bytes(FMT);
     vec = im.dst_align >= vec_need;
   }
 
@@ -943,7 +952,7 @@ __device__ __forceinline__ bool run_item(const TmaImage &im, int border, int seg
     if (full) return tma_item<FMT, false, true, ST, false>(im, border, seg, ya, R, lane, cx, err);
     return tma_item<FMT, false, false, ST, false>(im, border, seg, ya, R, lane, cx, err);
   } else if constexpr (MODE == kAll) {
-    constexpr int vec_need = FMT == kF32 ? 16 : (FMT == kU8 ? 4 : 8);
+    constexpr int vec_need = vec_bytes(FMT);
     if (im.dst_align >= vec_need) {
       if (full) return tma_item<FMT, false, true, ST, false>(im, border, seg, ya, R, lane, cx, err);
       return tma_item<FMT, false, false, ST, false>(im, border, seg, ya, R, lane, cx, err);

@@ -1,6 +1,6 @@
 // sobel4_tma_fmt.cuh — launch helpers of the TMA-family kernels for one
 // output format, explicitly instantiated once per format in
-// sobel4_tma_{f32,u8,s16,u16}.cu so the kernel variants compile in parallel.
+// sobel4_tma_{f32,u8,s16,u16,edge8}.cu so the kernel variants compile in parallel.
 #pragma once
 
 #include <algorithm>
@@ -89,5 +89,6 @@ extern template struct TmaFmt<kF32>;
 extern template struct TmaFmt<kU8>;
 extern template struct TmaFmt<kS16x4>;
 extern template struct TmaFmt<kU16>;
+extern template struct TmaFmt<kEdge8>;
 
 }  // namespace sobel4

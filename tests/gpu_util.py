@@ -8,8 +8,9 @@ import numpy as np
 import paper_2305_00515_gb300 as pkg
 
 GUARD = 0xA5
-ELEM = {"f32": 4, "u8": 1, "s16x4": 2, "u16": 2}
-DTYPE = {"f32": np.float32, "u8": np.uint8, "s16x4": np.int16, "u16": np.uint16}
+ELEM = {"f32": 4, "u8": 1, "s16x4": 2, "u16": 2, "edge8": 1}
+DTYPE = {"f32": np.float32, "u8": np.uint8, "s16x4": np.int16, "u16": np.uint16,
+         "edge8": np.uint8}
 
 
 class Placed:

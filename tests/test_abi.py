@@ -47,6 +47,7 @@ def test_null_handle_queries(lib):
     assert pkg.sobel4_set_variant(None, 0) == 1
     assert pkg.sobel4_set_weights(None, 1, 2, 4, 6) == 1
     assert pkg.sobel4_set_operator(None, 0) == 1
+    assert pkg.sobel4_set_threshold(None, 10.0) == 1
 
 
 def test_create_rejects_bad_options(lib):
@@ -80,7 +81,7 @@ BAD_RUNS = [
     dict(d_dst=DST + 2),                     # F32 destination not 4-byte aligned
     dict(border=4),
     dict(border=-1),
-    dict(fmt=4),
+    dict(fmt=5),
     dict(border=2, height=2),                # REFLECT101 needs >= 3
     dict(border=2, width=2, src_pitch=100, dst_pitch=400),
     dict(d_dst=SRC + 50),                    # output overlaps input

@@ -23,8 +23,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 BORDERS = ("valid", "replicate", "reflect101", "constant0")
-FORMATS = ("f32", "u8", "s16x4", "u16")
-ELEM = {"f32": 4, "u8": 1, "s16x4": 2, "u16": 2}
+FORMATS = ("f32", "u8", "s16x4", "u16", "edge8")
+ELEM = {"f32": 4, "u8": 1, "s16x4": 2, "u16": 2, "edge8": 1}
 NCPU = oracle.cpu_count()
 
 # (H, W, source offset, extra pitch bytes)

@@ -17,7 +17,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 BORDERS = ("valid", "replicate", "reflect101", "constant0")
-FORMATS = ("f32", "u8", "s16x4", "u16")
+FORMATS = ("f32", "u8", "s16x4", "u16", "edge8")
 NCPU = oracle.cpu_count()
 
 
@@ -81,7 +81,7 @@ PITCHES = [  # (src_pitch extra, src offset, dst pitch extra elements, dst offse
 def test_odd_pitches_and_offsets(handles, case, fmt):
     """Unaligned rows and unaligned/unpadded outputs take the general load/store paths."""
     spx, so, dpx, do = case
-    elem = {"f32": 4, "u8": 1, "s16x4": 2, "u16": 2}[fmt]
+    elem = {"f32": 4, "u8": 1, "s16x4": 2, "u16": 2, "edge8": 1}[fmt]
     for (H, W) in ((37, 301), (64, 512), (9, 140)):
         img = synth.rects_noise(H, W, 3 + W)
         for border in BORDERS:

@@ -21,8 +21,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 BORDERS = ("valid", "replicate", "reflect101", "constant0")
-FORMATS = ("f32", "u8", "s16x4", "u16")
-ELEM = {"f32": 4, "u8": 1, "s16x4": 2, "u16": 2}
+FORMATS = ("f32", "u8", "s16x4", "u16", "edge8")
+ELEM = {"f32": 4, "u8": 1, "s16x4": 2, "u16": 2, "edge8": 1}
 NCPU = oracle.cpu_count()
 
 SHAPES = [(1, 1), (1, 9), (9, 1), (2, 2), (3, 3), (4, 4), (5, 5), (6, 3), (7, 130), (5, 131),
@@ -114,7 +114,7 @@ def test_realigned_stores_every_phase(handles, fmt):
     sources: the lane-shifted stores, the head and tail elements of each
     segment and the zeroed frame of the paper's rule."""
     e = ELEM[fmt]
-    vec = {"f32": 16, "u8": 4, "s16x4": 8, "u16": 8}[fmt]
+    vec = {"f32": 16, "u8": 4, "s16x4": 8, "u16": 8, "edge8": 4}[fmt]
     for (H, W) in ((40, 256), (33, 384), (70, 517)):
         img = synth.rects_noise(H, W, 3 * W + H)
         for border in BORDERS:

@@ -19,7 +19,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 BORDERS = ("valid", "replicate", "reflect101", "constant0")
-FORMATS = ("f32", "u8", "s16x4", "u16")
+FORMATS = ("f32", "u8", "s16x4", "u16", "edge8")
 PARAMS = [(2, 0.5, 3, 4), (3, 1, 2, 5), (1, 3, 1, 1), (2, 1.5, 2, 2)]
 SHAPES = [(37, 61), (130, 256), (257, 300)]
 
@@ -53,7 +53,7 @@ def test_runtime_weights_match_oracle(built, abnm, variant):
             for border in BORDERS:
                 for fmt in FORMATS:
                     want = oracle.sobel4(img, border, fmt, masks=K)
-                    e = {"f32": 4, "u8": 1, "s16x4": 2, "u16": 2}[fmt]
+                    e = {"f32": 4, "u8": 1, "s16x4": 2, "u16": 2, "edge8": 1}[fmt]
                     for sp, dp in ((W, W * e), (ceil16(W), ceil16(W * e))):
                         got, guards = run_placed(torch, h, img, border, fmt, src_pitch=sp,
                                                  dst_pitch=dp)
@@ -119,7 +119,7 @@ def test_two_directional_operators(built, op, variant):
             for border in BORDERS:
                 for fmt in FORMATS:
                     want = oracle.sobel4(img, border, fmt, masks=K, radius=radius)
-                    e = {"f32": 4, "u8": 1, "s16x4": 2, "u16": 2}[fmt]
+                    e = {"f32": 4, "u8": 1, "s16x4": 2, "u16": 2, "edge8": 1}[fmt]
                     for sp, dp in ((W, W * e), (ceil16(W), ceil16(W * e))):
                         got, guards = run_placed(torch, h, img, border, fmt, src_pitch=sp,
                                                  dst_pitch=dp)
@@ -132,3 +132,26 @@ def test_two_directional_operators(built, op, variant):
         assert_same(got, oracle.sobel4(img, "valid", "f32"), "restored")
     finally:
         pkg.sobel4_destroy(h)
+
+
+def test_edge8_thresholds(built):
+    """EDGE8 with thresholds other than the default (T = 128), through the
+    TMA-family kernels (aligned and unaligned rows) and DIRECT."""
+    for variant in ("auto", "direct"):
+        st, h = pkg.sobel4_create(0, pkg.VARIANTS[variant])
+        assert st == 0
+        try:
+            for T in (0, 100.5, 777.25):
+                assert pkg.sobel4_set_threshold(h, T) == 0
+                for (H, W) in SHAPES:
+                    img = synth.rects_noise(H, W, 7 * H + W)
+                    for border in BORDERS:
+                        want = oracle.sobel4(img, border, "edge8", threshold=T)
+                        for sp in (W, ceil16(W)):
+                            got, guards = run_placed(torch, h, img, border, "edge8", src_pitch=sp)
+                            assert guards
+                            assert_same(got, want, f"{variant} T={T} {H}x{W} {border} sp {sp}")
+            assert pkg.sobel4_set_threshold(h, -1.0) == 1
+            assert pkg.sobel4_set_threshold(h, float("nan")) == 1
+        finally:
+            pkg.sobel4_destroy(h)

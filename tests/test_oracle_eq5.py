@@ -128,3 +128,23 @@ def test_two_directional_operators(o):
         R = oc.scipy_responses(img, border, o.masks()).astype(np.int64)
         f5 = o.sobel4(img, border, "f32", masks=m5)
         assert np.array_equal(f5, np.sqrt((R[0] ** 2 + R[1] ** 2).astype(np.float32))), border
+
+
+def test_edge8_rule(o):
+    """EDGE8 = 255 exactly where sqrt(S) >= T (S >= ceil(T^2)), frame 0."""
+    from fractions import Fraction
+    img = oc.rng_image(13, 25, 27)
+    for border in oc.BORDERS:
+        R = oc.scipy_responses(img, border, o.masks()).astype(np.int64)
+        S = (R ** 2).sum(axis=0)
+        for T in (0, 1, 100.5, 128, 1000.25, 5000):
+            got = o.sobel4(img, border, "edge8", threshold=T)
+            # sqrt(S) >= T  <=>  S >= T^2 (both sides non-negative), compared exactly
+            want = np.array([[255 if Fraction(int(v)) >= Fraction(T) ** 2 else 0 for v in row]
+                             for row in S], dtype=np.uint8)
+            if border == "valid":
+                frame = np.ones(S.shape, bool)
+                frame[2:-2, 2:-2] = False
+                want[frame] = 0
+            assert np.array_equal(got, want), (border, T)
+    assert oracle.edge_threshold(100.5) == 10101 and oracle.edge_threshold(128) == 16384
