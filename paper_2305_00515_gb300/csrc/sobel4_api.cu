@@ -670,31 +670,21 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
   // copies), the others in a second (bulk row copies).
   const bool tma_ok = fmt == kU16 || fmt == kEdge8 ||
                       (h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced && !bl);
-  // TMA strip height: explicit option, else the tuned one, else by the
-  // batch's make-up.  When every image has 16-byte aligned source rows and
-  // vector-aligned destination rows, about four items per resident warp (8 ..
-  // 128 rows): taller strips spend less on the 4-row window fill.  Otherwise
-  // about 64 items per warp (8 .. 64 rows): many short items balance the
-  // slower items of unaligned images (measured on the 512-image ragged batch:
-  // aligned rows 1.66 -> 1.37 ms from 8 to 64 rows, unaligned 2.18 -> 2.58 ms).
+  // TMA strip height: explicit option, else the tuned one, else about four
+  // items per resident warp (8 .. 128 rows): taller strips spend less on the
+  // 4-row window fill (measured on the 512-image ragged batch with tight
+  // pitches: 1.34 ms at 32 rows, 1.16 ms at 128).
   int Rt = tma_round_R(R);
   if (tma_ok && h->rows_per_strip <= 0) {
     if (bt && bt->kernel == 1) {
       Rt = bt->R;
     } else {
       int64_t seg_rows = 0;
-      bool every_aligned = true;
-      for (int32_t i = 0; i < n; ++i) {
-        const sobel4_image &m = imgs[i];
-        seg_rows += (int64_t)((m.width + 127) / 128) * m.height;
-        const int vec = vec_bytes(fmt);
-        every_aligned = every_aligned && tma_eligible(m.src, m.src_pitch) &&
-                     pow2_align((uintptr_t)m.dst | (uintptr_t)m.dst_pitch) >= vec;
-      }
+      for (int32_t i = 0; i < n; ++i)
+        seg_rows += (int64_t)((imgs[i].width + 127) / 128) * imgs[i].height;
       const int64_t warps = (int64_t)h->sm_count * 4 * kWarpsPerCta;
-      Rt = every_aligned
-               ? tma_round_R((int)std::min<int64_t>(128, std::max<int64_t>(8, seg_rows / (8 * warps))))
-               : tma_round_R((int)std::min<int64_t>(64, std::max<int64_t>(8, seg_rows / (128 * warps))));
+      Rt = tma_round_R(
+          (int)std::min<int64_t>(128, std::max<int64_t>(8, seg_rows / (8 * warps))));
     }
   }
   int n_lane = 0, n_tma = 0, n_grp[2] = {0, 0};
@@ -1213,10 +1203,10 @@ extern "C" sobel4_status sobel4_tune_batched(sobel4_handle h, const sobel4_image
       have = true;
     }
   };
-  // TMA-family kernel (any alignment): strip heights 8 .. 64.
+  // TMA-family kernel (any alignment): strip heights 8 .. 128.
   if (h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced) {
-    const int Rt[6] = {8, 16, 24, 32, 48, 64};
-    for (int b = 0; b < 6 && st == SOBEL4_OK; ++b) {
+    const int Rt[7] = {8, 16, 32, 48, 64, 96, 128};
+    for (int b = 0; b < 7 && st == SOBEL4_OK; ++b) {
       if (h->rows_per_strip > 0 && Rt[b] != tma_round_R(h->rows_per_strip)) continue;
       try_entry({1, 0, 0, (int)fmt, 4, Rt[b], h->ctas_per_sm, 0, 1});
     }

@@ -52,17 +52,19 @@ bool tensor_ok(const uint8_t *src, size_t sp) {
 }
 
 // Which kernel an image needs: every item on the fast path with vector
-// stores (the lean kernel), none (the general kernel), or anything else (one
-// kernel that carries both paths and the realigned stores, and hands the edge
-// items out first).
-enum Plan { kPlanFast, kPlanGeneral, kPlanAll };
+// stores (the lean kernel when the width is a multiple of the segment, the
+// ragged-width fast kernel otherwise), none (the general kernel), or anything
+// else (one kernel that carries both paths and the realigned stores, and
+// hands the edge items out first).
+enum Plan { kPlanFast, kPlanFastPart, kPlanGeneral, kPlanAll };
 
 Plan plan_for(int32_t W, int border, int fmt, int dst_align, int st) {
   const int vec_need = vec_bytes(fmt);
+  if (border == kValid || (st == tma::kTensor && border == kConstant0)) {
+    if (dst_align < vec_need) return kPlanAll;
+    return W % tma::kCols == 0 ? kPlanFast : kPlanFastPart;
+  }
   if (W < tma::kCols) return kPlanGeneral;
-  if (dst_align >= vec_need && W % tma::kCols == 0 &&
-      (border == kValid || (st == tma::kTensor && border == kConstant0)))
-    return kPlanFast;
   return kPlanAll;
 }
 
@@ -183,8 +185,10 @@ cudaError_t launch_tma_single(const uint8_t *src, size_t sp, void *dst, size_t d
   const int64_t items = (int64_t)im.n_seg * im.n_band;
   if (items >= (1ll << 31)) return cudaErrorInvalidValue;
   const Plan plan = plan_for(W, border, fmt, im.dst_align, staging);
-  const int mode = plan == kPlanFast ? tma::kFastOnly
-                                     : (plan == kPlanGeneral ? tma::kGeneralOnly : tma::kAll);
+  const int mode = plan == kPlanFast       ? tma::kFastOnly
+                   : plan == kPlanFastPart ? tma::kFastPart
+                   : plan == kPlanGeneral  ? tma::kGeneralOnly
+                                           : tma::kAll;
   (void)cudaGetLastError();  // report this launch only, not an earlier failed call
   single(fmt, mode, staging, map, im, border, R, (int)items, sm_count, pair, err, st);
   return cudaGetLastError();
@@ -213,7 +217,8 @@ bool tma_all_fast(int32_t W, int border, int fmt, const uint8_t *src, size_t sp,
   int a = 1;
   while (a < 16 && (((uintptr_t)dst | (uintptr_t)dp) % (uintptr_t)(2 * a)) == 0) a *= 2;
   const int staging = tensor_ok(src, sp) ? tma::kTensor : tma::kBulk;
-  return plan_for(W, border, fmt, a, staging) == kPlanFast;
+  const Plan plan = plan_for(W, border, fmt, a, staging);
+  return plan == kPlanFast || plan == kPlanFastPart;
 }
 
 cudaError_t launch_tma_batched(const void *d_descs, int n_img, int64_t total,

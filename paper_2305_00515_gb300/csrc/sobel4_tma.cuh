@@ -82,11 +82,15 @@ static_assert(kUnroll == 2 || kUnroll == 4, "the stage length must be a multiple
 #ifndef SOBEL4_TMA_FAST_CTAS
 #define SOBEL4_TMA_FAST_CTAS 4
 #endif
-// Kernel modes: every item, only fast-path items, only the other items.  A
-// kernel without the general path needs fewer registers and no spills.
-enum Mode : int { kAll = 0, kFastOnly = 1, kGeneralOnly = 2 };
+// Kernel modes: every item, only fast-path items, only the other items, and
+// (single images) only fast-path items of a width that is not a multiple of
+// the segment.  A kernel without the general path needs fewer registers and
+// no spills.
+enum Mode : int { kAll = 0, kFastOnly = 1, kGeneralOnly = 2, kFastPart = 3 };
 template <int MODE>
-constexpr int min_ctas() { return MODE == kFastOnly ? SOBEL4_TMA_FAST_CTAS : SOBEL4_TMA_MIN_CTAS; }
+__host__ __device__ constexpr bool fast_mode() { return MODE == kFastOnly || MODE == kFastPart; }
+template <int MODE>
+constexpr int min_ctas() { return fast_mode<MODE>() ? SOBEL4_TMA_FAST_CTAS : SOBEL4_TMA_MIN_CTAS; }
 
 // Upper bound on one mbarrier wait (globaltimer nanoseconds) before the
 // kernel gives up, records the failure and leaves.
@@ -316,96 +320,147 @@ __device__ __forceinline__ void gather_cols(const TmaImage &im, uint32_t base_a,
 // previous lane's last m elements and their own first 4-m; lane 0 writes the
 // head of the first chunk and lane 31 the tail of the last element by element,
 // so that no store touches another segment's columns.  Every lane calls these
-// (they shuffle); `on` is warp-uniform.
+// (they shuffle); `on` and m are warp-uniform, and an aligned row (m = 0)
+// takes plain vector stores without shuffling.
+//
+// PART: the segment runs past the image's last column; `wl` = W - x is the
+// number of this lane's four columns inside the image (may be <= 0 or > 4),
+// and no element at column >= W is written: a chunk that crosses column W is
+// written element by element up to it.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void st4_f32_realigned(float *p, const float v[4], bool on) {
+template <bool PART>
+__device__ __forceinline__ void st4_f32_realigned(float *p, const float v[4], bool on, int wl) {
   const int lane = threadIdx.x & 31;
   const uint32_t m = ((uint32_t)(uintptr_t)p >> 2) & 3u;  // elements past the chunk start
+  if (m == 0) {  // an aligned row (m is the same for every lane): plain stores
+    if (!on) return;
+    if (!PART || wl >= 4) {
+      *(float4 *)p = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (k < wl) p[k] = v[k];
+    }
+    return;
+  }
   const float p1 = __shfl_up_sync(0xffffffffu, v[1], 1);
   const float p2 = __shfl_up_sync(0xffffffffu, v[2], 1);
   const float p3 = __shfl_up_sync(0xffffffffu, v[3], 1);
   if (!on) return;
-  if (m == 0) {
-    *(float4 *)p = make_float4(v[0], v[1], v[2], v[3]);
-    return;
-  }
-  const float o0 = m == 1 ? p3 : (m == 2 ? p2 : p1);
-  const float o1 = m == 1 ? v[0] : (m == 2 ? p3 : p2);
-  const float o2 = m == 1 ? v[1] : (m == 2 ? v[0] : p3);
-  const float o3 = m == 1 ? v[2] : (m == 2 ? v[1] : v[0]);
+  const float o[4] = {m == 1 ? p3 : (m == 2 ? p2 : p1), m == 1 ? v[0] : (m == 2 ? p3 : p2),
+                      m == 1 ? v[1] : (m == 2 ? v[0] : p3), m == 1 ? v[2] : (m == 2 ? v[1] : v[0])};
   if (lane > 0) {
-    *(float4 *)(p - m) = make_float4(o0, o1, o2, o3);
+    if (!PART || wl + (int)m >= 4) {
+      *(float4 *)(p - m) = make_float4(o[0], o[1], o[2], o[3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j < wl + (int)m) (p - m)[j] = o[j];
+    }
   } else {
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-      if (k < 4 - (int)m) p[k] = v[k];
+      if (k < 4 - (int)m && (!PART || k < wl)) p[k] = v[k];
   }
   if (lane == 31) {
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-      if (k >= 4 - (int)m) p[k] = v[k];
+      if (k >= 4 - (int)m && (!PART || k < wl)) p[k] = v[k];
   }
 }
 
-__device__ __forceinline__ void st4_u8_realigned(uint8_t *p, uint32_t w, bool on) {
+template <bool PART>
+__device__ __forceinline__ void st4_u8_realigned(uint8_t *p, uint32_t w, bool on, int wl) {
   const int lane = threadIdx.x & 31;
   const uint32_t m = (uint32_t)(uintptr_t)p & 3u;
-  const uint32_t prev = __shfl_up_sync(0xffffffffu, w, 1);
-  if (!on) return;
-  if (m == 0) {
-    *(uint32_t *)p = w;
+  if (m == 0) {  // an aligned row: plain stores
+    if (!on) return;
+    if (!PART || wl >= 4) {
+      *(uint32_t *)p = w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (k < wl) p[k] = (uint8_t)(w >> (8 * k));
+    }
     return;
   }
+  const uint32_t prev = __shfl_up_sync(0xffffffffu, w, 1);
+  if (!on) return;
   if (lane > 0) {
-    *(uint32_t *)(p - m) = __funnelshift_l(prev, w, 8u * m);
+    const uint32_t o = __funnelshift_l(prev, w, 8u * m);
+    if (!PART || wl + (int)m >= 4) {
+      *(uint32_t *)(p - m) = o;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j < wl + (int)m) (p - m)[j] = (uint8_t)(o >> (8 * j));
+    }
   } else {
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-      if (k < 4 - (int)m) p[k] = (uint8_t)(w >> (8 * k));
+      if (k < 4 - (int)m && (!PART || k < wl)) p[k] = (uint8_t)(w >> (8 * k));
   }
   if (lane == 31) {
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-      if (k >= 4 - (int)m) p[k] = (uint8_t)(w >> (8 * k));
+      if (k >= 4 - (int)m && (!PART || k < wl)) p[k] = (uint8_t)(w >> (8 * k));
   }
 }
 
 // w0 holds elements 0, 1 and w1 elements 2, 3 (little-endian int16 pairs).
-__device__ __forceinline__ void st4_s16_realigned(int16_t *p, uint32_t w0, uint32_t w1, bool on) {
+template <bool PART>
+__device__ __forceinline__ void st4_s16_realigned(int16_t *p, uint32_t w0, uint32_t w1, bool on,
+                                                  int wl) {
   const int lane = threadIdx.x & 31;
   const uint32_t m = ((uint32_t)(uintptr_t)p >> 1) & 3u;
+  const uint64_t cur = ((uint64_t)w1 << 32) | w0;
+  if (m == 0) {  // an aligned row: plain stores
+    if (!on) return;
+    if (!PART || wl >= 4) {
+      *(uint2 *)p = make_uint2(w0, w1);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (k < wl) p[k] = (int16_t)(cur >> (16 * k));
+    }
+    return;
+  }
   const uint32_t q0 = __shfl_up_sync(0xffffffffu, w0, 1);
   const uint32_t q1 = __shfl_up_sync(0xffffffffu, w1, 1);
   if (!on) return;
-  if (m == 0) {
-    *(uint2 *)p = make_uint2(w0, w1);
-    return;
-  }
-  const uint64_t cur = ((uint64_t)w1 << 32) | w0, prev = ((uint64_t)q1 << 32) | q0;
+  const uint64_t prev = ((uint64_t)q1 << 32) | q0;
   const uint64_t out = (cur << (16u * m)) | (prev >> (64u - 16u * m));
   if (lane > 0) {
-    *(uint2 *)(p - m) = make_uint2((uint32_t)out, (uint32_t)(out >> 32));
+    if (!PART || wl + (int)m >= 4) {
+      *(uint2 *)(p - m) = make_uint2((uint32_t)out, (uint32_t)(out >> 32));
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j < wl + (int)m) (p - m)[j] = (int16_t)(out >> (16 * j));
+    }
   } else {
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-      if (k < 4 - (int)m) p[k] = (int16_t)(cur >> (16 * k));
+      if (k < 4 - (int)m && (!PART || k < wl)) p[k] = (int16_t)(cur >> (16 * k));
   }
   if (lane == 31) {
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-      if (k >= 4 - (int)m) p[k] = (int16_t)(cur >> (16 * k));
+      if (k >= 4 - (int)m && (!PART || k < wl)) p[k] = (int16_t)(cur >> (16 * k));
   }
 }
 
 // ---------------------------------------------------------------------------
 // RA (fast path only): the destination rows are not vector-aligned; the
-// realigned stores above take the place of the vector stores.
-template <int FMT, bool GEN, bool RA>
+// realigned stores above take the place of the vector stores.  PART (fast
+// path only): only the wl = W - x first of the lane's columns are stored.
+template <int FMT, bool GEN, bool RA, bool PART>
 __device__ __forceinline__ void store_rows(const TmaImage &im, uint8_t *row_a, uint8_t *row_b,
                                            int x, const uint32_t vx[4], const uint32_t vy[4],
                                            const uint32_t vd[4], const uint32_t vt[4],
                                            bool st_a, bool st_b, bool zero_a, bool zero_b,
-                                           uint32_t colmask, uint32_t framemask, bool vec) {
+                                           uint32_t colmask, uint32_t framemask, bool vec,
+                                           int wl) {
   if constexpr (FMT == kS16x4) {
     const uint64_t plane = (uint64_t)(uint32_t)im.H * im.dp;
     const uint32_t *vals[4] = {vx, vy, vd, vt};
@@ -420,11 +475,19 @@ __device__ __forceinline__ void store_rows(const TmaImage &im, uint8_t *row_a, u
         const uint2 lb = make_uint2(__byte_perm(v[0], v[1], 0x7632),
                                     __byte_perm(v[2], v[3], 0x7632));
         if constexpr (RA) {
-          st4_s16_realigned(pa, la.x, la.y, st_a);
-          st4_s16_realigned(pb, lb.x, lb.y, st_b);
-        } else {
+          st4_s16_realigned<PART>(pa, la.x, la.y, st_a, wl);
+          st4_s16_realigned<PART>(pb, lb.x, lb.y, st_b, wl);
+        } else if (!PART || wl >= 4) {
           if (st_a) *(uint2 *)pa = la;
           if (st_b) *(uint2 *)pb = lb;
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if (k >= wl) continue;
+            const uint32_t wa = k < 2 ? la.x : la.y, wb = k < 2 ? lb.x : lb.y;
+            if (st_a) pa[k] = (int16_t)(wa >> (16 * (k & 1)));
+            if (st_b) pb[k] = (int16_t)(wb >> (16 * (k & 1)));
+          }
         }
       } else {
 #pragma unroll
@@ -447,11 +510,18 @@ __device__ __forceinline__ void store_rows(const TmaImage &im, uint8_t *row_a, u
     float *pa = (float *)row_a + x, *pb = (float *)row_b + x;
     if (!GEN) {
       if constexpr (RA) {
-        st4_f32_realigned(pa, ga, st_a);
-        st4_f32_realigned(pb, gb, st_b);
-      } else {
+        st4_f32_realigned<PART>(pa, ga, st_a, wl);
+        st4_f32_realigned<PART>(pb, gb, st_b, wl);
+      } else if (!PART || wl >= 4) {
         if (st_a) *(float4 *)pa = make_float4(ga[0], ga[1], ga[2], ga[3]);
         if (st_b) *(float4 *)pb = make_float4(gb[0], gb[1], gb[2], gb[3]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (k >= wl) continue;
+          if (st_a) pa[k] = ga[k];
+          if (st_b) pb[k] = gb[k];
+        }
       }
     } else {
 #pragma unroll
@@ -492,11 +562,18 @@ __device__ __forceinline__ void store_rows(const TmaImage &im, uint8_t *row_a, u
     const uint2 wb = make_uint2(ub[0] | (ub[1] << 16), ub[2] | (ub[3] << 16));
     if (!GEN) {
       if constexpr (RA) {
-        st4_s16_realigned((int16_t *)pa, wa.x, wa.y, st_a);
-        st4_s16_realigned((int16_t *)pb, wb.x, wb.y, st_b);
-      } else {
+        st4_s16_realigned<PART>((int16_t *)pa, wa.x, wa.y, st_a, wl);
+        st4_s16_realigned<PART>((int16_t *)pb, wb.x, wb.y, st_b, wl);
+      } else if (!PART || wl >= 4) {
         if (st_a) *(uint2 *)pa = wa;
         if (st_b) *(uint2 *)pb = wb;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (k >= wl) continue;
+          if (st_a) pa[k] = (uint16_t)ua[k];
+          if (st_b) pb[k] = (uint16_t)ub[k];
+        }
       }
     } else if (vec && colmask == 0xFu) {
       if (st_a) *(uint2 *)pa = wa;
@@ -534,11 +611,18 @@ __device__ __forceinline__ void store_rows(const TmaImage &im, uint8_t *row_a, u
     const uint32_t wb = ub[0] | (ub[1] << 8) | (ub[2] << 16) | (ub[3] << 24);
     if (!GEN) {
       if constexpr (RA) {
-        st4_u8_realigned(pa, wa, st_a);
-        st4_u8_realigned(pb, wb, st_b);
-      } else {
+        st4_u8_realigned<PART>(pa, wa, st_a, wl);
+        st4_u8_realigned<PART>(pb, wb, st_b, wl);
+      } else if (!PART || wl >= 4) {
         if (st_a) *(uint32_t *)pa = wa;
         if (st_b) *(uint32_t *)pb = wb;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (k >= wl) continue;
+          if (st_a) pa[k] = (uint8_t)ua[k];
+          if (st_b) pb[k] = (uint8_t)ub[k];
+        }
       }
     } else if (vec && colmask == 0xFu) {
       if (st_a) *(uint32_t *)pa = wa;
@@ -687,7 +771,8 @@ __device__ __forceinline__ void issue_stage(const TmaImage &im, const ItemCtx &c
 
 // FULL: every output row of both strips lies inside the image (no row checks).
 // RA (fast path): realigned stores for a destination that is not vector-aligned.
-template <int FMT, bool GEN, bool FULL, int ST, bool RA>
+// PART (fast path): the segment runs past column W-1; stores stop at column W.
+template <int FMT, bool GEN, bool FULL, int ST, bool RA, bool PART>
 // ya: first row of strip a; R: this item's strip height (see strip_rows).
 __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg, int ya,
                                          int R, int lane, ItemCtx &cx, unsigned int *err) {
@@ -695,6 +780,7 @@ __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg
   const int H = im.H, W = im.W;
   const int x0 = seg * kCols;
   const int x = x0 + kNC * lane;
+  const int wl = W - x;  // this lane's columns inside the image (PART)
   const int yb = ya + R;
   const int steps = R + 4;
   const int n_stages = (steps + kStageRows - 1) / kStageRows;
@@ -789,8 +875,8 @@ __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg
           zero_b = yb + i < 2 || yb + i > H - 3;
         }
       }
-      store_rows<FMT, GEN, RA>(im, row_a, row_b, x, vx, vy, vd, vt, st_a, st_b, zero_a, zero_b,
-                               colmask, framemask, vec);
+      store_rows<FMT, GEN, RA, PART>(im, row_a, row_b, x, vx, vy, vd, vt, st_a, st_b, zero_a,
+                                     zero_b, colmask, framemask, vec, wl);
       row_a += im.dp;
       row_b += im.dp;
     } else {
@@ -847,9 +933,10 @@ __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         if (f[q] >= yr[t] && f[q] < yr[t] + nr[t] && (q < 2 || f[q] > 1)) {
-          if constexpr (RA) {
+          if constexpr (RA || PART) {
 #pragma unroll
-            for (int k = 0; k < kNC; ++k) zero_px<FMT>(im, f[q], x + k);
+            for (int k = 0; k < kNC; ++k)
+              if (!PART || k < wl) zero_px<FMT>(im, f[q], x + k);
           } else {
             zero_row4<FMT>(im, f[q], x);
           }
@@ -863,7 +950,7 @@ __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int c = fc[q];
-        if (c < x0 || c >= x0 + kCols || (q >= 2 && c < 2)) continue;
+        if (c < x0 || c >= x0 + kCols || c >= W || (q >= 2 && c < 2)) continue;
         for (int r = lane; r < na + nb; r += 32) zero_px<FMT>(im, r < na ? ya + r : yb + r - na, c);
       }
     }
@@ -871,16 +958,15 @@ __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg
   return true;
 }
 
-// An item for the fast path: every lane's four columns inside the image and
-// either a border rule the staging serves as is (VALID, frame zeroed afterwards;
-// CONSTANT0 with tensor staging, whose copies zero-fill) or every input row and
-// column inside the image.
+// An item for the fast path: a border rule the staging serves as is (VALID,
+// frame zeroed afterwards; CONSTANT0 with tensor staging, whose copies
+// zero-fill), with any segment, the last one of a ragged width included
+// (PART); or every input row and column inside the image.
 template <int ST>
 __device__ __forceinline__ bool fast_item(const TmaImage &im, int border, int seg, int ya,
                                           int R, int fmt) {
   const int x0 = seg * kCols;
   (void)fmt;
-  if (x0 + kCols > im.W) return false;
   if (border == kValid || (ST == kTensor && border == kConstant0)) return true;
   return x0 >= 2 && x0 + kCols + 2 <= im.W && ya >= 2 && ya + 2 * R + 2 <= im.H;
 }
@@ -941,26 +1027,38 @@ __device__ __forceinline__ int strip_rows(const TmaImage &im, int band, int R) {
 }
 
 // Runs one item through the variant its geometry needs; a kernel that runs
-// only fast items (or only the others) carries only that code.
-template <int FMT, int MODE, int ST>
+// only fast items (or only the others) carries only that code.  Each variant
+// is a large unrolled body, and warps of one SM running several of them at
+// once miss in the instruction cache (measured on ragged batches: 56 % hits
+// with three fast variants live, 98 % with one).  So the batched kernel
+// (ONE) and the single-image kernel of a ragged width (kFastPart) send every
+// fast item through a single body: row checks, stores that stop at column W,
+// and, in a kernel that may meet unaligned destinations (kAll), the realigned
+// stores, which fall through to plain vector stores on an aligned row.  The
+// lean single-image kernel (kFastOnly, width a multiple of the segment) keeps
+// the check-free body for full bands and carries no other.
+template <int FMT, int MODE, int ST, bool ONE>
 __device__ __forceinline__ bool run_item(const TmaImage &im, int border, int seg, int ya, int R,
                                          int lane, ItemCtx &cx, unsigned int *err, bool fast) {
-  if (MODE != kFastOnly && !fast)
-    return tma_item<FMT, true, false, ST, false>(im, border, seg, ya, R, lane, cx, err);
-  const bool full = ya + 2 * R <= im.H;
-  if constexpr (MODE == kFastOnly) {
-    if (full) return tma_item<FMT, false, true, ST, false>(im, border, seg, ya, R, lane, cx, err);
-    return tma_item<FMT, false, false, ST, false>(im, border, seg, ya, R, lane, cx, err);
-  } else if constexpr (MODE == kAll) {
-    constexpr int vec_need = vec_bytes(FMT);
-    if (im.dst_align >= vec_need) {
-      if (full) return tma_item<FMT, false, true, ST, false>(im, border, seg, ya, R, lane, cx, err);
-      return tma_item<FMT, false, false, ST, false>(im, border, seg, ya, R, lane, cx, err);
-    }
-    if (full) return tma_item<FMT, false, true, ST, true>(im, border, seg, ya, R, lane, cx, err);
-    return tma_item<FMT, false, false, ST, true>(im, border, seg, ya, R, lane, cx, err);
+  if (!fast_mode<MODE>() && !fast)
+    return tma_item<FMT, true, false, ST, false, false>(im, border, seg, ya, R, lane, cx, err);
+  constexpr bool kRA = MODE == kAll;  // realigned stores possible in this kernel
+  if constexpr (ONE || MODE == kFastPart) {
+    return tma_item<FMT, false, false, ST, kRA, true>(im, border, seg, ya, R, lane, cx, err);
+  } else if constexpr (MODE == kFastOnly) {
+    // The host plans this kernel only for widths that are a multiple of kCols.
+    if (ya + 2 * R <= im.H)
+      return tma_item<FMT, false, true, ST, false, false>(im, border, seg, ya, R, lane, cx, err);
+    return tma_item<FMT, false, false, ST, false, false>(im, border, seg, ya, R, lane, cx, err);
+  } else {
+    if (im.dst_align < vec_bytes(FMT))
+      return tma_item<FMT, false, false, ST, true, true>(im, border, seg, ya, R, lane, cx, err);
+    if (im.W % kCols != 0)
+      return tma_item<FMT, false, false, ST, false, true>(im, border, seg, ya, R, lane, cx, err);
+    if (ya + 2 * R <= im.H)
+      return tma_item<FMT, false, true, ST, false, false>(im, border, seg, ya, R, lane, cx, err);
+    return tma_item<FMT, false, false, ST, false, false>(im, border, seg, ya, R, lane, cx, err);
   }
-  return false;
 }
 
 template <int ST>
@@ -1006,8 +1104,8 @@ __global__ void __launch_bounds__(kWarps * 32, min_ctas<MODE>())
     cx.lose_stage = item == 0 ? im.lose_stage : -1;
     const int ya = band * 2 * R, Ri = strip_rows(im, band, R);
     const bool fast = fast_item<ST>(im, border, seg, ya, Ri, FMT);
-    if ((MODE == kFastOnly && !fast) || (MODE == kGeneralOnly && fast)) continue;
-    if (!run_item<FMT, MODE, ST>(im, border, seg, ya, Ri, lane, cx, err, fast)) break;
+    if ((fast_mode<MODE>() && !fast) || (MODE == kGeneralOnly && fast)) continue;
+    if (!run_item<FMT, MODE, ST, false>(im, border, seg, ya, Ri, lane, cx, err, fast)) break;
   }
   if (lane == 0) {
     __threadfence();  // this warp's last fetch is performed before it counts out
@@ -1049,14 +1147,14 @@ __global__ void __launch_bounds__(kWarps * 32, min_ctas<MODE>())
     item_coords<ST>(im, border, R, (int)(item - d->item0), &seg, &band);
     const int ya = band * 2 * R, Ri = strip_rows(im, band, R);
     const bool fast = fast_item<ST>(im, border, seg, ya, Ri, FMT);
-    if ((MODE == kFastOnly && !fast) || (MODE == kGeneralOnly && fast)) continue;
+    if ((fast_mode<MODE>() && !fast) || (MODE == kGeneralOnly && fast)) continue;
     if (ST == kTensor && lo != cur) {
       if (lane == 0) tensormap_acquire(&d->map);
       cur = lo;
     }
     cx.map = &d->map;
     cx.lose_stage = -1;
-    if (!run_item<FMT, MODE, ST>(im, border, seg, ya, Ri, lane, cx, err, fast)) break;
+    if (!run_item<FMT, MODE, ST, true>(im, border, seg, ya, Ri, lane, cx, err, fast)) break;
   }
 }
 

@@ -56,10 +56,21 @@ int resident_of() {
     }                                                                               \
   } while (0)
 
+// The single-image kernel has one more mode: fast items of a ragged width.
+#define SOBEL4_TMA_SWITCH_SINGLE(MODE_, ST_, CALL)                                  \
+  do {                                                                              \
+    if ((MODE_) == tma::kFastPart) {                                                \
+      if ((ST_) == tma::kTensor) { CALL(tma::kFastPart, tma::kTensor); }            \
+      else { CALL(tma::kFastPart, tma::kBulk); }                                    \
+    } else {                                                                        \
+      SOBEL4_TMA_SWITCH(MODE_, ST_, CALL);                                          \
+    }                                                                               \
+  } while (0)
+
 template <int FMT>
 int TmaFmt<FMT>::resident(int mode, int st) {
 #define SOBEL4_RES(M, S) return tma_detail::resident_of<FMT, M, S>()
-  SOBEL4_TMA_SWITCH(mode, st, SOBEL4_RES);
+  SOBEL4_TMA_SWITCH_SINGLE(mode, st, SOBEL4_RES);
 #undef SOBEL4_RES
 }
 
@@ -70,7 +81,7 @@ void TmaFmt<FMT>::single(int mode, int st, const CUtensorMap &map, const tma::Tm
 #define SOBEL4_SINGLE(M, S)                                                                  \
   tma::tma_single_kernel<FMT, M, S><<<(unsigned)grid, tma::kWarps * 32, 0, s>>>(map, im, border, \
                                                                            R, items, pair, err)
-  SOBEL4_TMA_SWITCH(mode, st, SOBEL4_SINGLE);
+  SOBEL4_TMA_SWITCH_SINGLE(mode, st, SOBEL4_SINGLE);
 #undef SOBEL4_SINGLE
 }
 

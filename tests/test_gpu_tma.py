@@ -127,3 +127,31 @@ def test_realigned_stores_every_phase(handles, fmt):
                                                  dst_pitch=W * e + e, dst_offset=doff)
                         assert guards, f"{name} {H}x{W} {border} doff {doff}: outside payload"
                         assert_same(got, want, f"{name} {H}x{W} {border} doff {doff} sp {sp}")
+
+
+RAGGED_W = (1, 2, 3, 4, 5, 7, 126, 127, 129, 131, 133, 134, 254, 255, 257, 259, 383)
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+def test_ragged_last_segment_fast_path(handles, fmt):
+    """Widths that end inside a 128-column segment, under the rules the fast
+    path serves at any width (VALID; CONSTANT0 from aligned rows): the last
+    segment's lanes stop their stores at column W, into vector-aligned and
+    lane-shifted destinations, from tensor- and bulk-staged sources, with the
+    frame columns W-2 and W-1 zeroed inside that segment.  The guard bytes
+    after each row's payload must survive."""
+    e = ELEM[fmt]
+    for W in RAGGED_W:
+        H = 21 + W % 7
+        img = np.random.default_rng(W).integers(0, 256, size=(H, W), dtype=np.uint8)
+        for border in ("valid", "constant0"):
+            want = oracle.sobel4(img, border, fmt)
+            for (dp, doff) in ((ceil16(W * e), 0), (W * e + e, e), (ceil16(W * e) + 16, 3 * e)):
+                for (sp, soff) in ((ceil16(W), 0), (W + 1, 5)):
+                    for name in ("tma", "tma_r4"):
+                        got, guards = run_placed(torch, handles[name], img, border, fmt,
+                                                 src_pitch=sp, src_offset=soff,
+                                                 dst_pitch=dp, dst_offset=doff)
+                        what = f"{name} {H}x{W} {border} dp {dp} doff {doff} sp {sp}"
+                        assert guards, f"{what}: write outside the payload"
+                        assert_same(got, want, what)
