@@ -24,7 +24,7 @@ def h():
 
 
 def run_batch(h, imgs, border, fmt, layout=None):
-    elem = {"f32": 4, "u8": 1, "s16x4": 2}[fmt]
+    elem = {"f32": 4, "u8": 1, "s16x4": 2, "u16": 2, "edge8": 1}[fmt]
     srcs, outs, descs = [], [], []
     for i, img in enumerate(imgs):
         H, W = img.shape
@@ -58,7 +58,7 @@ def test_batch_equals_single_runs_all_modes(h):
     layout = [(int(rng.integers(0, 9)), int(rng.integers(0, 4)), int(rng.integers(0, 5)),
                4 * int(rng.integers(0, 4))) for _ in imgs]
     for border in ("valid", "replicate", "reflect101", "constant0"):
-        for fmt in ("f32", "u8", "s16x4"):
+        for fmt in ("f32", "u8", "s16x4", "u16", "edge8"):
             res = run_batch(h, imgs, border, fmt, layout)
             for img, (got, guards) in zip(imgs, res):
                 assert guards
