@@ -267,13 +267,17 @@ def bench_batched(torch, pkg, synth, reps: int = 5):
 
 
 def bench_ablation(torch, pkg, synth):
-    """The paper's kernel ladder (Table 2, 5x5 four-directional) re-measured
-    here: GM = the direct 25-tap kernel, RG = the factored register-window
-    scheme with per-lane copies and with TMA staging, plus the tensor-core
-    variant; F32 VALID, mean CUDA-event time per launch (images up to 2048^2
-    stay in L2 between launches, as in the paper's repeated runs)."""
-    variants = (("GM_direct", "direct"), ("RG_lanecopy", "rg_lanecopy"), ("RG_tma", "rg"),
-                ("TC_tensor_core", "tc"))
+    """The paper's kernel ladder (Table 1, 5x5 four-directional) re-measured
+    here: GM = the direct 25-tap kernel; SM, SM-P, RG, RG-v1, RG-v2 = the
+    ladder variants in the paper's plain form (shared-memory tile, with
+    prefetching, register window with the diagonals direct / through K_d+ /
+    fully decomposed); then the GB300 kernels: the packed register window
+    with per-lane copies and with TMA staging, and the tensor-core variant.
+    F32 VALID, mean CUDA-event time per launch (images up to 2048^2 stay in
+    L2 between launches, as in the paper's repeated runs)."""
+    variants = (("GM_direct", "direct"), ("SM", "ladder_sm"), ("SM_P", "ladder_sm_p"),
+                ("RG", "ladder_rg"), ("RG_v1", "ladder_rg_v1"), ("RG_v2", "ladder_rg_v2"),
+                ("RG_lanecopy", "rg_lanecopy"), ("RG_tma", "rg"), ("TC_tensor_core", "tc"))
     res = {}
     stream = torch.cuda.Stream()
     for side in (512, 1024, 2048, 8192):

@@ -107,15 +107,32 @@ typedef enum {
  * banded f16 matrix products with fp32 accumulators in tensor memory) on the
  * images it covers (VALID, F32, source and destination rows on 16-byte
  * boundaries, width a multiple of 4) and RG on the others; AUTO uses it for
- * a shape only where sobel4_tune measured it fastest.  All variants give
- * identical results.
+ * a shape only where sobel4_tune measured it fastest.  The LADDER_* variants
+ * are the paper's kernel ladder (Section 5.2, Table 1), kept to re-measure its
+ * ablation: LADDER_SM stages a 32 x 8 tile and its halo in shared memory and
+ * sums the 25 taps per mask there; LADDER_SM_P adds prefetching (the next
+ * tile's loads issued before the current tile is summed, double-buffered);
+ * LADDER_RG is the plain register window (one column per lane, 28 output
+ * columns per warp, neighbours by warp shuffles, K_x and K_y factored, the
+ * diagonals summed over a 5x5 register window); LADDER_RG_V1 computes the
+ * diagonals through K_d+ (factored) and K_d- (Eq. 10-15); LADDER_RG_V2 also
+ * factors K_d- (Eq. 16-19).  They serve every border rule and format, take
+ * rows_per_strip as the RG strip height (default: up to 64 rows, fewer where
+ * an image would leave under 16 warps per SM), run one launch per
+ * image of a batch, and ignore runtime weights (a handle with weights set
+ * runs those as any other handle does).  All variants give identical results.
  */
 typedef enum {
   SOBEL4_VARIANT_AUTO = 0,
   SOBEL4_VARIANT_DIRECT = 1,
   SOBEL4_VARIANT_RG = 2,
   SOBEL4_VARIANT_RG_LANECOPY = 3,
-  SOBEL4_VARIANT_TC = 4
+  SOBEL4_VARIANT_TC = 4,
+  SOBEL4_VARIANT_LADDER_SM = 5,
+  SOBEL4_VARIANT_LADDER_SM_P = 6,
+  SOBEL4_VARIANT_LADDER_RG = 7,
+  SOBEL4_VARIANT_LADDER_RG_V1 = 8,
+  SOBEL4_VARIANT_LADDER_RG_V2 = 9
 } sobel4_variant;
 
 /* Creation options; pass NULL for defaults (all fields 0). */

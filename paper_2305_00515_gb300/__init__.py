@@ -32,7 +32,8 @@ __all__ = [
 _PKG = os.path.dirname(os.path.abspath(__file__))
 BORDERS = {"valid": 0, "replicate": 1, "reflect101": 2, "constant0": 3}
 FORMATS = {"f32": 0, "u8": 1, "s16x4": 2, "u16": 3, "edge8": 4}
-VARIANTS = {"auto": 0, "direct": 1, "rg": 2, "rg_lanecopy": 3, "tc": 4}
+VARIANTS = {"auto": 0, "direct": 1, "rg": 2, "rg_lanecopy": 3, "tc": 4, "ladder_sm": 5,
+            "ladder_sm_p": 6, "ladder_rg": 7, "ladder_rg_v1": 8, "ladder_rg_v2": 9}
 OPERATORS = {"4dir5x5": 0, "2dir5x5": 1, "2dir3x3": 2}
 ELEM_SIZE = {"f32": 4, "u8": 1, "s16x4": 2, "u16": 2, "edge8": 1}
 STATUS = {0: "SOBEL4_OK", 1: "SOBEL4_ERR_INVALID_ARG", 2: "SOBEL4_ERR_UNSUPPORTED",

@@ -325,6 +325,18 @@ unsigned int *next_pair(sobel4_ctx *h) {
 }
 
 // pair: the RG kernel's counter pair, or nullptr for the handle's next one.
+// The paper's kernel ladder (variants LADDER_*): one launch per image.
+bool is_ladder(int variant) {
+  return variant >= SOBEL4_VARIANT_LADDER_SM && variant <= SOBEL4_VARIANT_LADDER_RG_V2;
+}
+// Output rows per warp strip of the ladder's RG kernels: up to 64, fewer
+// where that leaves under 16 warps per SM (small images).
+int ladder_rows(int32_t H, int32_t W, int sm_count) {
+  const int64_t cols = (W + 27) / 28, target = (int64_t)sm_count * 16;
+  const int64_t rows = (int64_t)H * cols / std::max<int64_t>(1, target);
+  return (int)std::max<int64_t>(8, std::min<int64_t>(64, rows));
+}
+
 sobel4_status launch_one(sobel4_ctx *h, const uint8_t *src, size_t sp, void *dst, size_t dp,
                          int32_t H, int32_t W, int border, int fmt, cudaStream_t stream,
                          unsigned int *pair = nullptr) {
@@ -343,6 +355,11 @@ sobel4_status launch_one(sobel4_ctx *h, const uint8_t *src, size_t sp, void *dst
   } else if (h->variant == SOBEL4_VARIANT_DIRECT) {
     const ImageDesc im = make_desc(src, sp, dst, dp, H, W, 1, h->nc);
     e = launch_direct(im, border, fmt, nullptr, 2, h->thr, stream);
+  } else if (is_ladder(h->variant)) {
+    const ImageDesc im = make_desc(src, sp, dst, dp, H, W, 1, h->nc);
+    e = launch_ladder(im, border, fmt, h->variant - SOBEL4_VARIANT_LADDER_SM,
+                      h->rows_per_strip > 0 ? h->rows_per_strip : ladder_rows(H, W, h->sm_count),
+                      h->thr, stream);
   } else if (use_tc(h, src, sp, dst, dp, H, W, border, fmt)) {
     e = launch_tc_single(src, sp, dst, dp, H, W, border, fmt, h->sm_count, h->d_err, stream,
                          h->lose_stage);
@@ -424,7 +441,7 @@ const char *sobel4_status_string(sobel4_status s) {
 sobel4_status sobel4_create(sobel4_handle *out, int32_t device, const sobel4_options *opt) {
   if (!out) return SOBEL4_ERR_INVALID_ARG;
   *out = nullptr;
-  if (opt && (opt->variant < 0 || opt->variant > SOBEL4_VARIANT_TC || opt->rows_per_strip < 0 ||
+  if (opt && (opt->variant < 0 || opt->variant > SOBEL4_VARIANT_LADDER_RG_V2 || opt->rows_per_strip < 0 ||
               opt->rows_per_strip > 4096 || opt->persistent_ctas_per_sm < 0 ||
               opt->persistent_ctas_per_sm > 64 ||
               (opt->columns_per_lane != 0 && opt->columns_per_lane != 2 &&
@@ -575,7 +592,7 @@ sobel4_status sobel4_device_status(sobel4_handle h) {
 uint64_t sobel4_launch_count(sobel4_handle h) { return h ? h->launches : 0; }
 
 sobel4_status sobel4_set_variant(sobel4_handle h, int32_t variant) {
-  if (!h || variant < SOBEL4_VARIANT_AUTO || variant > SOBEL4_VARIANT_TC)
+  if (!h || variant < SOBEL4_VARIANT_AUTO || variant > SOBEL4_VARIANT_LADDER_RG_V2)
     return SOBEL4_ERR_INVALID_ARG;
   h->variant = variant;
   return SOBEL4_OK;
@@ -638,7 +655,7 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
     else end_in = std::max(end_in, v.e);
   }
   DeviceGuard g(h->device);
-  if (h->variant == SOBEL4_VARIANT_DIRECT || h->custom) {
+  if (h->variant == SOBEL4_VARIANT_DIRECT || is_ladder(h->variant) || h->custom) {
     for (int32_t i = 0; i < n; ++i) {
       const sobel4_image &m = imgs[i];
       sobel4_status s = launch_one(h, m.src, m.src_pitch, m.dst, m.dst_pitch, m.height, m.width,

@@ -85,6 +85,14 @@ cudaError_t launch_tc_single(const uint8_t *src, size_t sp, void *dst, size_t dp
 cudaError_t launch_direct(const ImageDesc &im, int border, int fmt, const Masks4 *masks,
                           int radius, int32_t thr, cudaStream_t st);
 
+// The paper's kernel ladder (Table 1), Eq. (3) masks only: shared-memory tile,
+// the same with the next tile prefetched, and the plain register window with
+// the diagonals direct (RG), through K_d+ (RG-v1) and fully decomposed
+// (RG-v2); `rows`: output rows per warp strip of the RG kernels.
+enum LadderKind : int { kLadderSM = 0, kLadderSMP, kLadderRG, kLadderRGv1, kLadderRGv2 };
+cudaError_t launch_ladder(const ImageDesc &im, int border, int fmt, int kind, int rows,
+                          int32_t thr, cudaStream_t st);
+
 // Masks of the operators besides the four-directional 5x5: op 1 = the
 // two-directional 5x5 (K_x, K_y of Eq. 3), op 2 = the two-directional 3x3 of
 // Eq. (1) centred in the 5x5 grid; diagonal masks zero.  Returns the support

@@ -52,7 +52,7 @@ def test_null_handle_queries(lib):
 
 def test_create_rejects_bad_options(lib):
     h = ctypes.c_void_p()
-    bad = pkg.Options(7, 0, 0, 0)
+    bad = pkg.Options(10, 0, 0, 0)  # one past the last variant
     assert lib.sobel4_create(ctypes.byref(h), 0, ctypes.byref(bad)) == 1
     assert not h.value
     assert lib.sobel4_create(None, 0, None) == 1
