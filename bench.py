@@ -62,6 +62,9 @@ def parse_args():
     ap.add_argument("--video-frames", type=int, default=2000)
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the Poisson serving run (the full configuration is 60)")
+    ap.add_argument("--profile-variants", action="store_true",
+                    help="run every kernel variant twice on the workload image and exit "
+                         "(a capture target for ncu; prints no JSON line)")
     return ap.parse_args()
 
 
@@ -644,8 +647,39 @@ def run_ours(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+PROFILE_VARIANTS = ("direct", "ladder_sm", "ladder_sm_p", "ladder_rg", "ladder_rg_v1",
+                    "ladder_rg_v2", "rg_lanecopy", "rg", "tc")
+
+
+def profile_variants():
+    """Each kernel variant (GM, the paper's ladder, the GB300 kernels) launched
+    twice on the 8192x8192 rects+noise image, F32 VALID, default options."""
+    import torch
+
+    import paper_2305_00515_gb300 as pkg
+    import synth
+    img = synth.rects_noise(H, W, 0)
+    src = torch.from_numpy(img).cuda()
+    out = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    for v in PROFILE_VARIANTS:
+        st, h = pkg.sobel4_create(0, pkg.VARIANTS[v])
+        assert st == 0, pkg.sobel4_status_string(st)
+        for _ in range(2):
+            rc = pkg.sobel4_run(h, src.data_ptr(), W, out.data_ptr(), 4 * W, H, W, 0, 0,
+                                stream.cuda_stream)
+            assert rc == 0, pkg.sobel4_status_string(rc)
+        stream.synchronize()
+        assert pkg.sobel4_device_status(h) == 0
+        pkg.sobel4_destroy(h)
+        print(f"{v}: ok", flush=True)
+
+
 def main():
     args = parse_args()
+    if args.profile_variants:
+        profile_variants()
+        return
     if args.impl == "reference":
         # the CPU oracle runs on rank 0 alone; other ranks exit without work
         run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))
