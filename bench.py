@@ -14,7 +14,8 @@ Default (our arm): prints one JSON line with
                  over its mean CUDA-event duration, against the measured HBM peak;
   e2e            the same metric through sobel4_run_host (pinned host buffers,
                  host->device copy, kernel, device->host copy every step);
-  cpu_baseline   the CPU oracle on this host's cores over a bounded sample;
+  cpu_baseline   the CPU oracle on all of this host's cores over a bounded sample
+                 (and on one core: "one_core");
   clocks         nvidia-smi SM clocks and throttle reasons sampled during the run.
 Under torchrun (N > 1) each rank processes its own image (weak scaling, no
 collective on the data path); the time is the max over ranks.
@@ -442,30 +443,38 @@ def bench_serving(torch, pkg, synth, seconds: float):
 
 # ----------------------------------------------------------------------------
 def cpu_baseline(img, seconds: float):
+    """The oracle over bands of the image on all host threads for `seconds`,
+    then on one thread for a third of that (both reported)."""
+    import numpy as np
+
     import oracle
     o = oracle.default()
     cores = oracle.cpu_count()
-    out = None
-    import numpy as np
     out = np.empty(img.shape, np.float32)
-    # rows of the same image, whole bands at a time, until `seconds` have passed
-    rows_done = 0
-    t0 = time.perf_counter()
-    band = 1024
-    y = 0
-    while True:
-        y1 = min(img.shape[0], y + band)
-        o.run_into(img[max(0, y - 2):min(img.shape[0], y1 + 2)],
-                   out[max(0, y - 2):min(img.shape[0], y1 + 2)], "valid", "f32", threads=cores)
-        rows_done += y1 - y
-        y = 0 if y1 >= img.shape[0] else y1
-        if time.perf_counter() - t0 >= seconds:
-            break
-    dt = time.perf_counter() - t0
+
+    def rate(threads: int, budget: float):
+        # rows of the same image, whole bands at a time, until `budget` has passed
+        rows_done, y, band = 0, 0, 1024 if threads > 1 else 128
+        t0 = time.perf_counter()
+        while True:
+            y1 = min(img.shape[0], y + band)
+            o.run_into(img[max(0, y - 2):min(img.shape[0], y1 + 2)],
+                       out[max(0, y - 2):min(img.shape[0], y1 + 2)], "valid", "f32",
+                       threads=threads)
+            rows_done += y1 - y
+            y = 0 if y1 >= img.shape[0] else y1
+            if time.perf_counter() - t0 >= budget:
+                break
+        return rows_done, time.perf_counter() - t0
+
+    rows_1, dt_1 = rate(1, seconds / 3)
+    rows_done, dt = rate(cores, seconds)
     px = rows_done * img.shape[1]
     return {"value": px / dt / 1e9, "unit": "Gpixel/s", "cores": cores, "kind": "oracle",
             "sample": f"{rows_done} rows of the 8192-wide image (1024-row bands + 2-row halos), "
-                      f"{dt:.1f} s on {cores} host threads"}
+                      f"{dt:.1f} s on {cores} host threads",
+            "one_core": {"value": rows_1 * img.shape[1] / dt_1 / 1e9, "unit": "Gpixel/s",
+                         "sample": f"{rows_1} rows (128-row bands), {dt_1:.1f} s on 1 thread"}}
 
 
 def run_reference(args, world, rank):
