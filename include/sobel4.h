@@ -323,10 +323,13 @@ sobel4_status sobel4_run_batched_static(const sobel4_image *h_images, int32_t n,
 
 /*
  * Autotuner: the per-shape form of the paper's block-configuration study
- * (Fig. 5, Section 5.2).  sobel4_tune times the register-window kernel for
- * every candidate (2 or 4 columns per thread x strip height R in 8, 16, 32,
- * 64; restricted by options that force either) on a height x width image in
- * scratch device buffers it allocates and frees, and records the fastest in
+ * (Fig. 5, Section 5.2).  sobel4_tune times, on a height x width image in
+ * scratch device buffers it allocates and frees, the tensor-core kernel
+ * (where it applies), the TMA-staged register-window kernel at strip heights
+ * R = 8, 16, 24 ... 128 (no taller than the image needs) plus its built-in
+ * choice, and the lane-copy kernel (2 or 4 columns per thread x R in 8, 16,
+ * 32, 64); options that force a variant, columns or R restrict the
+ * candidates.  It records the fastest in
  * the handle's table under the bucket (ceil log2 height, ceil log2 width,
  * fmt).  Later sobel4_run calls whose shape falls in that bucket use it.
  * *best_us (may be NULL) receives the chosen candidate's median time in
@@ -336,10 +339,12 @@ sobel4_status sobel4_tune(sobel4_handle h, int32_t height, int32_t width, sobel4
                           sobel4_format fmt, float *best_us);
 
 /*
- * Autotune the batched kernel on a real batch (columns per thread 2/4 x strip
- * height 8/16/32 x 2/4/6 CTAs per SM): runs sobel4_run_batched repeatedly on
- * `h_images` (their outputs are written), keeps the fastest for batches of
- * format `fmt`.  Synchronous.  Errors as sobel4_run_batched.
+ * Autotune the batched kernel on a real batch: the TMA-family batched
+ * kernel at strip heights 8, 16, 32, 48, 64, 96, 128 and the lane-copy one
+ * (columns per thread 2/4 x strip height 8/16/32 x 2/4/6 CTAs per SM).  Runs
+ * sobel4_run_batched repeatedly on `h_images` (their outputs are written)
+ * and keeps the fastest for batches of format `fmt`.  Synchronous.  Errors as
+ * sobel4_run_batched.
  */
 sobel4_status sobel4_tune_batched(sobel4_handle h, const sobel4_image *h_images, int32_t n,
                                   sobel4_border border, sobel4_format fmt, float *best_us);
