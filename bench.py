@@ -175,11 +175,20 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash() -> str:
+# Sources of each timed kernel family: its own files plus the shared device
+# headers (arithmetic, PTX wrappers, descriptors, launch declarations).
+KERNEL_SOURCES = {"tma": "sobel4_tma", "lanecopy": "sobel4_rg", "tc": "sobel4_tc"}
+SHARED_SOURCES = ("sobel4_arith.cuh", "sobel4_device.cuh", "sobel4_ptx.cuh", "sobel4_launch.h")
+
+
+def kernel_source_hash(stem: str = "tma") -> str:
+    """SHA-256 (first 16 hex digits) of the sources the `stem` kernel family
+    is compiled from; a committed ncu summary carries the value it was taken on."""
     csrc = os.path.join(ROOT, "paper_2305_00515_gb300", "csrc")
     h = hashlib.sha256()
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
+        if name in SHARED_SOURCES or (name.startswith(KERNEL_SOURCES.get(stem, "\0")) and
+                                      name.endswith((".cu", ".cuh", ".h"))):
             with open(os.path.join(csrc, name), "rb") as f:
                 h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
@@ -204,7 +213,7 @@ def recorded_traffic(stem: str):
             if ":" in line:
                 k, v = line.split(":", 1)
                 fields[k.strip()] = v.strip()
-    if fields.get("kernel_source_hash") != kernel_source_hash():
+    if fields.get("kernel_source_hash") != kernel_source_hash(stem):
         return None
     try:
         return int(fields["dram_bytes_per_launch"])
@@ -420,14 +429,24 @@ def bench_serving(torch, pkg, synth, seconds: float):
                 "max_batch": stats["max_batch_seen"], "span_s": span}
 
     res = {}
-    for name, plain in (("batched", 0), ("plain_launch_per_request", 1)):
-        res[name] = run(plain, t_arr)
-    # Saturation bursts: one short unrecorded burst per mode, then two rounds
-    # alternating the modes; each mode reports its faster round (a single
-    # burst's span moved by up to 2x with what ran before it in the process).
+    # One short unrecorded burst per mode first (kernel loading, first use of
+    # the pinned pools).  Then the Poisson trace twice per mode, alternating
+    # the modes; each mode reports its round with the lower p99 (on one box
+    # the same mode's p99 moved by 3x between rounds: the 3840x2160 frames'
+    # host-link copies dominate the tail and their speed drifts).
     burst = np.zeros(min(len(t_arr), 2000))
     for plain in (1, 0):
         run(plain, burst[:200])
+    poisson = {"batched": [], "plain_launch_per_request": []}
+    for _ in range(2):
+        for name, plain in (("plain_launch_per_request", 1), ("batched", 0)):
+            poisson[name].append(run(plain, t_arr))
+    for name, rs in poisson.items():
+        res[name] = min(rs, key=lambda r: r["p99_ms"])
+        res[name]["p99_rounds_ms"] = [r["p99_ms"] for r in rs]
+    # Saturation bursts: two rounds alternating the modes; each mode reports
+    # its faster round (a single burst's span moved by up to 2x with what ran
+    # before it in the process).
     rounds = {"burst_batched": [], "burst_plain": []}
     for _ in range(2):
         for name, plain in (("burst_plain", 1), ("burst_batched", 0)):
@@ -437,8 +456,9 @@ def bench_serving(torch, pkg, synth, seconds: float):
         res[name]["spans_s"] = [r["span_s"] for r in rs]
     return {"workload": f"Poisson 400 req/s for {seconds:.0f} s ({len(t_arr)} requests), "
                         "640x480 40% / 1280x720 30% / 1920x1080 20% / 3840x2160 10%, F32, "
-                        "8 GiB admission budget; burst = 2000 requests at t=0 (faster of two "
-                        "alternating rounds after a warm-up burst)", **res}
+                        "8 GiB admission budget, after a warm-up burst; each mode's round "
+                        "with the lower p99 of two alternating rounds; burst = 2000 "
+                        "requests at t=0 (faster of two alternating rounds)", **res}
 
 
 # ----------------------------------------------------------------------------

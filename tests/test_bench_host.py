@@ -40,5 +40,7 @@ def test_recorded_traffic_is_bytes_or_none():
     t = bench.recorded_traffic("tma")
     assert t is None or (isinstance(t, int) and t > 5 * 8192 * 8192 // 2)
     assert bench.recorded_traffic("no_such_kernel") is None
-    assert isinstance(bench.kernel_source_hash(), str) and len(bench.kernel_source_hash()) == 16
+    for stem in ("tma", "lanecopy", "tc"):
+        assert len(bench.kernel_source_hash(stem)) == 16
+    assert bench.kernel_source_hash("tma") != bench.kernel_source_hash("tc")
     assert np.isfinite(bench.weak_scaling_value(100, 2, 1, 1.0))
