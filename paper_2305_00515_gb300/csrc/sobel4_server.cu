@@ -4,9 +4,10 @@
 // uploaded on a copy stream, packed into one persistent batched launch per
 // scheduling step (at most kMaxInFlight batches on the GPU at once, so
 // requests that arrive while a batch runs join the next one), and downloaded
-// on a third stream.  Completion is signalled from the download stream by a
-// host function, so the scheduler never polls the GPU.  In plain mode every
-// request is its own single-image launch instead: the comparison point.
+// on a third stream (a batch of one runs as a single-image launch).
+// Completion is signalled from the download stream by a host function, so
+// the scheduler never polls the GPU.  In plain mode every request is its own
+// single-image launch instead: the comparison point.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -262,7 +263,9 @@ void scheduler(sobel4_server_ctx *s) {
       e = cudaEventRecord(b->done, s->up);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(s->comp, b->done, 0);
       if (e == cudaSuccess) {
-        if (s->opt.plain) {
+        // A batch of one runs as a single-image launch: the batched path adds
+        // a descriptor upload and gains nothing for one image.
+        if (s->opt.plain || members.size() == 1) {
           for (const Job &j : members) {
             st = sobel4_run(s->h, j.d_in, j.d_sp, j.d_out, j.d_dp, j.H, j.W,
                             (sobel4_border)s->opt.border, (sobel4_format)fmt, s->comp);
