@@ -28,6 +28,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -181,16 +182,24 @@ KERNEL_SOURCES = {"tma": "sobel4_tma", "lanecopy": "sobel4_rg", "tc": "sobel4_tc
 SHARED_SOURCES = ("sobel4_arith.cuh", "sobel4_device.cuh", "sobel4_ptx.cuh", "sobel4_launch.h")
 
 
+def code_only(text: str) -> str:
+    """C++ source without its comments and blank lines (what the compiler sees)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+
+
 def kernel_source_hash(stem: str = "tma") -> str:
-    """SHA-256 (first 16 hex digits) of the sources the `stem` kernel family
-    is compiled from; a committed ncu summary carries the value it was taken on."""
+    """SHA-256 (first 16 hex digits) of the code, comments stripped, of the
+    sources the `stem` kernel family is compiled from; a committed ncu summary
+    carries the value it was taken on."""
     csrc = os.path.join(ROOT, "paper_2305_00515_gb300", "csrc")
     h = hashlib.sha256()
     for name in sorted(os.listdir(csrc)):
         if name in SHARED_SOURCES or (name.startswith(KERNEL_SOURCES.get(stem, "\0")) and
                                       name.endswith((".cu", ".cuh", ".h"))):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + f.read())
+            with open(os.path.join(csrc, name), encoding="utf-8") as f:
+                h.update(name.encode() + code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

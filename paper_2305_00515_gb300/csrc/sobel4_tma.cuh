@@ -28,8 +28,11 @@
 //    after the row loop; edge items of REPLICATE / REFLECT101 (and of bulk
 //    staging) read the mapped columns from the staged row and gather rows
 //    outside the image from their mapped rows.
-//  * Kernel modes: fast items only (the lean kernel), general items only, or
-//    both in one kernel.
+//  * Kernel modes: fast items only (the lean kernel, widths that are a
+//    multiple of the segment), fast items of a ragged width (one body whose
+//    stores stop at column W), general items only, or both in one kernel.
+//    A batched launch sends all its fast items through one body (see
+//    run_item: several live bodies thrash the instruction cache).
 #pragma once
 
 #include <cuda.h>
