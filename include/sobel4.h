@@ -358,7 +358,11 @@ int32_t sobel4_tune_entries(sobel4_handle h);
  * *kernel = 2 for the tensor-core kernel, 1 for the TMA-staged register-window
  * kernel, 0 for the lane-copy one; its columns per lane and strip height
  * (tuned if sobel4_tune or a loaded cache covers the shape, else the
- * built-in rule).  Errors: INVALID_ARG.
+ * built-in rule).  Handles that do not run those report 3 for DIRECT (also
+ * runtime weights where the tensor-core kernel does not apply) and 4 .. 8
+ * for LADDER_SM, LADDER_SM_P, LADDER_RG, LADDER_RG_V1, LADDER_RG_V2, with 1
+ * column per lane and the RG ladder's strip height (else 0).
+ * Errors: INVALID_ARG.
  */
 sobel4_status sobel4_tune_config(sobel4_handle h, int32_t height, int32_t width,
                                  sobel4_format fmt, int32_t *kernel, int32_t *columns_per_lane,

@@ -1260,6 +1260,25 @@ extern "C" sobel4_status sobel4_tune_config(sobel4_handle h, int32_t height, int
   DeviceGuard g(h->device);
   const size_t sp = ((size_t)width + 15) & ~(size_t)15;
   const size_t dp = ((size_t)width * elem_size(fmt) + 15) & ~(size_t)15;
+  // The same routing as launch_one: runtime weights, DIRECT, the ladder.
+  if (h->custom || h->variant == SOBEL4_VARIANT_DIRECT || is_ladder(h->variant)) {
+    *columns_per_lane = 1;
+    *rows_per_strip = 0;
+    if (h->custom) {
+      *kernel = h->variant != SOBEL4_VARIANT_DIRECT &&
+                        tc_eligible(kAligned, sp, kAligned, dp, height, width,
+                                    SOBEL4_BORDER_VALID, fmt)
+                    ? 2 : 3;
+    } else if (h->variant == SOBEL4_VARIANT_DIRECT) {
+      *kernel = 3;
+    } else {
+      *kernel = 4 + (h->variant - SOBEL4_VARIANT_LADDER_SM);
+      if (h->variant >= SOBEL4_VARIANT_LADDER_RG)
+        *rows_per_strip = h->rows_per_strip > 0 ? h->rows_per_strip
+                                                : ladder_rows(height, width, h->sm_count);
+    }
+    return SOBEL4_OK;
+  }
   rg_config(h, kAligned, sp, kAligned, dp, height, width, SOBEL4_BORDER_VALID, fmt, &use_tma, &nc,
             &R);
   *kernel = use_tma ? 1 : 0;

@@ -128,3 +128,18 @@ def test_ladder_batch_and_host_buffers():
             big = synth.rects_noise(1300, 2100, 9)
             got = s.run_host(big, border="constant0", fmt="s16x4")
             assert_same(got, oracle.sobel4(big, "constant0", "s16x4", threads=NCPU), f"{v} host")
+
+
+def test_tune_config_names_the_ladder_kernels(handles):
+    for k, v in enumerate(LADDER):
+        st, kind, nc, R = pkg.sobel4_tune_config(handles[v], 2048, 2048, pkg.FORMATS["f32"])
+        assert st == 0 and kind == 4 + k and nc == 1
+        assert (R > 0) == v.startswith("ladder_rg")
+    st, kind, _, R = pkg.sobel4_tune_config(handles["ladder_rg_v1_r3"], 100, 100, 0)
+    assert st == 0 and kind == 7 and R == 3
+    st, hd = pkg.sobel4_create(0, pkg.VARIANTS["direct"])
+    assert st == 0
+    try:
+        assert pkg.sobel4_tune_config(hd, 512, 512, 0)[:2] == (0, 3)
+    finally:
+        pkg.sobel4_destroy(hd)
