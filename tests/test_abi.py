@@ -130,3 +130,17 @@ def test_missing_library_fails_loudly(monkeypatch):
     monkeypatch.setattr(pkg, "library_path", lambda: "/nonexistent/libsobel4.so")
     with pytest.raises(ImportError):
         pkg.load()
+
+
+def header_enum(prefix):
+    """{name: value} of the `prefix`* enumerators declared in sobel4.h."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    return {m.group(1).lower(): int(m.group(2))
+            for m in re.finditer(rf"\b{prefix}([A-Z0-9_]+)\s*=\s*(\d+)", text)}
+
+
+def test_binding_enums_match_the_header():
+    assert header_enum("SOBEL4_VARIANT_") == pkg.VARIANTS
+    assert header_enum("SOBEL4_BORDER_") == pkg.BORDERS
+    assert header_enum("SOBEL4_OUT_") == pkg.FORMATS
+    assert {k.replace("_", ""): v for k, v in header_enum("SOBEL4_OP_").items()} == pkg.OPERATORS
