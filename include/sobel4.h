@@ -423,8 +423,9 @@ sobel4_status sobel4_pipeline_destroy(sobel4_pipeline p);
  * `memory_budget` bytes (allocated once, at creation) has room for their
  * input and output, uploads them on a copy stream, packs everything admitted
  * into one persistent batched launch (sobel4_run_batched; at most two batches
- * on the GPU at once, so requests arriving while a batch runs join the next),
- * and downloads results on a third stream.  With plain = 1 each request is
+ * on the GPU at once, so requests arriving while a batch runs join the next;
+ * a batch of one runs as a sobel4_run launch), and downloads results on a
+ * third stream.  With plain = 1 each request is
  * its own sobel4_run launch instead (the comparison point).  Host buffers
  * passed to submit must stay valid until wait returns; pinned host memory
  * keeps the copies asynchronous (pageable memory serialises them).  Every
