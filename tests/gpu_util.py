@@ -8,6 +8,18 @@ import numpy as np
 import paper_2305_00515_gb300 as pkg
 
 GUARD = 0xA5
+
+
+def same_bits(a, b) -> bool:
+    """Element-by-element equality of the stored bits (so -0.0 and +0.0, equal
+    as numbers, differ here): the parity bar is 0 mismatched elements."""
+    a, b = np.asarray(a), np.asarray(b)
+    if a.shape != b.shape or a.dtype != b.dtype:
+        return False
+    if a.dtype.kind == "f":
+        u = {2: np.uint16, 4: np.uint32, 8: np.uint64}[a.dtype.itemsize]
+        return bool(np.array_equal(np.ascontiguousarray(a).view(u), np.ascontiguousarray(b).view(u)))
+    return bool(np.array_equal(a, b))
 ELEM = {"f32": 4, "u8": 1, "s16x4": 2, "u16": 2, "edge8": 1}
 DTYPE = {"f32": np.float32, "u8": np.uint8, "s16x4": np.int16, "u16": np.uint16,
          "edge8": np.uint8}

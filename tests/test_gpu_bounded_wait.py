@@ -8,7 +8,7 @@ import pytest
 import oracle
 import paper_2305_00515_gb300 as pkg
 import synth
-from gpu_util import run_placed
+from gpu_util import run_placed, same_bits
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -28,7 +28,7 @@ def test_withheld_stage_times_out_and_context_survives():
         assert pkg.sobel4_device_status(h) == 0            # the word was cleared
         got, guards = run_placed(torch, h, img, "valid", "f32")
         assert guards
-        assert np.array_equal(got, oracle.sobel4(img, "valid", "f32"))
+        assert same_bits(got, oracle.sobel4(img, "valid", "f32"))
         assert pkg.sobel4_device_status(h) == 0
         assert pkg.sobel4_inject_stage_loss(h, -1) == 1
         assert pkg.sobel4_inject_stage_loss(None, 0) == 1

@@ -15,7 +15,7 @@ import pytest
 import oracle
 import paper_2305_00515_gb300 as pkg
 import synth
-from gpu_util import run_placed
+from gpu_util import run_placed, same_bits
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -51,7 +51,7 @@ def handles():
 
 
 def assert_same(got, want, what):
-    if not np.array_equal(got, want):
+    if not same_bits(got, want):
         bad = np.argwhere(got != want)
         raise AssertionError(f"{what}: {len(bad)} mismatches, first at {bad[:4].tolist()}")
 
