@@ -179,8 +179,13 @@ sobel4_status sobel4_run(sobel4_handle h, const uint8_t *d_src, size_t src_pitch
                          sobel4_format fmt, cudaStream_t stream);
 
 /*
- * Many images of uneven sizes in ONE persistent launch: CTAs pull tiles of
- * all images from a device-side work queue.  `h_images` is HOST memory with
+ * Many images of uneven sizes in persistent launches whose CTAs pull the
+ * tiles of all images from a device-side work queue: one small launch (more
+ * for very large batches) carries the image descriptors in its parameters,
+ * then one batched kernel for the images whose source rows are 16-byte
+ * aligned (staged by tensor copies) and one for the others (staged by bulk
+ * row copies) -- at most two batched kernels per call; with the RG_LANECOPY
+ * variant, one lane-copy batched kernel.  `h_images` is HOST memory with
  * n >= 1 descriptors (each obeying sobel4_run's rules, all with the batch's
  * `border` and `fmt`); it is copied before the call returns.  No two images
  * may write overlapping output, and no output may overlap any input.
@@ -297,23 +302,26 @@ sobel4_status sobel4_check_magnitude(sobel4_handle h, int32_t s_begin, int32_t s
  * point exists for callers that cannot allocate GPU memory -- plugins inside
  * a host framework that owns every device buffer, services held to a fixed
  * memory budget, latency-critical threads that must not pay for cudaMalloc or
- * cudaFree.  It runs the same persistent batched kernel as sobel4_run_batched
- * on the CURRENT device, with no handle, and calls no cudaMalloc, cudaFree or
- * other allocating routine.  Its scratch (image descriptors and the
- * work-queue counter) lives in a static device array of
+ * cudaFree.  It runs on the CURRENT device, with no handle, and calls no
+ * cudaMalloc, cudaFree or other allocating routine.  Its scratch (image
+ * descriptors and the work-queue counter) lives in a static device array of
  * SOBEL4_STATIC_SCRATCH_BYTES bytes inside the library, which every GPU that
  * loads the library holds until the process exits.
  *   h_images, n, border, fmt, stream: as for sobel4_run_batched, with
- *   1 <= n <= SOBEL4_STATIC_MAX_IMAGES; a larger n returns UNSUPPORTED.
- * The first call on a device looks up the array's device address and the SM
- * count; make that first call before any stream capture.  The descriptors are
- * copied from host stack memory as pageable copies, which return only after
- * earlier work on `stream` has finished and the bytes are staged; the kernel
- * itself runs asynchronously.  Every call shares the one array and resets its
- * queue counter: calls that overlap on the GPU race, so serialise them (for
- * example on one stream).  The call uses about 52 KB of the calling thread's
- * stack.  Results equal sobel4_run_batched's bit for bit.
- * Errors: INVALID_ARG (nothing enqueued), UNSUPPORTED, CUDA.
+ *   1 <= n <= SOBEL4_STATIC_MAX_IMAGES (a larger n returns UNSUPPORTED) and
+ *   fmt F32, U8 or S16X4 (U16 and EDGE8 return UNSUPPORTED).
+ * What it enqueues on `stream`: one to three small launches that carry the
+ * descriptors in their kernel parameters (the first also zeroes the queue
+ * counter), then the lane-copy persistent batched kernel (the batched kernel
+ * of the RG_LANECOPY variant) over all n images.  `h_images` is read before
+ * the call returns.  Every call looks up the array's device address on the
+ * current device; the first call on a device can also load the library's
+ * device code there, so make that first call before any stream capture.
+ * Every call shares the one array and overwrites it: calls that overlap on
+ * the GPU race, so serialise them (for example on one stream).  The call uses
+ * about 4 KB of the calling thread's stack.  Results equal
+ * sobel4_run_batched's bit for bit.
+ * Errors: INVALID_ARG and UNSUPPORTED (nothing enqueued), CUDA.
  */
 #define SOBEL4_STATIC_MAX_IMAGES 1024
 #define SOBEL4_STATIC_SCRATCH_BYTES (SOBEL4_STATIC_MAX_IMAGES * 64 + 256)

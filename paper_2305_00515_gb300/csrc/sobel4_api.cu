@@ -98,26 +98,38 @@ __global__ void param_copy_kernel(const __grid_constant__ ParamChunk chunk, uint
   for (int i = t; i < n16; i += stride) dst[i] = chunk.w[i];
 }
 
-// Uploads `bytes` (a multiple of 16) from host `src` to device `dst`.  Zeroes
-// `queue` with the first launch when it is not null.
-cudaError_t param_upload(const void *src, void *dst, size_t bytes, unsigned int *queue,
-                         cudaStream_t st) {
-  static ParamChunk chunk;  // host staging of one launch's parameter block
-  static std::mutex mu;
-  std::lock_guard<std::mutex> lock(mu);
+ParamChunk g_param_chunk;  // host staging of one launch's parameter block
+std::mutex g_param_mu;
+
+// Uploads `bytes` (a multiple of 16) to device `dst`: fill(buf, off, n) writes
+// bytes [off, off + n) of the data into buf, one launch's block at a time.
+// Zeroes `queue` with the first launch when it is not null.
+template <class Fill>
+cudaError_t param_upload_fill(size_t bytes, void *dst, unsigned int *queue, cudaStream_t st,
+                              Fill fill) {
+  std::lock_guard<std::mutex> lock(g_param_mu);
   size_t off = 0;
   do {
     const size_t n = std::min(bytes - off, (size_t)kParamChunk);
-    if (n) memcpy(&chunk, (const uint8_t *)src + off, n);
+    if (n) fill((uint8_t *)&g_param_chunk, off, n);
     (void)cudaGetLastError();
-    param_copy_kernel<<<2, 256, 0, st>>>(chunk, (uint4 *)((uint8_t *)dst + off), (int)(n / 16),
-                                         queue);
+    param_copy_kernel<<<2, 256, 0, st>>>(g_param_chunk, (uint4 *)((uint8_t *)dst + off),
+                                         (int)(n / 16), queue);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     queue = nullptr;
     off += n;
   } while (off < bytes);
   return cudaSuccess;
+}
+
+// Uploads `bytes` (a multiple of 16) from host `src` to device `dst`.  Zeroes
+// `queue` with the first launch when it is not null.
+cudaError_t param_upload(const void *src, void *dst, size_t bytes, unsigned int *queue,
+                         cudaStream_t st) {
+  return param_upload_fill(bytes, dst, queue, st, [src](uint8_t *buf, size_t off, size_t n) {
+    memcpy(buf, (const uint8_t *)src + off, n);
+  });
 }
 
 size_t elem_size(int fmt) { return fmt == kF32 ? 4 : ((fmt == kU8 || fmt == kEdge8) ? 1 : 2); }
@@ -922,58 +934,28 @@ sobel4_status sobel4_check_magnitude(sobel4_handle h, int32_t s_begin, int32_t s
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// Allocation-free batched entry point.
-//
-// Some callers cannot allocate GPU memory: plugins hosted by a framework that
-// owns every device buffer, services with a fixed memory budget, and
-// latency-critical threads that must not pay for cudaMalloc/cudaFree.  For
-// them, sobel4_run_batched_static runs the same persistent batched kernel
-// without a handle, with its scratch (the image descriptors and the work-queue
-// counter) in the file-scope device array below.  The caller still owns the
-// images.  The array is part of the library's device image, so every GPU that
-// loads the library holds it (about 64 KB) until the process exits.
+// Allocation-free batched entry point.  Some callers cannot allocate device
+// memory at all: plugins inside a host framework that owns every device
+// buffer, services held to a fixed memory budget, latency-critical threads
+// that must not pay for cudaMalloc or cudaFree.  For them
+// sobel4_run_batched_static runs the lane-copy persistent batched kernel
+// without a handle, with its scratch (the image descriptors and the
+// work-queue counter) in the file-scope device array below.  The caller still
+// owns the images.  The array is part of the library's device image, so every
+// GPU that loads the library holds it (about 64 KB) until the process exits.
 // ---------------------------------------------------------------------------
 namespace {
 
 constexpr int kStaticMaxImages = SOBEL4_STATIC_MAX_IMAGES;
 constexpr size_t kStaticDescBytes = sizeof(ImageDesc) * kStaticMaxImages;
-constexpr size_t kStaticScratchBytes = kStaticDescBytes + 256;  // descriptors + queue counter
-constexpr int kStaticChunk = 64;  // descriptors staged per host->device copy
-constexpr int kStaticMaxDevices = 64;
+constexpr size_t kStaticScratchBytes = kStaticDescBytes + 256;  // descriptors + queue words
 
 static_assert(sizeof(ImageDesc) == 64, "descriptor size is part of SOBEL4_STATIC_SCRATCH_BYTES");
 static_assert(kStaticScratchBytes == SOBEL4_STATIC_SCRATCH_BYTES, "scratch size mismatch");
+static_assert(kParamChunk % sizeof(ImageDesc) == 0, "descriptors must not straddle uploads");
+static_assert(2 * kStaticMaxImages <= 65536, "range indices are 16-bit");
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
-
-struct StaticDevice {
-  bool ready = false;
-  unsigned char *scratch = nullptr;  // device address of g_static_scratch on this device
-  int sm_count = 0;
-};
-StaticDevice g_static_dev[kStaticMaxDevices];
-std::mutex g_static_mu;
-
-// Once per device, with that device current: the array's device address (the
-// host-side symbol is only a stand-in and must never reach a kernel) and the
-// SM count.
-cudaError_t static_setup(int dev, StaticDevice **out) {
-  std::lock_guard<std::mutex> lock(g_static_mu);
-  StaticDevice &d = g_static_dev[dev];
-  if (!d.ready) {
-    void *ptr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    int sms = 0;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    d.scratch = (unsigned char *)ptr;
-    d.sm_count = sms;
-    d.ready = true;
-  }
-  *out = &d;
-  return cudaSuccess;
-}
 
 }  // namespace
 
@@ -983,67 +965,81 @@ extern "C" sobel4_status sobel4_run_batched_static(const sobel4_image *imgs, int
   if (!imgs || n < 1 || !valid_enum(border, fmt)) return SOBEL4_ERR_INVALID_ARG;
   if (n > kStaticMaxImages || fmt == kU16 || fmt == kEdge8)
     return SOBEL4_ERR_UNSUPPORTED;  // the lane-copy kernel has no such output
+  const int R = kBatchR;
+  int64_t total = 0;  // work items of the whole batch
   for (int32_t i = 0; i < n; ++i) {
     const sobel4_image &m = imgs[i];
     if (!m.src || !valid_dst_ptr(m.dst, fmt) ||
         !valid_shape(m.src_pitch, m.dst_pitch, m.height, m.width, border, fmt))
       return SOBEL4_ERR_INVALID_ARG;
+    const ImageDesc d = make_desc(m.src, m.src_pitch, m.dst, m.dst_pitch, m.height, m.width, R,
+                                  kDefaultNC);
+    total += (int64_t)d.n_seg * d.n_band;
   }
-  // Overlap rule: sorted sweep over fixed-size stack arrays (no heap).
-  struct Iv {
-    uintptr_t b, e;
-    bool out;
-  };
-  Iv iv[2 * kStaticMaxImages];
-  for (int32_t i = 0; i < n; ++i) {
+  // Overlap rule: a sweep over the 2n byte ranges sorted by their start,
+  // through 16-bit indices on the stack (4 KB; no heap).
+  auto range_of = [&](int k, uintptr_t *b, uintptr_t *e) {
+    const sobel4_image &m = imgs[k >> 1];
     uintptr_t r[4];
-    ranges(imgs[i].src, imgs[i].src_pitch, imgs[i].dst, imgs[i].dst_pitch, imgs[i].height,
-           imgs[i].width, fmt, r);
-    iv[2 * i] = {r[0], r[1], false};
-    iv[2 * i + 1] = {r[2], r[3], true};
-  }
-  std::sort(iv, iv + 2 * n, [](const Iv &a, const Iv &b) { return a.b < b.b; });
+    ranges(m.src, m.src_pitch, m.dst, m.dst_pitch, m.height, m.width, fmt, r);
+    *b = r[2 * (k & 1)];
+    *e = r[2 * (k & 1) + 1];
+  };
+  uint16_t idx[2 * kStaticMaxImages];
+  for (int k = 0; k < 2 * n; ++k) idx[k] = (uint16_t)k;
+  std::sort(idx, idx + 2 * n, [&](uint16_t a, uint16_t b) {
+    uintptr_t ba, ea, bb, eb;
+    range_of(a, &ba, &ea);
+    range_of(b, &bb, &eb);
+    return ba < bb;
+  });
   uintptr_t end_out = 0, end_in = 0;
-  for (int32_t i = 0; i < 2 * n; ++i) {
-    const Iv &v = iv[i];
-    if (v.out ? (v.b < end_out || v.b < end_in) : (v.b < end_out)) return SOBEL4_ERR_INVALID_ARG;
-    if (v.out) end_out = std::max(end_out, v.e);
-    else end_in = std::max(end_in, v.e);
+  for (int k = 0; k < 2 * n; ++k) {
+    uintptr_t b, e;
+    range_of(idx[k], &b, &e);
+    const bool out = idx[k] & 1;  // odd index: an output range
+    if (out ? (b < end_out || b < end_in) : (b < end_out)) return SOBEL4_ERR_INVALID_ARG;
+    if (out) end_out = std::max(end_out, e);
+    else end_in = std::max(end_in, e);
   }
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices)
+  if (total >= (1ll << 31)) return SOBEL4_ERR_UNSUPPORTED;  // before anything is enqueued
+  // The array's device address on the current device: the host-side symbol
+  // is only a stand-in and must never reach a kernel.  Looked up on every
+  // call (a host-side query once the device code is loaded), so no address
+  // outlives a context.
+  int dev = 0, sms = 0;
+  void *scratch = nullptr;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaGetSymbolAddress(&scratch, g_static_scratch) != cudaSuccess) {
+    (void)cudaGetLastError();
     return SOBEL4_ERR_CUDA;
-  StaticDevice *sd = nullptr;
-  cudaError_t e = static_setup(dev, &sd);
-  if (e != cudaSuccess) return SOBEL4_ERR_CUDA;
-  ImageDesc *d_desc = (ImageDesc *)sd->scratch;
-  unsigned int *d_queue = (unsigned int *)(sd->scratch + kStaticDescBytes);
-  // Descriptors go through a small stack buffer; a copy from pageable memory
-  // returns once the bytes are staged, so the buffer can be reused at once.
-  const int R = kBatchR;
-  ImageDesc chunk[kStaticChunk];
-  int64_t total = 0;
-  for (int32_t i0 = 0; i0 < n; i0 += kStaticChunk) {
-    const int cnt = std::min<int32_t>(kStaticChunk, n - i0);
-    for (int j = 0; j < cnt; ++j) {
-      const sobel4_image &m = imgs[i0 + j];
-      ImageDesc d = make_desc(m.src, m.src_pitch, m.dst, m.dst_pitch, m.height, m.width, R,
-                              kDefaultNC);
-      d.item0 = total;
-      total += (int64_t)d.n_seg * d.n_band;
-      chunk[j] = d;
-    }
-    e = cudaMemcpyAsync(d_desc + i0, chunk, sizeof(ImageDesc) * cnt, cudaMemcpyHostToDevice,
-                        stream);
-    if (e != cudaSuccess) return SOBEL4_ERR_CUDA;
   }
-  if (total >= (1ll << 31)) return SOBEL4_ERR_UNSUPPORTED;
-  e = cudaMemsetAsync(d_queue, 0, sizeof(unsigned int), stream);  // the queue starts at zero
+  ImageDesc *d_desc = (ImageDesc *)scratch;
+  unsigned int *d_queue = (unsigned int *)((unsigned char *)scratch + kStaticDescBytes);
+  // The descriptors travel in the parameters of small copy launches, built in
+  // place (no host buffer outlives the call); the first launch also zeroes
+  // the queue words.
+  int64_t item0 = 0;
+  cudaError_t e = param_upload_fill(
+      sizeof(ImageDesc) * (size_t)n, d_desc, d_queue, stream,
+      [&](uint8_t *buf, size_t off, size_t bytes) {
+        ImageDesc *out = (ImageDesc *)buf;
+        const size_t i0 = off / sizeof(ImageDesc), cnt = bytes / sizeof(ImageDesc);
+        for (size_t j = 0; j < cnt; ++j) {
+          const sobel4_image &m = imgs[i0 + j];
+          ImageDesc d = make_desc(m.src, m.src_pitch, m.dst, m.dst_pitch, m.height, m.width, R,
+                                  kDefaultNC);
+          d.item0 = item0;
+          item0 += (int64_t)d.n_seg * d.n_band;
+          out[j] = d;
+        }
+      });
   if (e != cudaSuccess) return SOBEL4_ERR_CUDA;
   const int64_t want = (total + kWarpsPerCta - 1) / kWarpsPerCta;
-  const int grid = (int)std::min<int64_t>(want, (int64_t)sd->sm_count * 4);
+  const int grid = (int)std::min<int64_t>(want, (int64_t)sms * 4);
   e = launch_rg_batched(d_desc, n, total, d_queue, border, fmt, R, kDefaultNC, std::max(grid, 1),
-                        sd->sm_count, stream);
+                        sms, stream);
   return e == cudaSuccess ? SOBEL4_OK : SOBEL4_ERR_CUDA;
 }
 
