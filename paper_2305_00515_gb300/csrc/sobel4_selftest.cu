@@ -1,6 +1,7 @@
 // sobel4_selftest.cu — on-device self-check of the magnitude step: the
-// library's F32 magnitudes (the one of the direct kernel, and the two-strip
-// one of the register-window kernels) against CUDA's IEEE
+// library's F32 magnitudes (the one of the direct kernel, the two-strip one
+// of the register-window kernels, and the one that takes S negated) against
+// CUDA's IEEE
 // sqrtf((float)S), and its U8 magnitudes against the exact rule
 // min(255, round(sqrt(S))), for every S in a range (the operator's whole
 // domain is 0 .. 599,270,400).
@@ -23,6 +24,7 @@ __global__ void check_magnitude_kernel(int64_t s0, int64_t s1, unsigned long lon
     const int32_t s = (int32_t)i;
     const float want = sqrtf((float)s);
     if (__float_as_uint(magnitude_f32(s)) != __float_as_uint(want)) ++nb;
+    if (__float_as_uint(magnitude_newton_neg(-s)) != __float_as_uint(want)) ++nb;
     if (!u8_ok(magnitude_u8(s), s)) ++nb;
     // packed pair: s in the low lane, its mirror s1 - 1 - (s - s0) in the high lane
     const int32_t m = (int32_t)(s1 - 1 - (i - s0));

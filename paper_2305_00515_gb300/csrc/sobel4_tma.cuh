@@ -75,8 +75,17 @@ constexpr int kSlotBytes = Geo<kTensor>::kSlot;      // 2560 (strip a, then stri
 constexpr int kUnroll = SOBEL4_TMA_UNROLL;    // row steps per main-loop trip (2 or 4)
 static_assert(kUnroll == 2 || kUnroll == 4, "the stage length must be a multiple of the unroll");
 
+#ifndef SOBEL4_RA_SPLIT
+#define SOBEL4_RA_SPLIT 1  // unaligned destination rows: 1 = each lane's own elements in
+                           // at most three aligned stores, 0 = lane-shifted vector stores
+#endif
+
 #ifndef SOBEL4_TMA_CLD
 #define SOBEL4_TMA_CLD 1  // ring reads on the fast path: 1 = plain loads, 0 = volatile asm loads
+#endif
+
+#ifndef SOBEL4_PDL
+#define SOBEL4_PDL 0  // 1: launched as programmatic dependents (prologue overlaps the previous grid)
 #endif
 
 #ifndef SOBEL4_TMA_MIN_CTAS
@@ -159,6 +168,17 @@ __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
+}
+
+// Programmatic dependent launch: the grid may start while the previous grid
+// on the stream is finishing; it waits here for that grid's completion and
+// memory before its first global access, and lets the next grid start its
+// own prologue on SMs this grid has left.
+__device__ __forceinline__ void grid_dependency_wait() {
+#if SOBEL4_PDL
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
 }
 
 // Acquire a tensor map in global memory for the copy engine (tensor-map
@@ -331,8 +351,86 @@ __device__ __forceinline__ void gather_cols(const TmaImage &im, uint32_t base_a,
 // and no element at column >= W is written: a chunk that crosses column W is
 // written element by element up to it.
 // ---------------------------------------------------------------------------
+// SOBEL4_RA_SPLIT: the misalignment m of a row is the same for every lane, and
+// each lane stores its own four elements in at most three naturally aligned
+// pieces (m = 0: one 16-byte store; m = 2: two 8-byte stores; m odd: 4, 8 and
+// 4 bytes), so no lane touches another lane's elements and no shuffles are
+// needed.  U8 and 16-bit formats split the same way at their scale.
+template <bool PART>
+__device__ __forceinline__ void st4_f32_split(float *p, const float v[4], bool on, int wl) {
+  if (!on) return;
+  if (PART && wl < 4) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k < wl) p[k] = v[k];
+    return;
+  }
+  const uint32_t m = ((uint32_t)(uintptr_t)p >> 2) & 3u;
+  if (m == 0) {
+    *(float4 *)p = make_float4(v[0], v[1], v[2], v[3]);
+  } else if (m == 2) {
+    *(float2 *)p = make_float2(v[0], v[1]);
+    *(float2 *)(p + 2) = make_float2(v[2], v[3]);
+  } else {
+    p[0] = v[0];
+    *(float2 *)(p + 1) = make_float2(v[1], v[2]);
+    p[3] = v[3];
+  }
+}
+
+template <bool PART>
+__device__ __forceinline__ void st4_u8_split(uint8_t *p, uint32_t w, bool on, int wl) {
+  if (!on) return;
+  if (PART && wl < 4) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k < wl) p[k] = (uint8_t)(w >> (8 * k));
+    return;
+  }
+  const uint32_t m = (uint32_t)(uintptr_t)p & 3u;
+  if (m == 0) {
+    *(uint32_t *)p = w;
+  } else if (m == 2) {
+    *(uint16_t *)p = (uint16_t)w;
+    *(uint16_t *)(p + 2) = (uint16_t)(w >> 16);
+  } else {
+    p[0] = (uint8_t)w;
+    *(uint16_t *)(p + 1) = (uint16_t)(w >> 8);
+    p[3] = (uint8_t)(w >> 24);
+  }
+}
+
+// w0 holds elements 0, 1 and w1 elements 2, 3 (little-endian 16-bit pairs).
+template <bool PART>
+__device__ __forceinline__ void st4_s16_split(int16_t *p, uint32_t w0, uint32_t w1, bool on,
+                                              int wl) {
+  if (!on) return;
+  if (PART && wl < 4) {
+    const uint64_t cur = ((uint64_t)w1 << 32) | w0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k < wl) p[k] = (int16_t)(cur >> (16 * k));
+    return;
+  }
+  const uint32_t m = ((uint32_t)(uintptr_t)p >> 1) & 3u;
+  if (m == 0) {
+    *(uint2 *)p = make_uint2(w0, w1);
+  } else if (m == 2) {
+    *(uint32_t *)p = w0;
+    *(uint32_t *)(p + 2) = w1;
+  } else {
+    p[0] = (int16_t)w0;
+    *(uint32_t *)(p + 1) = __funnelshift_r(w0, w1, 16);
+    p[3] = (int16_t)(w1 >> 16);
+  }
+}
+
 template <bool PART>
 __device__ __forceinline__ void st4_f32_realigned(float *p, const float v[4], bool on, int wl) {
+#if SOBEL4_RA_SPLIT
+  st4_f32_split<PART>(p, v, on, wl);
+  return;
+#endif
   const int lane = threadIdx.x & 31;
   const uint32_t m = ((uint32_t)(uintptr_t)p >> 2) & 3u;  // elements past the chunk start
   if (m == 0) {  // an aligned row (m is the same for every lane): plain stores
@@ -374,6 +472,10 @@ __device__ __forceinline__ void st4_f32_realigned(float *p, const float v[4], bo
 
 template <bool PART>
 __device__ __forceinline__ void st4_u8_realigned(uint8_t *p, uint32_t w, bool on, int wl) {
+#if SOBEL4_RA_SPLIT
+  st4_u8_split<PART>(p, w, on, wl);
+  return;
+#endif
   const int lane = threadIdx.x & 31;
   const uint32_t m = (uint32_t)(uintptr_t)p & 3u;
   if (m == 0) {  // an aligned row: plain stores
@@ -414,6 +516,10 @@ __device__ __forceinline__ void st4_u8_realigned(uint8_t *p, uint32_t w, bool on
 template <bool PART>
 __device__ __forceinline__ void st4_s16_realigned(int16_t *p, uint32_t w0, uint32_t w1, bool on,
                                                   int wl) {
+#if SOBEL4_RA_SPLIT
+  st4_s16_split<PART>(p, w0, w1, on, wl);
+  return;
+#endif
   const int lane = threadIdx.x & 31;
   const uint32_t m = ((uint32_t)(uintptr_t)p >> 1) & 3u;
   const uint64_t cur = ((uint64_t)w1 << 32) | w0;
@@ -473,10 +579,10 @@ __device__ __forceinline__ void store_rows(const TmaImage &im, uint8_t *row_a, u
       int16_t *pa = (int16_t *)(row_a + q * plane) + x;
       int16_t *pb = (int16_t *)(row_b + q * plane) + x;
       if (!GEN) {
-        const uint2 la = make_uint2(__byte_perm(v[0], v[1], 0x5410) ^ 0x80008000u,
-                                    __byte_perm(v[2], v[3], 0x5410) ^ 0x80008000u);
-        const uint2 lb = make_uint2(__byte_perm(v[0], v[1], 0x7632),
-                                    __byte_perm(v[2], v[3], 0x7632));
+        const uint2 la = make_uint2(__byte_perm(v[0], v[1], 0x5410) ^ (kBias * 0x10001u),
+                                    __byte_perm(v[2], v[3], 0x5410) ^ (kBias * 0x10001u));
+        const uint2 lb = make_uint2(__byte_perm(hi_ready(v[0]), hi_ready(v[1]), 0x7632),
+                                    __byte_perm(hi_ready(v[2]), hi_ready(v[3]), 0x7632));
         if constexpr (RA) {
           st4_s16_realigned<PART>(pa, la.x, la.y, st_a, wl);
           st4_s16_realigned<PART>(pb, lb.x, lb.y, st_b, wl);
@@ -504,12 +610,29 @@ __device__ __forceinline__ void store_rows(const TmaImage &im, uint8_t *row_a, u
     }
   } else {
   int32_t sa[4], sb[4];
+#if SOBEL4_SQW == 2
+  // F32: strip b's S stays negated (the square root folds the sign in).
+  if constexpr (FMT == kF32) {
 #pragma unroll
-  for (int k = 0; k < 4; ++k) squares(vx[k], vy[k], vd[k], vt[k], sa[k], sb[k]);
+    for (int k = 0; k < 4; ++k) squares_wide(vx[k], vy[k], vd[k], vt[k], sa[k], sb[k]);
+  } else
+#endif
+  {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) squares(vx[k], vy[k], vd[k], vt[k], sa[k], sb[k]);
+  }
   if constexpr (FMT == kF32) {
     float ga[4], gb[4];
+#if SOBEL4_SQW == 2
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      ga[k] = magnitude_newton(sa[k]);
+      gb[k] = magnitude_newton_neg(sb[k]);
+    }
+#else
 #pragma unroll
     for (int k = 0; k < 4; ++k) magnitude_f32x2(sa[k], sb[k], ga[k], gb[k]);
+#endif
     float *pa = (float *)row_a + x, *pb = (float *)row_b + x;
     if (!GEN) {
       if constexpr (RA) {
@@ -1096,6 +1219,7 @@ __global__ void __launch_bounds__(kWarps * 32, min_ctas<MODE>())
   ItemCtx cx;
   init_ring<ST>(cx, rings[threadIdx.x >> 5], lane);
   cx.map = &map;
+  grid_dependency_wait();
   for (;;) {
     unsigned int got = 0;
     if (lane == 0) got = atomicAdd(&pair[0], 1u);
@@ -1131,6 +1255,7 @@ __global__ void __launch_bounds__(kWarps * 32, min_ctas<MODE>())
   const int lane = threadIdx.x & 31;
   ItemCtx cx;
   init_ring<ST>(cx, rings[threadIdx.x >> 5], lane);
+  grid_dependency_wait();
   int cur = -1;
   for (;;) {
     unsigned int got = 0;

@@ -74,13 +74,37 @@ int TmaFmt<FMT>::resident(int mode, int st) {
 #undef SOBEL4_RES
 }
 
+#if SOBEL4_PDL
+// Launch with the programmatic-stream-serialization attribute (the kernel
+// waits for the previous grid itself, in grid_dependency_wait).
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kernel)(KArgs...), int grid, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(tma::kWarps * 32);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  (void)cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+#endif
+
 template <int FMT>
 void TmaFmt<FMT>::single(int mode, int st, const CUtensorMap &map, const tma::TmaImage &im,
                          int border, int R, int items, int grid, unsigned int *pair,
                          unsigned int *err, cudaStream_t s) {
+#if SOBEL4_PDL
+#define SOBEL4_SINGLE(M, S) \
+  launch_pdl(tma::tma_single_kernel<FMT, M, S>, grid, s, map, im, border, R, items, pair, err)
+#else
 #define SOBEL4_SINGLE(M, S)                                                                  \
   tma::tma_single_kernel<FMT, M, S><<<(unsigned)grid, tma::kWarps * 32, 0, s>>>(map, im, border, \
                                                                            R, items, pair, err)
+#endif
   SOBEL4_TMA_SWITCH_SINGLE(mode, st, SOBEL4_SINGLE);
 #undef SOBEL4_SINGLE
 }
