@@ -64,6 +64,9 @@ def parse_args():
     ap.add_argument("--video-frames", type=int, default=2000)
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the Poisson serving run (the full configuration is 60)")
+    ap.add_argument("--profile-batch", type=int, default=0, metavar="N",
+                    help="run the first N images of the 512-image ragged batch (seed 1) through "
+                         "sobel4_run_batched twice and exit (a capture target for ncu)")
     ap.add_argument("--profile-variants", action="store_true",
                     help="run every kernel variant twice on the workload image and exit "
                          "(a capture target for ncu; prints no JSON line)")
@@ -279,8 +282,9 @@ def bench_batched(torch, pkg, synth, reps: int = 5):
     same = all(torch.equal(a, b) for a, b in zip(outs_b, outs_s))
     import oracle
     for k in (0, 100, 511):
-        assert np.array_equal(outs_b[k].cpu().numpy(),
-                              oracle.default().sobel4(imgs[k], "valid", "f32", threads=8))
+        assert np.array_equal(outs_b[k].cpu().numpy().view(np.uint32),
+                              oracle.default().sobel4(imgs[k], "valid", "f32",
+                                                      threads=8).view(np.uint32))
     pkg.sobel4_destroy(h)
     return {"workload": "512 ragged uint8 images, sides U{37..2048} (seed 1), F32, VALID",
             "pixels": px, **res, "speedup": res["separate_launches"]["ms_median"] /
@@ -357,8 +361,9 @@ def bench_video(torch, pkg, synth, frames: int, slots: int = 4):
         dt = time.perf_counter() - t0
         import oracle
         last = (frames - 1) % slots
-        ok = np.array_equal(pipe.outputs[last],
-                            oracle.default().sobel4(ring[last], "valid", "f32", threads=8))
+        ok = np.array_equal(np.ascontiguousarray(pipe.outputs[last]).view(np.uint32),
+                            oracle.default().sobel4(ring[last], "valid", "f32",
+                                                    threads=8).view(np.uint32))
         pipe.close()
     fps = frames / dt
     bytes_per_frame = H * W * 5
@@ -506,6 +511,15 @@ def cpu_baseline(img, seconds: float):
                          "sample": f"{rows_1} rows (128-row bands), {dt_1:.1f} s on 1 thread"}}
 
 
+def workload_config(world: int) -> dict:
+    """The `config` both arms print (the same dict, so the two lines compare)."""
+    return {"workload": WORKLOAD, "height": H, "width": W, "format": "f32", "border": "valid",
+            "per_rank_images": 1, "parallelism": f"replicas{world}",
+            "l2": "inputs larger than L2: the GPU arm rotates over buffer sets of "
+                  "336 MB each (> 2x the 129 MB L2) instead of a flush; the CPU arm "
+                  "streams row bands of the image"}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -538,7 +552,7 @@ def run_reference(args, world, rank):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32+f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample_rows_per_step": rows},
+        "config": workload_config(world),
         "cpu_baseline": {"value": value, "unit": "Gpixel/s", "cores": cores, "kind": "oracle",
                          "sample": f"{rows}x{W} rows of the 8192x8192 image per step"},
         "e2e": {"value": value, "unit": "Gpixel/s", "h2d_bytes_per_step": 0,
@@ -595,7 +609,8 @@ def run_ours(args, world, rank, local):
         got = outs[(args.warmup - 1) % nsets][4000:4016].cpu().numpy() if args.warmup else None
         if got is not None:
             want = oracle.default().sobel4(img[3998:4018], "valid", "f32")[2:18]
-            assert np.array_equal(got, want), "bench output differs from the oracle"
+            assert np.array_equal(got.view(np.uint32), want.view(np.uint32)), \
+                "bench output differs from the oracle"
 
     clocks = ClockSampler(dev)
     clocks.start()
@@ -666,10 +681,9 @@ def run_ours(args, world, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u8->int32->f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "height": H, "width": W, "format": "f32",
-                   "border": "valid", "per_rank_images": 1, "parallelism": f"replicas{world}",
-                   "l2": f"{nsets} rotating buffer sets of {per_set / 1e6:.0f} MB "
-                         f"(> 2x L2) instead of a flush", "autotuned": tuned},
+        "config": workload_config(world),
+        "autotuned": tuned,
+        "l2_buffer_sets": nsets,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": kernel_name, "peak_kind": peak_kind,
@@ -713,10 +727,39 @@ def profile_variants():
         print(f"{v}: ok", flush=True)
 
 
+def profile_batch(n: int):
+    """The first n images of the 512-image ragged batch (sides U{37..2048},
+    seed 1, tight pitches), F32 VALID, through sobel4_run_batched twice with
+    the handle's default configuration."""
+    import torch
+
+    import paper_2305_00515_gb300 as pkg
+    import synth
+    imgs = synth.batch_images(512, 1)[:n]
+    srcs = [torch.from_numpy(i).cuda() for i in imgs]
+    outs = [torch.empty(i.shape, dtype=torch.float32, device="cuda") for i in imgs]
+    descs = (pkg.Image * len(imgs))(*[pkg.Image(s.data_ptr(), s.stride(0), o.data_ptr(),
+                                                 o.stride(0) * 4, *s.shape)
+                                      for s, o in zip(srcs, outs)])
+    st, h = pkg.sobel4_create(0)
+    assert st == 0, pkg.sobel4_status_string(st)
+    stream = torch.cuda.Stream()
+    for _ in range(2):
+        rc = pkg.sobel4_run_batched(h, descs, 0, 0, stream.cuda_stream)
+        assert rc == 0, pkg.sobel4_status_string(rc)
+    stream.synchronize()
+    assert pkg.sobel4_device_status(h) == 0
+    pkg.sobel4_destroy(h)
+    print(f"batch of {n}: ok ({sum(i.size for i in imgs)} pixels)", flush=True)
+
+
 def main():
     args = parse_args()
     if args.profile_variants:
         profile_variants()
+        return
+    if args.profile_batch:
+        profile_batch(args.profile_batch)
         return
     if args.impl == "reference":
         # the CPU oracle runs on rank 0 alone; other ranks exit without work
