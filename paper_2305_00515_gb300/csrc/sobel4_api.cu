@@ -411,7 +411,7 @@ cudaError_t grow_slot(BatchSlot &slot, int cap) {
   slot.h_tma = nullptr;
   slot.d_tma = nullptr;
   slot.cap = 0;
-  const size_t tb = tma_batch_desc_bytes() * cap;
+  const size_t tb = std::max(tma_batch_desc_bytes(false), tma_batch_desc_bytes(true)) * cap;
   cudaError_t e = cudaHostAlloc((void **)&slot.h_desc, sizeof(ImageDesc) * cap, cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaMalloc((void **)&slot.d_desc, sizeof(ImageDesc) * cap);
   if (e == cudaSuccess) e = cudaHostAlloc((void **)&slot.h_tma, tb, cudaHostAllocDefault);
@@ -694,9 +694,10 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
     e = grow_slot(slot, std::max(n, 2 * slot.cap));
     if (e != cudaSuccess) return cuda_fail(h, e);
   }
-  // Every image goes to the TMA-family batched kernel unless the handle asks
-  // for lane copies: 16-byte aligned sources in one launch group (tensor
-  // copies), the others in a second (bulk row copies).
+  // Every image goes to ONE launch of the TMA-family batched kernel unless
+  // the handle asks for lane copies: staged by tensor copies when every
+  // source is 16-byte aligned, else all by bulk row copies (which take any
+  // alignment), so that a mixed batch is still one persistent launch.
   const bool tma_ok = fmt == kU16 || fmt == kEdge8 ||
                       (h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced && !bl);
   // TMA strip height: explicit option, else the tuned one, else about four
@@ -716,25 +717,22 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
           (int)std::min<int64_t>(128, std::max<int64_t>(8, seg_rows / (8 * warps))));
     }
   }
-  int n_lane = 0, n_tma = 0, n_grp[2] = {0, 0};
-  int64_t total = 0, total_grp[2] = {0, 0};
-  bool all_fast[2] = {true, true};
+  int n_lane = 0, n_tma = 0;
+  int64_t total = 0, total_tma = 0;
+  bool all_fast = true, bulk = false;
   if (tma_ok) {
-    for (int g = 0; g < 2; ++g) {  // g = 0: tensor staging, 1: bulk staging
-      for (int32_t i = 0; i < n; ++i) {
-        const sobel4_image &m = imgs[i];
-        if (tma_eligible(m.src, m.src_pitch) != (g == 0)) continue;
-        int64_t items = 0;
-        e = tma_fill_batch_desc(slot.h_tma + tma_batch_desc_bytes() * n_tma, m.src, m.src_pitch,
-                                m.dst, m.dst_pitch, m.height, m.width, Rt, total_grp[g], &items,
-                                h->thr);
-        if (e != cudaSuccess) return cuda_fail(h, e);
-        total_grp[g] += items;
-        ++n_grp[g];
-        ++n_tma;
-        all_fast[g] = all_fast[g] && tma_all_fast(m.width, border, fmt, m.src, m.src_pitch,
-                                                        m.dst, m.dst_pitch);
-      }
+    for (int32_t i = 0; i < n && !bulk; ++i) bulk = !tma_eligible(imgs[i].src, imgs[i].src_pitch);
+    const size_t db = tma_batch_desc_bytes(bulk);
+    for (int32_t i = 0; i < n; ++i) {
+      const sobel4_image &m = imgs[i];
+      int64_t items = 0;
+      e = tma_fill_batch_desc(slot.h_tma + db * n_tma, bulk, m.src, m.src_pitch, m.dst,
+                              m.dst_pitch, m.height, m.width, Rt, total_tma, &items, h->thr);
+      if (e != cudaSuccess) return cuda_fail(h, e);
+      total_tma += items;
+      ++n_tma;
+      // the lean kernel needs every item on the fast path with vector stores
+      all_fast = all_fast && tma_all_fast_staged(m.width, border, fmt, bulk, m.dst, m.dst_pitch);
     }
   } else {
     for (int32_t i = 0; i < n; ++i) {
@@ -745,26 +743,23 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
       slot.h_desc[n_lane++] = d;
     }
   }
-  if (total >= (1ll << 31) || total_grp[0] >= (1ll << 31) || total_grp[1] >= (1ll << 31))
-    return SOBEL4_ERR_UNSUPPORTED;
+  if (total >= (1ll << 31) || total_tma >= (1ll << 31)) return SOBEL4_ERR_UNSUPPORTED;
   // The descriptors reach the device in kernel parameters (param_upload), not
   // by a host-to-device copy, which would queue behind the caller's uploads.
-  // (n >= 1, so at least one of the two uploads runs and zeroes the queue.)
-  const size_t lane_bytes = sizeof(ImageDesc) * n_lane, tma_bytes = tma_batch_desc_bytes() * n_tma;
+  // (n >= 1, so one of the two uploads runs and zeroes the queue.)
+  const size_t lane_bytes = sizeof(ImageDesc) * n_lane;
+  const size_t tma_bytes = tma_batch_desc_bytes(bulk) * n_tma;
   if (n_lane) e = param_upload(slot.h_desc, slot.d_desc, lane_bytes, slot.d_queue, stream);
   if (e == cudaSuccess && n_tma)
     e = param_upload(slot.h_tma, slot.d_tma, tma_bytes, n_lane ? nullptr : slot.d_queue, stream);
   if (e != cudaSuccess) return cuda_fail(h, e);
   h->launches += (lane_bytes + kParamChunk - 1) / kParamChunk +
                  (tma_bytes + kParamChunk - 1) / kParamChunk;
-  for (int g = 0; g < 2; ++g) {
-    if (!n_grp[g]) continue;
-    const int64_t want = (total_grp[g] + kWarpsPerCta - 1) / kWarpsPerCta;
+  if (n_tma) {
+    const int64_t want = (total_tma + kWarpsPerCta - 1) / kWarpsPerCta;
     const int grid = (int)std::min<int64_t>(want, 1 << 30);  // capped at residency below
-    const size_t off = g == 0 ? 0 : tma_batch_desc_bytes() * n_grp[0];
-    e = launch_tma_batched(slot.d_tma + off, n_grp[g], total_grp[g], slot.d_queue + 32 + 8 * g,
-                           border, fmt, Rt, std::max(grid, 1), h->sm_count, h->d_err, stream,
-                           all_fast[g], g == 1);
+    e = launch_tma_batched(slot.d_tma, n_tma, total_tma, slot.d_queue + 32, border, fmt, Rt,
+                           std::max(grid, 1), h->sm_count, h->d_err, stream, all_fast, bulk);
     if (e != cudaSuccess) return cuda_fail(h, e);
     h->launches += 1;
   }

@@ -43,15 +43,18 @@ cudaError_t launch_tma_single(const uint8_t *src, size_t sp, void *dst, size_t d
                               int lose_stage = -1, int32_t thr = 0);
 
 // TMA-family batches: the host fills one descriptor (tma_batch_desc_bytes
-// bytes, 64-byte aligned) per image, copies them to the device and launches
-// min(grid, resident CTAs) CTAs that pull items from *d_queue (zeroed before
-// the launch).  One launch takes images of one staging: all tma_eligible
-// (bulk = false) or all not (bulk = true); R as for launch_tma_single.
-size_t tma_batch_desc_bytes();
-// thr: the EDGE8 threshold on S.
-cudaError_t tma_fill_batch_desc(void *out, const uint8_t *src, size_t sp, void *dst, size_t dp,
-                                int32_t H, int32_t W, int R, int64_t item0, int64_t *items,
-                                int32_t thr = 0);
+// bytes: with a tensor map for tensor staging, without for bulk staging) per
+// image, copies them to the device and launches min(grid, resident CTAs)
+// CTAs that pull items from *d_queue (zeroed before the launch).  A launch
+// stages every image one way: tensor copies (bulk = false; every source
+// tma_eligible) or bulk row copies (bulk = true; any source); R as for
+// launch_tma_single.
+size_t tma_batch_desc_bytes(bool bulk);
+// thr: the EDGE8 threshold on S.  INVALID_VALUE for tensor staging of a
+// source that is not tma_eligible.
+cudaError_t tma_fill_batch_desc(void *out, bool bulk, const uint8_t *src, size_t sp, void *dst,
+                                size_t dp, int32_t H, int32_t W, int R, int64_t item0,
+                                int64_t *items, int32_t thr = 0);
 // d_queue: one zeroed counter; all_fast (every image's items on the fast
 // path with vector stores, see tma_all_fast) selects the lean kernel.
 cudaError_t launch_tma_batched(const void *d_descs, int n_img, int64_t total,
@@ -60,6 +63,8 @@ cudaError_t launch_tma_batched(const void *d_descs, int n_img, int64_t total,
                                bool bulk);
 bool tma_all_fast(int32_t W, int border, int fmt, const uint8_t *src, size_t sp, const void *dst,
                   size_t dp);
+// The same with the staging given (bulk: bulk row copies, else tensor copies).
+bool tma_all_fast_staged(int32_t W, int border, int fmt, bool bulk, const void *dst, size_t dp);
 // A 2-D tensor map (uint8 or float32 elements) over `base` with row pitch
 // `pitch` bytes, H x W elements, a box of box_w x box_h elements, zero fill,
 // and optionally the 128-byte shared-memory swizzle; `map` points to a

@@ -194,31 +194,43 @@ cudaError_t launch_tma_single(const uint8_t *src, size_t sp, void *dst, size_t d
   return cudaGetLastError();
 }
 
-size_t tma_batch_desc_bytes() { return sizeof(tma::TmaBatchDesc); }
+size_t tma_batch_desc_bytes(bool bulk) {
+  return bulk ? sizeof(tma::TmaBulkDesc) : sizeof(tma::TmaBatchDesc);
+}
 
-cudaError_t tma_fill_batch_desc(void *out, const uint8_t *src, size_t sp, void *dst, size_t dp,
-                                int32_t H, int32_t W, int R, int64_t item0, int64_t *items,
-                                int32_t thr) {
-  tma::TmaBatchDesc *d = (tma::TmaBatchDesc *)out;
-  memset(&d->map, 0, sizeof(d->map));
-  if (tensor_ok(src, sp)) {
+cudaError_t tma_fill_batch_desc(void *out, bool bulk, const uint8_t *src, size_t sp, void *dst,
+                                size_t dp, int32_t H, int32_t W, int R, int64_t item0,
+                                int64_t *items, int32_t thr) {
+  tma::TmaImage im = make_image(src, sp, dst, dp, H, W, R);
+  im.thr = thr;
+  if (bulk) {
+    tma::TmaBulkDesc *d = (tma::TmaBulkDesc *)out;
+    memset(d, 0, sizeof(*d));
+    d->im = im;
+    d->item0 = item0;
+  } else {
+    if (!tensor_ok(src, sp)) return cudaErrorInvalidValue;
+    tma::TmaBatchDesc *d = (tma::TmaBatchDesc *)out;
+    memset(d, 0, sizeof(*d));
     const cudaError_t e = encode_map(&d->map, src, sp, H, W);
     if (e != cudaSuccess) return e;
+    d->im = im;
+    d->item0 = item0;
   }
-  d->im = make_image(src, sp, dst, dp, H, W, R);
-  d->im.thr = thr;
-  d->item0 = item0;
-  *items = (int64_t)d->im.n_seg * d->im.n_band;
+  *items = (int64_t)im.n_seg * im.n_band;
   return cudaSuccess;
+}
+
+bool tma_all_fast_staged(int32_t W, int border, int fmt, bool bulk, const void *dst, size_t dp) {
+  int a = 1;
+  while (a < 16 && (((uintptr_t)dst | (uintptr_t)dp) % (uintptr_t)(2 * a)) == 0) a *= 2;
+  const Plan plan = plan_for(W, border, fmt, a, bulk ? tma::kBulk : tma::kTensor);
+  return plan == kPlanFast || plan == kPlanFastPart;
 }
 
 bool tma_all_fast(int32_t W, int border, int fmt, const uint8_t *src, size_t sp,
                         const void *dst, size_t dp) {
-  int a = 1;
-  while (a < 16 && (((uintptr_t)dst | (uintptr_t)dp) % (uintptr_t)(2 * a)) == 0) a *= 2;
-  const int staging = tensor_ok(src, sp) ? tma::kTensor : tma::kBulk;
-  const Plan plan = plan_for(W, border, fmt, a, staging);
-  return plan == kPlanFast || plan == kPlanFastPart;
+  return tma_all_fast_staged(W, border, fmt, !tensor_ok(src, sp), dst, dp);
 }
 
 cudaError_t launch_tma_batched(const void *d_descs, int n_img, int64_t total,
@@ -226,7 +238,7 @@ cudaError_t launch_tma_batched(const void *d_descs, int n_img, int64_t total,
                                int sm_count, unsigned int *err, cudaStream_t st, bool all_fast,
                                bool bulk) {
   if (R < tma::kUnroll || R % tma::kUnroll || total >= (1ll << 31)) return cudaErrorInvalidValue;
-  const tma::TmaBatchDesc *d = (const tma::TmaBatchDesc *)d_descs;
+  const void *d = d_descs;
   const int staging = bulk ? tma::kBulk : tma::kTensor;
   (void)cudaGetLastError();  // report this launch only, not an earlier failed call
   auto go = [&](int mode, unsigned int *queue) {

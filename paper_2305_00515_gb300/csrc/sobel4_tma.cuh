@@ -85,7 +85,7 @@ static_assert(kUnroll == 2 || kUnroll == 4, "the stage length must be a multiple
 #endif
 
 #ifndef SOBEL4_PDL
-#define SOBEL4_PDL 0  // 1: launched as programmatic dependents (prologue overlaps the previous grid)
+#define SOBEL4_PDL 1  // 1: launched as programmatic dependents (prologue overlaps the previous grid)
 #endif
 
 #ifndef SOBEL4_TMA_MIN_CTAS
@@ -134,6 +134,21 @@ struct __align__(64) TmaBatchDesc {
   CUtensorMap map;
   TmaImage im;
   int64_t item0;
+};
+
+// One image of a bulk-staged batch: no tensor map.
+struct __align__(16) TmaBulkDesc {
+  TmaImage im;
+  int64_t item0;
+};
+
+template <int ST>
+struct BatchDescOf {
+  using type = TmaBatchDesc;
+};
+template <>
+struct BatchDescOf<kBulk> {
+  using type = TmaBulkDesc;
 };
 
 // ---------------------------------------------------------------------------
@@ -618,8 +633,9 @@ __device__ __forceinline__ void store_rows(const TmaImage &im, uint8_t *row_a, u
   } else
 #endif
   {
+    constexpr bool kSqb = (RA || GEN) ? (SOBEL4_SQB_RA != 0) : (SOBEL4_SQB != 0);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) squares(vx[k], vy[k], vd[k], vt[k], sa[k], sb[k]);
+    for (int k = 0; k < 4; ++k) squares<kSqb>(vx[k], vy[k], vd[k], vt[k], sa[k], sb[k]);
   }
   if constexpr (FMT == kF32) {
     float ga[4], gb[4];
@@ -1249,8 +1265,8 @@ __global__ void __launch_bounds__(kWarps * 32, min_ctas<MODE>())
 // finds an item's image by binary search over the descriptors' first items.
 template <int FMT, int MODE, int ST>
 __global__ void __launch_bounds__(kWarps * 32, min_ctas<MODE>())
-    tma_batched_kernel(const TmaBatchDesc *__restrict__ descs, int n_img, int total,
-                       unsigned int *queue, int border, int R, unsigned int *err) {
+    tma_batched_kernel(const typename BatchDescOf<ST>::type *__restrict__ descs, int n_img,
+                       int total, unsigned int *queue, int border, int R, unsigned int *err) {
   __shared__ WarpRing<ST> rings[kWarps];
   const int lane = threadIdx.x & 31;
   ItemCtx cx;
@@ -1269,18 +1285,22 @@ __global__ void __launch_bounds__(kWarps * 32, min_ctas<MODE>())
       if (__ldg(&descs[mid].item0) <= item) lo = mid;
       else hi = mid - 1;
     }
-    const TmaBatchDesc *d = descs + lo;
+    const typename BatchDescOf<ST>::type *d = descs + lo;
     const TmaImage im = d->im;
     int seg, band;
     item_coords<ST>(im, border, R, (int)(item - d->item0), &seg, &band);
     const int ya = band * 2 * R, Ri = strip_rows(im, band, R);
     const bool fast = fast_item<ST>(im, border, seg, ya, Ri, FMT);
     if ((fast_mode<MODE>() && !fast) || (MODE == kGeneralOnly && fast)) continue;
-    if (ST == kTensor && lo != cur) {
-      if (lane == 0) tensormap_acquire(&d->map);
-      cur = lo;
+    if constexpr (ST == kTensor) {
+      if (lo != cur) {
+        if (lane == 0) tensormap_acquire(&d->map);
+        cur = lo;
+      }
+      cx.map = &d->map;
+    } else {
+      cx.map = nullptr;  // bulk staging reads rows through im.src
     }
-    cx.map = &d->map;
     cx.lose_stage = -1;
     if (!run_item<FMT, MODE, ST, true>(im, border, seg, ya, Ri, lane, cx, err, fast)) break;
   }

@@ -16,7 +16,8 @@ struct TmaFmt {
   static void single(int mode, int st, const CUtensorMap &map, const tma::TmaImage &im,
                      int border, int R, int items, int grid, unsigned int *pair,
                      unsigned int *err, cudaStream_t s);
-  static void batched(int mode, int st, const tma::TmaBatchDesc *d, int n_img, int total,
+  // d: TmaBatchDesc array (tensor staging) or TmaBulkDesc array (bulk staging).
+  static void batched(int mode, int st, const void *d, int n_img, int total,
                       unsigned int *queue, int border, int R, int grid, unsigned int *err,
                       cudaStream_t s);
 };
@@ -110,12 +111,18 @@ void TmaFmt<FMT>::single(int mode, int st, const CUtensorMap &map, const tma::Tm
 }
 
 template <int FMT>
-void TmaFmt<FMT>::batched(int mode, int st, const tma::TmaBatchDesc *d, int n_img, int total,
+void TmaFmt<FMT>::batched(int mode, int st, const void *d, int n_img, int total,
                           unsigned int *queue, int border, int R, int grid, unsigned int *err,
                           cudaStream_t s) {
-#define SOBEL4_BATCH(M, S)                                                                    \
-  tma::tma_batched_kernel<FMT, M, S><<<(unsigned)grid, tma::kWarps * 32, 0, s>>>(d, n_img, total, \
-                                                                            queue, border, R, err)
+#if SOBEL4_PDL
+#define SOBEL4_BATCH(M, S)                                                                     \
+  launch_pdl(tma::tma_batched_kernel<FMT, M, S>, grid, s,                                      \
+             (const typename tma::BatchDescOf<S>::type *)d, n_img, total, queue, border, R, err)
+#else
+#define SOBEL4_BATCH(M, S)                                                                     \
+  tma::tma_batched_kernel<FMT, M, S><<<(unsigned)grid, tma::kWarps * 32, 0, s>>>(              \
+      (const typename tma::BatchDescOf<S>::type *)d, n_img, total, queue, border, R, err)
+#endif
   SOBEL4_TMA_SWITCH(mode, st, SOBEL4_BATCH);
 #undef SOBEL4_BATCH
 }
