@@ -79,6 +79,9 @@ class Oracle:
                                                      ctypes.POINTER(ctypes.c_int32)]
         lib.sobel4_oracle_operator_masks.restype = ctypes.c_int
         lib.sobel4_oracle_run_masks.restype = ctypes.c_int
+        lib.sobel4_oracle_rgb_to_gray.argtypes = [u8p, ctypes.c_size_t, ctypes.c_int32,
+                                                  ctypes.c_int32, u8p, ctypes.c_size_t]
+        lib.sobel4_oracle_rgb_to_gray.restype = ctypes.c_int
         lib.sobel4_oracle_magnitude_f32.argtypes = [ctypes.c_int32]
         lib.sobel4_oracle_magnitude_f32.restype = ctypes.c_float
         lib.sobel4_oracle_magnitude_u8.argtypes = [ctypes.c_int32]
@@ -169,6 +172,29 @@ class Oracle:
             raise ValueError(f"Eq. (5) weights are not integers for {(a, b, n, m)}")
         return out.reshape(4, 5, 5)
 
+    # -- grayscale input (the host preparation of Section 4.3) ------------------
+    def rgb_to_gray(self, rgb: np.ndarray) -> np.ndarray:
+        """Y = (77 R + 150 G + 29 B + 128) >> 8 per pixel of an (H, W, 3) uint8 RGB
+        image (rows may be padded: row stride >= 3 W), as an (H, W) uint8 image."""
+        if rgb.dtype != np.uint8 or rgb.ndim != 3 or rgb.shape[2] != 3:
+            raise ValueError("image must be an (H, W, 3) uint8 array")
+        if rgb.strides[1:] != (3, 1):
+            rgb = np.ascontiguousarray(rgb)
+        H, W, _ = rgb.shape
+        sp = rgb.strides[0] if H > 1 else 3 * W  # a single row may carry stride 0
+        out = np.empty((H, W), dtype=np.uint8)
+        u8 = ctypes.POINTER(ctypes.c_uint8)
+        rc = self.lib.sobel4_oracle_rgb_to_gray(rgb.ctypes.data_as(u8), sp, H, W,
+                                                out.ctypes.data_as(u8), W)
+        if rc != 0:
+            raise ValueError("oracle rejected arguments")
+        return out
+
+    def sobel4_rgb(self, rgb: np.ndarray, border: str = "valid", fmt: str = "f32",
+                   threads: int = 1) -> np.ndarray:
+        """The operator on the grayscale of an RGB image: convert, then Eq. (3)-(4)."""
+        return self.sobel4(self.rgb_to_gray(rgb), border, fmt, threads)
+
     def magnitude_f32(self, s: int) -> np.float32:
         return np.float32(self.lib.sobel4_oracle_magnitude_f32(int(s)))
 
@@ -207,6 +233,14 @@ def edge_threshold(t) -> int:
     import math
     q = Fraction(t) ** 2
     return math.ceil(q)
+
+
+def rgb_to_gray(rgb: np.ndarray) -> np.ndarray:
+    return default().rgb_to_gray(rgb)
+
+
+def sobel4_rgb(rgb: np.ndarray, border: str = "valid", fmt: str = "f32", threads: int = 1):
+    return default().sobel4_rgb(rgb, border, fmt, threads)
 
 
 def operator_masks(op: str):

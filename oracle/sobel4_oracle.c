@@ -371,6 +371,29 @@ int sobel4_oracle_operator_masks(int32_t op, int32_t *out100, int32_t *radius) {
 }
 
 /* sqrtf((float)s) as the oracle evaluates it, exposed for the rounding pins. */
+/*
+ * Grayscale from interleaved 8-bit RGB: the host-side preparation before the
+ * kernel (Section 4.3), whose rule the paper leaves to another work.  The
+ * reading taken here: the ITU-R BT.601 luma weights 0.299, 0.587, 0.114 in
+ * 8-bit fixed point (77, 150, 29; they sum to 256), rounded half up:
+ *     Y = (77 R + 150 G + 29 B + 128) >> 8.
+ * Pixel x of row y is bytes 3x (R), 3x+1 (G), 3x+2 (B) of that row.
+ */
+int sobel4_oracle_rgb_to_gray(const uint8_t *rgb, size_t rgb_pitch, int32_t H, int32_t W,
+                              uint8_t *gray, size_t gray_pitch) {
+  if (!rgb || !gray || H < 1 || W < 1 || rgb_pitch < 3 * (size_t)W || gray_pitch < (size_t)W)
+    return -1;
+  for (int32_t y = 0; y < H; ++y) {
+    const uint8_t *in = rgb + (size_t)y * rgb_pitch;
+    uint8_t *out = gray + (size_t)y * gray_pitch;
+    for (int32_t x = 0; x < W; ++x) {
+      const uint32_t r = in[3 * x], g = in[3 * x + 1], b = in[3 * x + 2];
+      out[x] = (uint8_t)((77u * r + 150u * g + 29u * b + 128u) >> 8);
+    }
+  }
+  return 0;
+}
+
 float sobel4_oracle_magnitude_f32(int32_t s) { return sqrtf((float)s); }
 
 /* The exact U8 rule, exposed for its pin. */

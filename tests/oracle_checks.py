@@ -346,9 +346,69 @@ def check_valid_frame(o):
                 assert not G[frame].any()
 
 
+# -- grayscale input (the host preparation of Section 4.3; the rule is a reading) --
+def check_rgb_gray_inputs_and_hand_values(o):
+    # R = G = B = v gives v exactly: (256 v + 128) >> 8 = v
+    v = np.arange(256, dtype=np.uint8)
+    rgb = np.repeat(v[None, :, None], 3, axis=2)
+    assert np.array_equal(o.rgb_to_gray(rgb)[0], v)
+    # hand-computed pixels: Y = (77 R + 150 G + 29 B + 128) >> 8
+    cases = {(255, 0, 0): 77,      # 19763 >> 8
+             (0, 255, 0): 149,     # 38378 >> 8
+             (0, 0, 255): 29,      # 7523 >> 8
+             (10, 20, 30): 18,     # (770 + 3000 + 870 + 128) = 4768 >> 8
+             (128, 64, 32): 80,    # (9856 + 9600 + 928 + 128) = 20512 >> 8
+             (1, 1, 0): 1,         # 355 >> 8
+             (0, 0, 1): 0,         # 157 >> 8
+             (255, 255, 255): 255}  # 65408 >> 8
+    px = np.array([list(k) for k in cases], dtype=np.uint8)[None]
+    assert o.rgb_to_gray(px)[0].tolist() == list(cases.values())
+
+
+def check_rgb_within_bt601(o):
+    # every one of the 2^24 colours lies within 1 of the real-valued BT.601
+    # luma 0.299 R + 0.587 G + 0.114 B (weight error <= 0.46, rounding <= 0.5)
+    i = np.arange(1 << 24, dtype=np.uint32)
+    rgb = np.stack([(i >> 16) & 255, (i >> 8) & 255, i & 255], axis=1).astype(np.uint8)
+    y = o.rgb_to_gray(rgb.reshape(4096, 4096, 3)).reshape(-1).astype(np.float64)
+    real = 0.299 * rgb[:, 0] + 0.587 * rgb[:, 1] + 0.114 * rgb[:, 2]
+    assert np.abs(y - real).max() < 1.0
+    # monotone in each channel
+    for c in range(3):
+        lo = rgb.copy()
+        lo[:, c] = np.minimum(lo[:, c], 254)
+        hi = lo.copy()
+        hi[:, c] += 1
+        a = o.rgb_to_gray(lo[:1 << 20].reshape(1024, 1024, 3)).astype(int)
+        b = o.rgb_to_gray(hi[:1 << 20].reshape(1024, 1024, 3)).astype(int)
+        assert (b >= a).all()
+
+
+def check_rgb_channel_steps(o):
+    path = os.path.join(GOLDEN, "rgb_channel_steps_7x7.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")][1:]
+    for ch, h, s in rows:
+        c = "RGB".index(ch)
+        rgb = np.zeros((7, 7, 3), dtype=np.uint8)
+        rgb[:, 3:, c] = 255
+        assert int(o.rgb_to_gray(rgb)[0, 3]) == int(h)
+        G = o.sobel4_rgb(rgb, "valid", "f32")
+        R = o.responses(o.rgb_to_gray(rgb), "valid")
+        S = int((R[:, 3, 3].astype(np.int64) ** 2).sum())
+        assert S == int(s), (ch, S)
+        assert G[3, 3] == np.sqrt(np.float32(int(s)))
+    # a grey RGB image gives the operator of its grey values
+    img = rng_image(5, 23, 31)
+    rgb = np.repeat(img[:, :, None], 3, axis=2)
+    for border in ("valid", "replicate"):
+        assert np.array_equal(o.sobel4_rgb(rgb, border, "f32").view(np.uint32),
+                              o.sobel4(img, border, "f32").view(np.uint32))
+
+
 ALL_CHECKS = [
     check_masks_eq3_equal_eq5, check_mask_structure, check_kd_plus_minus, check_constant_image,
     check_ramp_closed_form, check_impulse, check_golden, check_rotation_flip_transpose,
     check_inversion_linearity, check_against_scipy, check_against_factored,
     check_magnitude_rounding, check_u8_rule, check_pitched_rows_and_threads, check_valid_frame,
+    check_rgb_gray_inputs_and_hand_values, check_rgb_within_bt601, check_rgb_channel_steps,
 ]

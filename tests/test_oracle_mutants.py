@@ -54,6 +54,10 @@ MUTANTS = {
     "u8_truncates": ("if ((uint32_t)s > n * n + n) n += 1;", "if ((uint32_t)s > n * n) n += 0;"),
     "u8_no_saturation": ("return (uint8_t)(n > 255u ? 255u : n);", "return (uint8_t)n;"),
     "s16_plane_stride": ("(size_t)k * (size_t)jb->H * jb->dp", "(size_t)k * (size_t)jb->W * jb->dp"),
+    "rgb_bgr_order": ("const uint32_t r = in[3 * x], g = in[3 * x + 1], b = in[3 * x + 2];",
+                      "const uint32_t r = in[3 * x + 2], g = in[3 * x + 1], b = in[3 * x];"),
+    "rgb_truncates": ("29u * b + 128u) >> 8", "29u * b) >> 8"),
+    "rgb_weight_sum_255": ("(77u * r + 150u * g", "(76u * r + 150u * g"),
     "band_split_gap": ("(int)((int64_t)H * (t + 1) / nthreads)}", "(int)((int64_t)H * (t + 1) / nthreads) - (t + 1 < nthreads)}"),
 }
 
