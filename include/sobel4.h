@@ -179,6 +179,25 @@ sobel4_status sobel4_run(sobel4_handle h, const uint8_t *d_src, size_t src_pitch
                          sobel4_format fmt, cudaStream_t stream);
 
 /*
+ * Gradient output of one COLOUR image, converted to gray on the fly: the
+ * paper prepares grayscale input on the host before the kernel (Section 4.3)
+ * without stating the rule; this library reads it as the ITU-R BT.601 luma
+ * in 8-bit fixed point, Y = (77 R + 150 G + 29 B + 128) >> 8, and applies
+ * Eq. (3) and Eq. (4) to Y.  The conversion happens inside the kernel, as it
+ * reads the rows: 3 bytes in and the output's bytes out per pixel.
+ *   d_src     : device pointer to height rows of width interleaved RGB pixels
+ *               (bytes R, G, B per pixel); any alignment.
+ *   src_pitch : bytes between rows; >= 3 * width.
+ *   d_dst, dst_pitch, height, width, border, fmt, stream: as for sobel4_run.
+ * Runs the TMA-family register-window kernel whatever the handle's variant.
+ * Errors: INVALID_ARG (nothing enqueued), UNSUPPORTED (the handle has runtime
+ * weights or another operator set), CUDA.
+ */
+sobel4_status sobel4_run_rgb(sobel4_handle h, const uint8_t *d_src, size_t src_pitch, void *d_dst,
+                             size_t dst_pitch, int32_t height, int32_t width, sobel4_border border,
+                             sobel4_format fmt, cudaStream_t stream);
+
+/*
  * Many images of uneven sizes in persistent launches whose CTAs pull the
  * tiles of all images from a device-side work queue: one small launch (more
  * for very large batches) carries the image descriptors in its parameters,
@@ -419,6 +438,20 @@ sobel4_status sobel4_pipeline_buffers(sobel4_pipeline p, int32_t slot, uint8_t *
 /* Launch the slot's graph; INVALID_ARG if the slot's previous frame was not waited for. */
 sobel4_status sobel4_pipeline_submit(sobel4_pipeline p, int32_t slot);
 
+/*
+ * One frame from caller host buffers: h_in (the frame, height rows at the
+ * pipeline's input pitch) is copied to the slot's device buffer and the
+ * result to h_out (the pipeline's output pitch and planes); NULL keeps the
+ * slot's own buffer.  With both NULL (or the slot's own buffers) this is
+ * sobel4_pipeline_submit, one graph launch; otherwise the slot's stream gets
+ * the upload, a graph of the kernel alone and the download.  The buffers
+ * should be pinned (cudaHostAlloc / cudaHostRegister) for the copies to run
+ * asynchronously, and must stay valid until wait(slot) returns.  Errors:
+ * INVALID_ARG (as submit), CUDA (sobel4_last_cuda_error has the code).
+ */
+sobel4_status sobel4_pipeline_submit_from(sobel4_pipeline p, int32_t slot, const uint8_t *h_in,
+                                          void *h_out);
+
 /* Block until the slot's last submitted frame is complete (OK if none is pending). */
 sobel4_status sobel4_pipeline_wait(sobel4_pipeline p, int32_t slot);
 
@@ -433,8 +466,10 @@ sobel4_status sobel4_pipeline_destroy(sobel4_pipeline p);
  * into one persistent batched launch (sobel4_run_batched; at most two batches
  * on the GPU at once, so requests arriving while a batch runs join the next;
  * a batch of one runs as a sobel4_run launch), and downloads results on a
- * third stream.  With plain = 1 each request is
- * its own sobel4_run launch instead (the comparison point).  Host buffers
+ * third stream; each request completes when its own download has landed.
+ * Comparison modes: plain = 1 makes each request its own sobel4_run launch
+ * on the same three streams; plain = 2 runs one request at a time in arrival
+ * order on ONE stream (upload, sobel4_run, download).  Host buffers
  * passed to submit must stay valid until wait returns; pinned host memory
  * keeps the copies asynchronous (pageable memory serialises them).  Every
  * result equals sobel4_run's output for that image.
@@ -446,7 +481,7 @@ typedef struct {
   int32_t max_batch;     /* images per launch; 0 = 256 */
   int32_t border;        /* sobel4_border of every request */
   int32_t format;        /* sobel4_format of every request */
-  int32_t plain;         /* 1 = one launch per request, 0 = batched */
+  int32_t plain;         /* 0 = batched; 1 = one launch per request; 2 = one stream, in order */
 } sobel4_server_options;
 
 typedef struct {

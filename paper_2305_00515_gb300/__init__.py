@@ -18,13 +18,13 @@ import threading
 
 __all__ = [
     "BORDERS", "FORMATS", "VARIANTS", "Sobel4", "Sobel4Error", "Image", "Options",
-    "library_path", "load", "sobel4_create", "sobel4_destroy", "sobel4_run",
+    "library_path", "load", "sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_rgb",
     "sobel4_run_batched", "sobel4_run_host", "sobel4_status_string", "sobel4_last_cuda_error",
     "sobel4_device_status", "sobel4_inject_stage_loss", "sobel4_set_weights", "sobel4_set_operator", "sobel4_set_threshold", "OPERATORS", "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
     "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched", "sobel4_tune_entries",
     "sobel4_tune_config", "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create",
-    "sobel4_pipeline_buffers", "sobel4_pipeline_submit", "sobel4_pipeline_wait",
-    "sobel4_pipeline_destroy", "Pipeline",
+    "sobel4_pipeline_buffers", "sobel4_pipeline_submit", "sobel4_pipeline_submit_from",
+    "sobel4_pipeline_wait", "sobel4_pipeline_destroy", "Pipeline",
     "sobel4_server_create", "sobel4_server_submit", "sobel4_server_wait", "sobel4_server_stats",
     "sobel4_server_destroy", "ServerOptions", "ServerStats", "EXPORTED_SYMBOLS",
 ]
@@ -40,14 +40,15 @@ STATUS = {0: "SOBEL4_OK", 1: "SOBEL4_ERR_INVALID_ARG", 2: "SOBEL4_ERR_UNSUPPORTE
           3: "SOBEL4_ERR_OOM", 4: "SOBEL4_ERR_CUDA", 5: "SOBEL4_ERR_TIMEOUT"}
 
 EXPORTED_SYMBOLS = (
-    "sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_batched", "sobel4_run_host",
+    "sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_rgb", "sobel4_run_batched",
+    "sobel4_run_host",
     "sobel4_status_string", "sobel4_last_cuda_error", "sobel4_device_status",
     "sobel4_inject_stage_loss", "sobel4_set_weights", "sobel4_set_operator",
     "sobel4_set_threshold", "sobel4_launch_count", "sobel4_set_variant", "sobel4_version", "sobel4_check_magnitude",
     "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched", "sobel4_tune_entries",
     "sobel4_tune_config", "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create",
-    "sobel4_pipeline_buffers", "sobel4_pipeline_submit", "sobel4_pipeline_wait",
-    "sobel4_pipeline_destroy", "sobel4_server_create", "sobel4_server_submit", "sobel4_server_wait", "sobel4_server_stats",
+    "sobel4_pipeline_buffers", "sobel4_pipeline_submit", "sobel4_pipeline_submit_from",
+    "sobel4_pipeline_wait", "sobel4_pipeline_destroy", "sobel4_server_create", "sobel4_server_submit", "sobel4_server_wait", "sobel4_server_stats",
     "sobel4_server_destroy",
 )
 
@@ -107,6 +108,7 @@ def load() -> ctypes.CDLL:
         lib.sobel4_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(Options)]
         lib.sobel4_destroy.argtypes = [vp]
         lib.sobel4_run.argtypes = [vp, vp, sz, vp, sz, i32, i32, i32, i32, vp]
+        lib.sobel4_run_rgb.argtypes = [vp, vp, sz, vp, sz, i32, i32, i32, i32, vp]
         lib.sobel4_run_batched.argtypes = [vp, ctypes.POINTER(Image), i32, i32, i32, vp]
         lib.sobel4_run_host.argtypes = [vp, vp, sz, vp, sz, i32, i32, i32, i32]
         lib.sobel4_status_string.argtypes = [ctypes.c_int]
@@ -138,6 +140,7 @@ def load() -> ctypes.CDLL:
         lib.sobel4_pipeline_buffers.argtypes = [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                                 ctypes.POINTER(sz), ctypes.POINTER(sz)]
         lib.sobel4_pipeline_submit.argtypes = [vp, i32]
+        lib.sobel4_pipeline_submit_from.argtypes = [vp, i32, vp, vp]
         lib.sobel4_pipeline_wait.argtypes = [vp, i32]
         lib.sobel4_pipeline_destroy.argtypes = [vp]
         lib.sobel4_server_create.argtypes = [vp, ctypes.POINTER(ServerOptions), ctypes.POINTER(vp)]
@@ -147,13 +150,15 @@ def load() -> ctypes.CDLL:
                                            ctypes.POINTER(ctypes.c_double)]
         lib.sobel4_server_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
         lib.sobel4_server_destroy.argtypes = [vp]
-        for name in ("sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_batched",
+        for name in ("sobel4_create", "sobel4_destroy", "sobel4_run", "sobel4_run_rgb",
+                     "sobel4_run_batched",
                      "sobel4_run_host", "sobel4_set_variant", "sobel4_check_magnitude",
                      "sobel4_device_status", "sobel4_inject_stage_loss", "sobel4_tune_config",
                      "sobel4_set_weights", "sobel4_set_operator", "sobel4_set_threshold",
                      "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched",
                      "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create",
-                     "sobel4_pipeline_buffers", "sobel4_pipeline_submit", "sobel4_pipeline_wait",
+                     "sobel4_pipeline_buffers", "sobel4_pipeline_submit",
+                     "sobel4_pipeline_submit_from", "sobel4_pipeline_wait",
                      "sobel4_pipeline_destroy", "sobel4_server_create", "sobel4_server_submit",
                      "sobel4_server_wait", "sobel4_server_stats", "sobel4_server_destroy"):
             getattr(lib, name).restype = ctypes.c_int
@@ -178,6 +183,13 @@ def sobel4_run(h, d_src: int, src_pitch: int, d_dst: int, dst_pitch: int, height
                width: int, border: int, fmt: int, stream: int) -> int:
     return load().sobel4_run(h, d_src, src_pitch, d_dst, dst_pitch, height, width, border, fmt,
                              stream)
+
+
+def sobel4_run_rgb(h, d_src: int, src_pitch: int, d_dst: int, dst_pitch: int, height: int,
+                   width: int, border: int, fmt: int, stream: int) -> int:
+    """The operator on the gray of an interleaved RGB image (device pointers)."""
+    return load().sobel4_run_rgb(h, d_src, src_pitch, d_dst, dst_pitch, height, width, border,
+                                 fmt, stream)
 
 
 def sobel4_run_batched(h, images, border: int, fmt: int, stream: int) -> int:
@@ -297,6 +309,11 @@ def sobel4_pipeline_submit(p, slot: int) -> int:
     return load().sobel4_pipeline_submit(p, slot)
 
 
+def sobel4_pipeline_submit_from(p, slot: int, h_in: int, h_out: int) -> int:
+    """Launch the slot on caller host buffers (0 keeps the slot's own buffer)."""
+    return load().sobel4_pipeline_submit_from(p, slot, h_in or None, h_out or None)
+
+
 def sobel4_pipeline_wait(p, slot: int) -> int:
     return load().sobel4_pipeline_wait(p, slot)
 
@@ -331,6 +348,12 @@ class Pipeline:
 
     def submit(self, slot: int):
         _check(sobel4_pipeline_submit(self.p, slot), "sobel4_pipeline_submit")
+
+    def submit_from(self, slot: int, h_in: int, h_out: int = 0):
+        """Launch the slot on a caller frame (pinned host address of height rows at
+        the input pitch); the result goes to h_out, or to the slot's output if 0."""
+        _check(sobel4_pipeline_submit_from(self.p, slot, h_in, h_out),
+               "sobel4_pipeline_submit_from")
 
     def wait(self, slot: int):
         _check(sobel4_pipeline_wait(self.p, slot), "sobel4_pipeline_wait")
@@ -473,6 +496,20 @@ class Sobel4:
         H, W = src.shape
         _check(sobel4_run(self.handle, src.data_ptr(), sp, out.data_ptr(), dp, H, W,
                           BORDERS[border], FORMATS[fmt], self._stream(stream)), "sobel4_run")
+        return out
+
+    def run_rgb(self, src, out=None, border: str = "valid", fmt: str = "f32", stream=None):
+        """Gradient output of the gray of a uint8 CUDA tensor [H, W, 3] (interleaved
+        RGB, rows may be strided); asynchronous on `stream`."""
+        H, W, C = src.shape
+        if C != 3 or src.stride(2) != 1 or src.stride(1) != 3:
+            raise ValueError("src must be a uint8 [H, W, 3] tensor with interleaved pixels")
+        if out is None:
+            out = self.empty_output(src[:, :, 0], fmt)
+        dp = out.stride(-2) * ELEM_SIZE[fmt]
+        _check(sobel4_run_rgb(self.handle, src.data_ptr(), src.stride(0), out.data_ptr(), dp, H,
+                              W, BORDERS[border], FORMATS[fmt], self._stream(stream)),
+               "sobel4_run_rgb")
         return out
 
     def run_batched(self, srcs, outs=None, border: str = "valid", fmt: str = "f32",

@@ -201,6 +201,9 @@ struct sobel4_ctx {
 namespace sobel4 {
 HandleInfo handle_info(sobel4_handle h) { return HandleInfo{h->device}; }
 void note_launches(sobel4_handle h, int64_t delta) { h->launches += (uint64_t)delta; }
+void note_cuda_error(sobel4_handle h, cudaError_t e) {
+  if (h) h->last_err = (int32_t)e;
+}
 }  // namespace sobel4
 
 namespace {
@@ -638,6 +641,30 @@ sobel4_status run_with_pair(sobel4_handle h, const uint8_t *d_src, size_t src_pi
 }  // namespace sobel4
 
 extern "C" {
+
+sobel4_status sobel4_run_rgb(sobel4_handle h, const uint8_t *d_src, size_t src_pitch, void *d_dst,
+                             size_t dst_pitch, int32_t height, int32_t width,
+                             sobel4_border border, sobel4_format fmt, cudaStream_t stream) {
+  if (!h || !d_src || !valid_dst_ptr(d_dst, fmt) || width < 1 || width > kMaxSide ||
+      src_pitch < 3 * (size_t)width)
+    return SOBEL4_ERR_INVALID_ARG;
+  if (!valid_shape(src_pitch, dst_pitch, height, width, border, fmt))
+    return SOBEL4_ERR_INVALID_ARG;
+  uintptr_t r[4];
+  ranges(d_src, src_pitch, d_dst, dst_pitch, height, width, fmt, r);
+  r[1] = (uintptr_t)d_src + (uintptr_t)(height - 1) * src_pitch + 3 * (uintptr_t)width;
+  if (overlaps(r[0], r[1], r[2], r[3])) return SOBEL4_ERR_INVALID_ARG;
+  if (h->custom) return SOBEL4_ERR_UNSUPPORTED;  // runtime masks run on other kernels
+  DeviceGuard g(h->device);
+  const int R = tma_pick_R(fmt, h->sm_count, height, width,
+                           tma_all_fast_staged(width, border, fmt, true, d_dst, dst_pitch));
+  const cudaError_t e = launch_tma_single_rgb(d_src, src_pitch, d_dst, dst_pitch, height, width,
+                                              border, fmt, R, h->sm_count, next_pair(h),
+                                              h->d_err, stream, h->thr);
+  if (e != cudaSuccess) return cuda_fail(h, e);
+  h->launches += 1;
+  return SOBEL4_OK;
+}
 
 sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int32_t n,
                                  sobel4_border border, sobel4_format fmt, cudaStream_t stream) {

@@ -42,6 +42,14 @@ cudaError_t launch_tma_single(const uint8_t *src, size_t sp, void *dst, size_t d
                               unsigned int *pair, unsigned int *err, cudaStream_t st,
                               int lose_stage = -1, int32_t thr = 0);
 
+// The same for an interleaved RGB source (3 bytes per pixel, row pitch sp >=
+// 3W, any alignment): the kernel stages RGB rows and turns them into gray
+// (Y = (77R + 150G + 29B + 128) >> 8) as it reads them.
+cudaError_t launch_tma_single_rgb(const uint8_t *src, size_t sp, void *dst, size_t dp, int32_t H,
+                                  int32_t W, int border, int fmt, int R, int sm_count,
+                                  unsigned int *pair, unsigned int *err, cudaStream_t st,
+                                  int32_t thr = 0);
+
 // TMA-family batches: the host fills one descriptor (tma_batch_desc_bytes
 // bytes: with a tensor map for tensor staging, without for bulk staging) per
 // image, copies them to the device and launches min(grid, resident CTAs)
@@ -119,6 +127,8 @@ struct HandleInfo {
 };
 __attribute__((visibility("hidden"))) HandleInfo handle_info(sobel4_handle h);
 __attribute__((visibility("hidden"))) void note_launches(sobel4_handle h, int64_t delta);
+// Records a failed CUDA call as the handle's last error (sobel4_last_cuda_error).
+__attribute__((visibility("hidden"))) void note_cuda_error(sobel4_handle h, cudaError_t e);
 // sobel4_run with caller-owned RG counters (four zeroed words in device
 // memory: a launch may use two counter pairs; nullptr takes the handle's next
 // block).  A captured graph must own its

@@ -194,6 +194,27 @@ cudaError_t launch_tma_single(const uint8_t *src, size_t sp, void *dst, size_t d
   return cudaGetLastError();
 }
 
+cudaError_t launch_tma_single_rgb(const uint8_t *src, size_t sp, void *dst, size_t dp, int32_t H,
+                                  int32_t W, int border, int fmt, int R, int sm_count,
+                                  unsigned int *pair, unsigned int *err, cudaStream_t st,
+                                  int32_t thr) {
+  if (R < tma::kUnroll || R % tma::kUnroll) return cudaErrorInvalidValue;
+  CUtensorMap map;  // not used by the RGB staging
+  memset(&map, 0, sizeof(map));
+  tma::TmaImage im = make_image(src, sp, dst, dp, H, W, R);
+  im.thr = thr;
+  const int64_t items = (int64_t)im.n_seg * im.n_band;
+  if (items >= (1ll << 31)) return cudaErrorInvalidValue;
+  const Plan plan = plan_for(W, border, fmt, im.dst_align, tma::kBulk);
+  const int mode = plan == kPlanFast       ? tma::kFastOnly
+                   : plan == kPlanFastPart ? tma::kFastPart
+                   : plan == kPlanGeneral  ? tma::kGeneralOnly
+                                           : tma::kAll;
+  (void)cudaGetLastError();  // report this launch only, not an earlier failed call
+  single(fmt, mode, tma::kRgbBulk, map, im, border, R, (int)items, sm_count, pair, err, st);
+  return cudaGetLastError();
+}
+
 size_t tma_batch_desc_bytes(bool bulk) {
   return bulk ? sizeof(tma::TmaBulkDesc) : sizeof(tma::TmaBatchDesc);
 }

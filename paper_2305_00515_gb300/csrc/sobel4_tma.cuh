@@ -52,20 +52,30 @@ constexpr int kStageRows = 8;                 // rows per stage and strip
 constexpr int kSlots = 3;                     // ring slots per warp
 constexpr int kWarps = 4;                     // warps per CTA
 
-// Two stagings share the kernel.  kTensor: 2-D tensor copies (TMA) of a box
+// Three stagings share the kernel.  kTensor: 2-D tensor copies (TMA) of a box
 // of 160 x 8 bytes per strip; needs 16-byte aligned rows.  kBulk: 1-D bulk
 // copies (cp.async.bulk), one per row, of the 16-byte granules that hold the
 // row's bytes for columns x0-2 .. x0+129 (at most 176 bytes), for rows of any
 // alignment; each row slot keeps a 16-byte pad in front of the data and the
 // slot keeps, per row, the byte offset of column x0-2 from the copied data.
-enum Staging : int { kTensor = 0, kBulk = 1 };
+// kRgbBulk: an interleaved RGB source (3 bytes per pixel, any alignment),
+// staged like kBulk -- one 1-D bulk copy per row of the 16-byte granules that
+// hold the bytes of columns x0-2 .. x0+129 (at most 432 bytes) behind a
+// 32-byte pad -- in stages of 4 rows; the ring reads turn each pixel into gray
+// (rgb_cols below).
+enum Staging : int { kTensor = 0, kBulk = 1, kRgbBulk = 2 };
 template <int ST>
 struct Geo {
-  static constexpr int kRowPitch = ST == kBulk ? 192 : kBoxW;  // bytes per staged row
-  static constexpr int kRowData = ST == kBulk ? 16 : 0;        // copied bytes start here
+  static constexpr bool kRows = ST != kTensor;  // per-row copies with per-row offsets
+  static constexpr int kBpp = ST == kRgbBulk ? 3 : 1;           // source bytes per pixel
+  static constexpr int kStageRows = ST == kRgbBulk ? 4 : 8;     // rows per stage and strip
+  static constexpr int kSlots = 3;                              // ring slots per warp
+  static constexpr int kRowPitch =                              // bytes per staged row
+      ST == kBulk ? 192 : (ST == kRgbBulk ? 480 : kBoxW);
+  static constexpr int kRowData = ST == kBulk ? 16 : (ST == kRgbBulk ? 32 : 0);
   static constexpr int kStrip = kStageRows * kRowPitch;
-  static constexpr int kHdr = 2 * kStrip;                      // per-row offsets (kBulk)
-  static constexpr int kSlot = 2 * kStrip + (ST == kBulk ? 64 : 0);
+  static constexpr int kHdr = 2 * kStrip;                      // per-row offsets
+  static constexpr int kSlot = 2 * kStrip + (kRows ? 64 : 0);
 };
 constexpr int kStripBytes = Geo<kTensor>::kStrip;    // 1280
 constexpr int kSlotBytes = Geo<kTensor>::kSlot;      // 2560 (strip a, then strip b)
@@ -110,8 +120,8 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
 template <int ST>
 struct __align__(128) WarpRing {
-  uint8_t slot[kSlots][Geo<ST>::kSlot];
-  uint64_t bar[kSlots];
+  uint8_t slot[Geo<ST>::kSlots][Geo<ST>::kSlot];
+  uint64_t bar[Geo<ST>::kSlots];
 };
 
 // One image as the TMA kernel sees it (the source is staged through the
@@ -314,6 +324,54 @@ __device__ __forceinline__ void read_cols_any(uint32_t a, uint32_t b, uint32_t c
   c[7] = __byte_perm(t3, 0u, 0x4342);
 }
 
+// Gray of interleaved RGB pixels (the host preparation of Section 4.3; the
+// rule read for it): Y = (77 R + 150 G + 29 B + 128) >> 8, as 4-way byte dot
+// products whose weight bytes sit where the pixel's bytes sit in a word.  The
+// result is Y * 256 + (fraction), below 2^16, so Y is its byte 1.
+__device__ __forceinline__ uint32_t dp4(uint32_t w, uint32_t k, uint32_t c) {
+  return __dp4a(w, k, c);
+}
+constexpr uint32_t kRgbW0 = 0x001D964Du;  // R, G, B weights at bytes 0, 1, 2
+
+// Packed gray columns c[0..7] (columns x-2 .. x+5 of both strips) from RGB
+// rows at any byte offset: pixel x-2 of strip a at shared address `a`, of
+// strip b at `b`.  The 24 bytes of each strip are funnel-shifted out of seven
+// aligned words (the shift is the same for every lane of a row) into six
+// words in which pixel j starts at byte 3j, then each pixel is one dot product
+// (within a word) or two (across two words).
+__device__ __forceinline__ void rgb_words(uint32_t a, uint32_t n[6]) {
+  const uint32_t q = a & ~3u, sh = (a & 3u) * 8u;
+  uint32_t w[7];
+#pragma unroll
+  for (int i = 0; i < 7; ++i) w[i] = lds_u32(q + 4 * i);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) n[i] = __funnelshift_r(w[i], w[i + 1], sh);
+}
+__device__ __forceinline__ void rgb_gray6(const uint32_t n[6], uint32_t y[8]) {
+  y[0] = dp4(n[0], kRgbW0, 128u);                                   // bytes 0-2
+  y[1] = dp4(n[1], 0x00001D96u, dp4(n[0], 0x4D000000u, 128u));      // bytes 3 | 4-5
+  y[2] = dp4(n[2], 0x0000001Du, dp4(n[1], 0x964D0000u, 128u));      // bytes 6-7 | 8
+  y[3] = dp4(n[2], kRgbW0 << 8, 128u);                              // bytes 9-11
+  y[4] = dp4(n[3], kRgbW0, 128u);                                   // bytes 12-14
+  y[5] = dp4(n[4], 0x00001D96u, dp4(n[3], 0x4D000000u, 128u));      // bytes 15 | 16-17
+  y[6] = dp4(n[5], 0x0000001Du, dp4(n[4], 0x964D0000u, 128u));      // bytes 18-19 | 20
+  y[7] = dp4(n[5], kRgbW0 << 8, 128u);                              // bytes 21-23
+}
+__device__ __forceinline__ void read_cols_rgb(uint32_t a, uint32_t b, uint32_t c[8]) {
+  uint32_t na[6], nb[6], ya[8], yb[8];
+  rgb_words(a, na);
+  rgb_words(b, nb);
+  rgb_gray6(na, ya);
+  rgb_gray6(nb, yb);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) c[j] = __byte_perm(ya[j], yb[j], 0x6521);  // (Y_a, Y_b)
+}
+
+// The gray of one RGB pixel from three bytes (edge items).
+__device__ __forceinline__ uint32_t rgb_gray1(uint32_t r, uint32_t g, uint32_t b) {
+  return (77u * r + 150u * g + 29u * b + 128u) >> 8;
+}
+
 // Edge lanes under REPLICATE / REFLECT101: column j comes from staged byte
 // offset off[j] (relative to column x0-2) of each strip's row.
 __device__ __forceinline__ void read_cols_mapped(uint32_t base_a, uint32_t base_b,
@@ -328,6 +386,8 @@ __device__ __forceinline__ void read_cols_mapped(uint32_t base_a, uint32_t base_
 // strip's row is inside the image, else the mapped row's byte in global
 // memory (REPLICATE / REFLECT101) or 0 (CONSTANT0, VALID); zmask marks
 // columns outside the image that read 0 (CONSTANT0).
+// BPP = 3: RGB pixels, turned into gray.
+template <int BPP = 1>
 __device__ __forceinline__ void gather_cols(const TmaImage &im, uint32_t base_a, uint32_t base_b,
                                             const int32_t off[8], uint32_t zmask, int x, int ra,
                                             int rb, bool out_a, bool out_b, int border,
@@ -339,8 +399,18 @@ __device__ __forceinline__ void gather_cols(const TmaImage &im, uint32_t base_a,
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const int col = map_index(x - 2 + j, im.W, border, &z);
-    uint32_t va = out_a ? (mapped ? (uint32_t)__ldg(ga + col) : 0u) : lds_u8(base_a + off[j]);
-    uint32_t vb = out_b ? (mapped ? (uint32_t)__ldg(gb + col) : 0u) : lds_u8(base_b + off[j]);
+    uint32_t va, vb;
+    if constexpr (BPP == 3) {
+      const uint8_t *pa = ga + 3 * col, *pb = gb + 3 * col;
+      const uint32_t sa = base_a + 3 * off[j], sb = base_b + 3 * off[j];
+      va = out_a ? (mapped ? rgb_gray1(__ldg(pa), __ldg(pa + 1), __ldg(pa + 2)) : 0u)
+                 : rgb_gray1(lds_u8(sa), lds_u8(sa + 1), lds_u8(sa + 2));
+      vb = out_b ? (mapped ? rgb_gray1(__ldg(pb), __ldg(pb + 1), __ldg(pb + 2)) : 0u)
+                 : rgb_gray1(lds_u8(sb), lds_u8(sb + 1), lds_u8(sb + 2));
+    } else {
+      va = out_a ? (mapped ? (uint32_t)__ldg(ga + col) : 0u) : lds_u8(base_a + off[j]);
+      vb = out_b ? (mapped ? (uint32_t)__ldg(gb + col) : 0u) : lds_u8(base_b + off[j]);
+    }
     if ((zmask >> j) & 1u) va = vb = 0u;
     c[j] = va | (vb << 16);
   }
@@ -829,14 +899,14 @@ struct ItemCtx {
 
 template <int ST>
 __device__ __forceinline__ uint32_t bar_addr(const ItemCtx &cx, uint32_t g) {
-  return cx.ring + (uint32_t)(kSlots * Geo<ST>::kSlot + 8 * (g % kSlots));
+  return cx.ring + (uint32_t)(Geo<ST>::kSlots * Geo<ST>::kSlot + 8 * (g % Geo<ST>::kSlots));
 }
 
 // Waits until stage counter g has landed (all lanes agree on the outcome).
 template <int ST>
 __device__ __forceinline__ bool wait_stage(const ItemCtx &cx, uint32_t g, unsigned int *err) {
   const uint32_t bar = bar_addr<ST>(cx, g);
-  const uint32_t parity = (g / kSlots) & 1u;
+  const uint32_t parity = (g / Geo<ST>::kSlots) & 1u;
   if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
   const uint64_t t0 = global_ns();
   for (;;) {
@@ -855,13 +925,13 @@ __device__ __forceinline__ void drain_stages(const ItemCtx &cx, uint32_t g_from,
   for (uint32_t g = g_from; g < g_to; ++g) {
     const uint32_t bar = bar_addr<ST>(cx, g);
     const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(bar, (g / kSlots) & 1u) && global_ns() - t0 < kWaitLimitNs) {
+    while (!mbar_try_wait(bar, (g / Geo<ST>::kSlots) & 1u) && global_ns() - t0 < kWaitLimitNs) {
     }
   }
 }
 
 // Copies stage j of an item (rows 8j .. 8j+7 of both strips) into ring slot
-// g % kSlots.  All lanes call it after a warp barrier.  Tensor staging: lane
+// g % Geo<ST>::kSlots.  All lanes call it after a warp barrier.  Tensor staging: lane
 // 0 issues two box copies.  Bulk staging: lane 8s+k copies row k of strip s
 // (the granules that hold columns x0-2 .. x0+129 of an image row; rows outside
 // the image are not copied) and records the offset of column x0-2 from the
@@ -871,33 +941,34 @@ template <int ST>
 __device__ __forceinline__ void issue_stage(const TmaImage &im, const ItemCtx &cx, int x0, int ya,
                                             int yb, int j, uint32_t g, int lane) {
   using G = Geo<ST>;
-  const uint32_t slot = cx.ring + (uint32_t)(G::kSlot * (g % kSlots));
+  const uint32_t slot = cx.ring + (uint32_t)(G::kSlot * (g % Geo<ST>::kSlots));
   const uint32_t bar = bar_addr<ST>(cx, g);
   if (j == cx.lose_stage) return;  // injected loss: this stage's wait must run out
   if constexpr (ST == kTensor) {
     if (lane == 0) {
       fence_proxy_async();
       mbar_expect_tx(bar, (uint32_t)G::kSlot);
-      tma_load_2d(slot, cx.map, x0 - 16, ya - 2 + kStageRows * j, bar);
-      tma_load_2d(slot + (uint32_t)G::kStrip, cx.map, x0 - 16, yb - 2 + kStageRows * j, bar);
+      tma_load_2d(slot, cx.map, x0 - 16, ya - 2 + Geo<ST>::kStageRows * j, bar);
+      tma_load_2d(slot + (uint32_t)G::kStrip, cx.map, x0 - 16, yb - 2 + Geo<ST>::kStageRows * j, bar);
     }
   } else {
     uint32_t bytes = 0;
     const uint8_t *from = nullptr;
     uint32_t to = 0;
-    if (lane < 2 * kStageRows) {
-      const int s = lane / kStageRows, k = lane % kStageRows;
-      const int y = (s ? yb : ya) - 2 + kStageRows * j + k;
+    if (lane < 2 * Geo<ST>::kStageRows) {
+      constexpr int B = G::kBpp;
+      const int s = lane / Geo<ST>::kStageRows, k = lane % Geo<ST>::kStageRows;
+      const int y = (s ? yb : ya) - 2 + Geo<ST>::kStageRows * j + k;
       to = slot + (uint32_t)(s * G::kStrip + k * G::kRowPitch + G::kRowData);
       int32_t hdr = 0;
       if (y >= 0 && y < im.H) {
         const uintptr_t row = (uintptr_t)im.src + (uintptr_t)(uint32_t)y * im.sp;
-        const uintptr_t lo = row + (uintptr_t)max(x0 - 2, 0);
-        const uintptr_t hi = row + (uintptr_t)min(x0 + kCols + 2, im.W);
+        const uintptr_t lo = row + (uintptr_t)(B * max(x0 - 2, 0));
+        const uintptr_t hi = row + (uintptr_t)(B * min(x0 + kCols + 2, im.W));
         const uintptr_t g0 = lo & ~(uintptr_t)15;
         from = (const uint8_t *)g0;
         bytes = (uint32_t)(((hi + 15) & ~(uintptr_t)15) - g0);
-        hdr = (int32_t)((intptr_t)(row + (uintptr_t)(x0 - 2)) - (intptr_t)g0);
+        hdr = (int32_t)((intptr_t)row + (intptr_t)(B * (x0 - 2)) - (intptr_t)g0);
       }
       *(int32_t *)(cx.ringp + (slot - cx.ring) + G::kHdr + 4 * lane) = hdr;
     }
@@ -925,12 +996,12 @@ __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg
   const int wl = W - x;  // this lane's columns inside the image (PART)
   const int yb = ya + R;
   const int steps = R + 4;
-  const int n_stages = (steps + kStageRows - 1) / kStageRows;
+  const int n_stages = (steps + Geo<ST>::kStageRows - 1) / Geo<ST>::kStageRows;
   const uint32_t g0 = cx.gstage;
   const bool mapped_rule = border == kReplicate || border == kReflect101;
 
   __syncwarp();  // every lane is done with the ring slots about to be refilled
-  for (int j = 0; j < kSlots && j < n_stages; ++j)
+  for (int j = 0; j < Geo<ST>::kSlots && j < n_stages; ++j)
     issue_stage<ST>(im, cx, x0, ya, yb, j, g0 + (uint32_t)j, lane);
 
   // Edge-item bookkeeping.
@@ -954,12 +1025,12 @@ __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg
       const int m = map_index(col, W, border, &z);
       const int o = m - (x0 - 2);  // staged offset relative to column x0-2
       off[j] = o < 0 ? 0 : (o > kCols + 3 ? kCols + 3 : o);
-      if (ST == kBulk && border != kReplicate && border != kReflect101 && (col < 0 || col >= W))
+      if (G::kRows && border != kReplicate && border != kReflect101 && (col < 0 || col >= W))
         zmask |= 1u << j;
     }
     // Lanes whose columns cross an image edge read through the mapping (the
     // bulk staging also for CONSTANT0, whose outside columns read 0).
-    edge_lane = (mapped_rule || (ST == kBulk && border == kConstant0)) &&
+    edge_lane = (mapped_rule || (G::kRows && border == kConstant0)) &&
                 (x - 2 < 0 || x + 5 >= W);
     const int vec_need = vec_bytes(FMT);
     vec = im.dst_align >= vec_need;
@@ -982,16 +1053,18 @@ __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg
     } else {
       const uint32_t slot = rd - (uint32_t)(k * G::kRowPitch + G::kRowData);
       base_a = rd + (uint32_t)lds_s32(slot + G::kHdr + 4 * k);
-      base_b = rd + (uint32_t)G::kStrip + (uint32_t)lds_s32(slot + G::kHdr + 4 * (kStageRows + k));
+      base_b = rd + (uint32_t)G::kStrip + (uint32_t)lds_s32(slot + G::kHdr + 4 * (Geo<ST>::kStageRows + k));
     }
     uint32_t c[8];
     if (GEN) {
       const int ra = ya - 2 + s, rb = yb - 2 + s;  // input rows of this step
       const bool out_a = ra < 0 || ra >= H, out_b = rb < 0 || rb >= H;
-      if (((mapped_rule || ST == kBulk) && (out_a || out_b)) || edge_lane)
-        gather_cols(im, base_a, base_b, off, zmask, x, ra, rb, out_a, out_b, border, c);
-      else if (ST == kTensor)
+      if (((mapped_rule || G::kRows) && (out_a || out_b)) || edge_lane)
+        gather_cols<G::kBpp>(im, base_a, base_b, off, zmask, x, ra, rb, out_a, out_b, border, c);
+      else if constexpr (ST == kTensor)
         read_cols<G::kStrip>(base_a + kNC * lane, c);
+      else if constexpr (ST == kRgbBulk)
+        read_cols_rgb(base_a + 3 * kNC * lane, base_b + 3 * kNC * lane, c);
       else
         read_cols_any(base_a + kNC * lane, base_b + kNC * lane, c);
     } else if constexpr (ST == kTensor) {
@@ -1000,6 +1073,8 @@ __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg
 #else
       read_cols<G::kStrip>(base_a + kNC * lane, c);
 #endif
+    } else if constexpr (ST == kRgbBulk) {
+      read_cols_rgb(base_a + 3 * kNC * lane, base_b + 3 * kNC * lane, c);
     } else {
       read_cols_any(base_a + kNC * lane, base_b + kNC * lane, c);
     }
@@ -1030,10 +1105,10 @@ __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg
   };
 
   if (!wait_stage<ST>(cx, g0, err)) {
-    drain_stages<ST>(cx, g0 + 1, g0 + (uint32_t)min(kSlots, n_stages));
+    drain_stages<ST>(cx, g0 + 1, g0 + (uint32_t)min(Geo<ST>::kSlots, n_stages));
     return false;
   }
-  uint32_t rd = cx.ring + (uint32_t)(G::kSlot * (g0 % kSlots) + G::kRowData);
+  uint32_t rd = cx.ring + (uint32_t)(G::kSlot * (g0 % Geo<ST>::kSlots) + G::kRowData);
 #pragma unroll
   for (int s = 0; s < 4; ++s)  // rows 0..3 only fill the window
     step(rd + (uint32_t)(s * G::kRowPitch), s, s, false);
@@ -1042,20 +1117,20 @@ __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg
   // trips tile the steps and the stage boundaries fall on trip boundaries).
 #pragma unroll 1
   for (int s = 4; s < steps; s += kUnroll) {
-    if ((s & (kStageRows - 1)) == 0) {
-      const int j = s / kStageRows;
+    if ((s & (Geo<ST>::kStageRows - 1)) == 0) {
+      const int j = s / Geo<ST>::kStageRows;
       __syncwarp();  // stage j-1 has been read by every lane
-      if (j - 1 + kSlots < n_stages)
-        issue_stage<ST>(im, cx, x0, ya, yb, j - 1 + kSlots, g0 + (uint32_t)(j - 1 + kSlots),
+      if (j - 1 + Geo<ST>::kSlots < n_stages)
+        issue_stage<ST>(im, cx, x0, ya, yb, j - 1 + Geo<ST>::kSlots, g0 + (uint32_t)(j - 1 + Geo<ST>::kSlots),
                         lane);
       if (!wait_stage<ST>(cx, g0 + (uint32_t)j, err)) {
         drain_stages<ST>(cx, g0 + (uint32_t)j + 1,
-                         g0 + (uint32_t)min(j - 1 + kSlots + 1, n_stages));
+                         g0 + (uint32_t)min(j - 1 + Geo<ST>::kSlots + 1, n_stages));
         return false;
       }
-      rd = cx.ring + (uint32_t)(G::kSlot * ((g0 + (uint32_t)j) % kSlots) + G::kRowData);
+      rd = cx.ring + (uint32_t)(G::kSlot * ((g0 + (uint32_t)j) % Geo<ST>::kSlots) + G::kRowData);
     }
-    const int k0 = s & (kStageRows - 1);
+    const int k0 = s & (Geo<ST>::kStageRows - 1);
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) step(rd + (uint32_t)(u * G::kRowPitch), k0 + u, s + u, true);
     rd += kUnroll * G::kRowPitch;
@@ -1210,14 +1285,14 @@ __device__ __forceinline__ void init_ring(ItemCtx &cx, WarpRing<ST> &ring, int l
   cx.gstage = 0;
   cx.lose_stage = -1;
   if (lane == 0) {
-    for (int i = 0; i < kSlots; ++i)
-      mbar_init(cx.ring + (uint32_t)(kSlots * Geo<ST>::kSlot + 8 * i), 1u);
+    for (int i = 0; i < Geo<ST>::kSlots; ++i)
+      mbar_init(cx.ring + (uint32_t)(Geo<ST>::kSlots * Geo<ST>::kSlot + 8 * i), 1u);
     mbar_init_fence();
   }
-  if constexpr (ST == kBulk) {
+  if constexpr (Geo<ST>::kRows) {
     // Zero the pads and offsets once so that no read of the ring ever meets
     // uninitialised bytes.
-    for (int i = lane; i < kSlots * Geo<ST>::kSlot / 4; i += 32)
+    for (int i = lane; i < Geo<ST>::kSlots * Geo<ST>::kSlot / 4; i += 32)
       ((uint32_t *)&ring.slot[0][0])[i] = 0u;
   }
   __syncwarp();

@@ -57,10 +57,16 @@ int resident_of() {
     }                                                                               \
   } while (0)
 
-// The single-image kernel has one more mode: fast items of a ragged width.
+// The single-image kernel has one more mode (fast items of a ragged width)
+// and one more staging (RGB sources).
 #define SOBEL4_TMA_SWITCH_SINGLE(MODE_, ST_, CALL)                                  \
   do {                                                                              \
-    if ((MODE_) == tma::kFastPart) {                                                \
+    if ((ST_) == tma::kRgbBulk) {                                                   \
+      if ((MODE_) == tma::kFastOnly) { CALL(tma::kFastOnly, tma::kRgbBulk); }       \
+      else if ((MODE_) == tma::kFastPart) { CALL(tma::kFastPart, tma::kRgbBulk); }  \
+      else if ((MODE_) == tma::kGeneralOnly) { CALL(tma::kGeneralOnly, tma::kRgbBulk); } \
+      else { CALL(tma::kAll, tma::kRgbBulk); }                                      \
+    } else if ((MODE_) == tma::kFastPart) {                                         \
       if ((ST_) == tma::kTensor) { CALL(tma::kFastPart, tma::kTensor); }            \
       else { CALL(tma::kFastPart, tma::kBulk); }                                    \
     } else {                                                                        \
