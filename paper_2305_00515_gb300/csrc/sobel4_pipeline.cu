@@ -22,6 +22,7 @@ struct Slot {
   unsigned int *d_pair = nullptr;  // the captured kernel's work-queue counter pair (4 words)
   cudaStream_t stream = nullptr;
   cudaGraphExec_t exec = nullptr;
+  cudaGraphExec_t kexec = nullptr;  // the slot's kernel alone (caller buffers)
   cudaEvent_t done = nullptr;
   bool pending = false;
 };
@@ -48,6 +49,7 @@ void release(sobel4_pipeline_ctx *p) {
   for (Slot &s : p->slots) {
     if (s.stream) cudaStreamSynchronize(s.stream);
     if (s.exec) cudaGraphExecDestroy(s.exec);
+    if (s.kexec) cudaGraphExecDestroy(s.kexec);
     if (s.done) cudaEventDestroy(s.done);
     if (s.stream) cudaStreamDestroy(s.stream);
     if (s.h_in) cudaFreeHost(s.h_in);
@@ -100,22 +102,45 @@ extern "C" sobel4_status sobel4_pipeline_create(sobel4_handle h, int32_t height,
     e = cudaMemsetAsync(s.d_in, 0, p->in_bytes, s.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s.stream);
     if (e != cudaSuccess) break;
+    // The kernel is captured alone (kexec, for frames in caller buffers),
+    // then the slot's two copies are added as 1-D memcpy nodes before and
+    // after it (exec: upload, kernel, download as one graph).
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) break;
-    cudaError_t ce = cudaMemcpyAsync(s.d_in, s.h_in, p->in_bytes, cudaMemcpyHostToDevice, s.stream);
-    if (ce == cudaSuccess)
-      st = sobel4::run_with_pair(h, s.d_in, p->in_pitch, s.d_out, p->out_pitch, height, width,
-                                 border, fmt, s.stream, s.d_pair);
-    if (ce == cudaSuccess && st == SOBEL4_OK)
-      ce = cudaMemcpyAsync(s.h_out, s.d_out, p->out_bytes, cudaMemcpyDeviceToHost, s.stream);
+    st = sobel4::run_with_pair(h, s.d_in, p->in_pitch, s.d_out, p->out_pitch, height, width,
+                               border, fmt, s.stream, s.d_pair);
     e = cudaStreamEndCapture(s.stream, &g);
-    if (e == cudaSuccess) e = ce;
     if (st != SOBEL4_OK || e != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
       break;
     }
-    e = cudaGraphInstantiate(&s.exec, g, 0);
+    e = cudaGraphInstantiate(&s.kexec, g, 0);
+    if (e == cudaSuccess) {
+      size_t n = 0;
+      e = cudaGraphGetNodes(g, nullptr, &n);
+      std::vector<cudaGraphNode_t> kernels(n);
+      if (e == cudaSuccess && n) e = cudaGraphGetNodes(g, kernels.data(), &n);
+      // roots: nodes without dependencies; leaves: nodes nothing depends on
+      std::vector<cudaGraphNode_t> roots, leaves;
+      for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
+        size_t nd = 0, nu = 0;
+        e = cudaGraphNodeGetDependencies(kernels[i], nullptr, nullptr, &nd);
+        if (e == cudaSuccess) e = cudaGraphNodeGetDependentNodes(kernels[i], nullptr, nullptr, &nu);
+        if (e == cudaSuccess && nd == 0) roots.push_back(kernels[i]);
+        if (e == cudaSuccess && nu == 0) leaves.push_back(kernels[i]);
+      }
+      cudaGraphNode_t copy_in = nullptr, copy_out = nullptr;
+      if (e == cudaSuccess)
+        e = cudaGraphAddMemcpyNode1D(&copy_in, g, nullptr, 0, s.d_in, s.h_in, p->in_bytes,
+                                     cudaMemcpyHostToDevice);
+      for (size_t i = 0; i < roots.size() && e == cudaSuccess; ++i)
+        e = cudaGraphAddDependencies(g, &copy_in, &roots[i], nullptr, 1);
+      if (e == cudaSuccess)
+        e = cudaGraphAddMemcpyNode1D(&copy_out, g, leaves.data(), leaves.size(), s.h_out,
+                                     s.d_out, p->out_bytes, cudaMemcpyDeviceToHost);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&s.exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) break;
   }
@@ -146,17 +171,45 @@ extern "C" sobel4_status sobel4_pipeline_buffers(sobel4_pipeline p, int32_t slot
   return SOBEL4_OK;
 }
 
+namespace {
+
+// Launches the slot's frame: its graph on its own buffers, else the caller's
+// upload, the kernel's graph and the caller's download on the slot's stream.
+sobel4_status launch_slot(sobel4_pipeline p, Slot &s, const void *in, void *out) {
+  cudaError_t e = cudaSuccess;
+  if (in == s.h_in && out == s.h_out) {
+    e = cudaGraphLaunch(s.exec, s.stream);
+  } else {
+    e = cudaMemcpyAsync(s.d_in, in, p->in_bytes, cudaMemcpyHostToDevice, s.stream);
+    if (e == cudaSuccess) e = cudaGraphLaunch(s.kexec, s.stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(out, s.d_out, p->out_bytes, cudaMemcpyDeviceToHost, s.stream);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(s.done, s.stream);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    sobel4::note_cuda_error(p->h, e);
+    return SOBEL4_ERR_CUDA;
+  }
+  s.pending = true;
+  sobel4::note_launches(p->h, p->kernels_per_frame);
+  return SOBEL4_OK;
+}
+
+}  // namespace
+
 extern "C" sobel4_status sobel4_pipeline_submit(sobel4_pipeline p, int32_t slot) {
+  return sobel4_pipeline_submit_from(p, slot, nullptr, nullptr);
+}
+
+extern "C" sobel4_status sobel4_pipeline_submit_from(sobel4_pipeline p, int32_t slot,
+                                                     const uint8_t *h_in, void *h_out) {
   if (!p || slot < 0 || slot >= (int32_t)p->slots.size()) return SOBEL4_ERR_INVALID_ARG;
   Slot &s = p->slots[slot];
   if (s.pending) return SOBEL4_ERR_INVALID_ARG;  // wait for the slot before refilling it
   sobel4::DeviceScope scope(p->device);
-  cudaError_t e = cudaGraphLaunch(s.exec, s.stream);
-  if (e == cudaSuccess) e = cudaEventRecord(s.done, s.stream);
-  if (e != cudaSuccess) return SOBEL4_ERR_CUDA;
-  s.pending = true;
-  sobel4::note_launches(p->h, p->kernels_per_frame);
-  return SOBEL4_OK;
+  return launch_slot(p, s, h_in ? (const void *)h_in : (const void *)s.h_in,
+                     h_out ? h_out : s.h_out);
 }
 
 extern "C" sobel4_status sobel4_pipeline_wait(sobel4_pipeline p, int32_t slot) {

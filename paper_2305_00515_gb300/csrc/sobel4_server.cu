@@ -4,10 +4,13 @@
 // uploaded on a copy stream, packed into one persistent batched launch per
 // scheduling step (at most kMaxInFlight batches on the GPU at once, so
 // requests that arrive while a batch runs join the next one), and downloaded
-// on a third stream (a batch of one runs as a single-image launch).
-// Completion is signalled from the download stream by a host function, so
-// the scheduler never polls the GPU.  In plain mode every request is its own
-// single-image launch instead: the comparison point.
+// on a third stream (a batch of one runs as a single-image launch).  Each
+// request completes when its own download has landed: a host function after
+// each download signals it, so the scheduler never polls the GPU and a small
+// request never waits for a large one's download.  Two comparison modes:
+// every request its own single-image launch on the same three streams
+// (plain = 1), or one sobel4_run per request in arrival order on ONE stream,
+// upload, kernel and download back to back (plain = 2).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -125,34 +128,47 @@ struct sobel4_server_ctx {
 
 namespace {
 
+struct Batch;
+
+// One request of a batch, the argument of its completion host function.
+struct Member {
+  Batch *b;
+  uint64_t ticket;
+};
+
 struct Batch {
   sobel4_server_ctx *s;
-  std::vector<uint64_t> tickets;
+  std::vector<Member> members;
+  int remaining = 0;  // members whose download has not landed yet
   cudaEvent_t done;
 };
 
-// Download stream reached the end of a batch: results are in host memory.
-void CUDART_CB batch_finished(void *arg) {
-  Batch *b = (Batch *)arg;
+// A request's download has landed: its result is in host memory.  The batch
+// leaves the GPU with its last member.
+void CUDART_CB member_finished(void *arg) {
+  Member *m = (Member *)arg;
+  Batch *b = m->b;
   sobel4_server_ctx *s = b->s;
+  bool last = false;
   {
     std::lock_guard<std::mutex> lock(s->mu);
-    const Clock::time_point now = Clock::now();
-    for (uint64_t t : b->tickets) {
-      auto it = s->reqs.find(t);
-      if (it == s->reqs.end()) continue;
+    auto it = s->reqs.find(m->ticket);
+    if (it != s->reqs.end()) {
       Request &r = it->second;
-      r.t_done = now;
+      r.t_done = Clock::now();
       r.state = kDone;
       s->arena.release(r.off, r.arena_bytes());
       s->stats.completed += 1;
     }
-    s->in_flight -= 1;
-    s->event_pool.push_back(b->done);
+    last = --b->remaining == 0;
+    if (last) {
+      s->in_flight -= 1;
+      s->event_pool.push_back(b->done);
+    }
   }
   s->cv_done.notify_all();
   s->cv_work.notify_one();
-  delete b;
+  if (last) delete b;
 }
 
 void fail_all(sobel4_server_ctx *s) {
@@ -198,7 +214,11 @@ void scheduler(sobel4_server_ctx *s) {
   sobel4::DeviceScope scope(s->device);
   const int fmt = s->opt.format;
   const size_t planes = fmt == SOBEL4_OUT_S16X4 ? 4 : 1;
+  const bool serial = s->opt.plain == 2;
+  // the one-stream mode runs everything on the upload stream
+  cudaStream_t up = s->up, comp = serial ? s->up : s->comp, down = serial ? s->up : s->down;
   std::vector<Job> uploads, members;
+  bool more = false;  // one-stream mode: admitted requests still to issue
   for (;;) {
     uploads.clear();
     members.clear();
@@ -206,9 +226,10 @@ void scheduler(sobel4_server_ctx *s) {
     {
       std::unique_lock<std::mutex> lock(s->mu);
       s->cv_work.wait(lock, [&] {
-        return s->stop || s->failed || !s->incoming.empty() ||
+        return more || s->stop || s->failed || !s->incoming.empty() ||
                (!s->admitted.empty() && s->in_flight < kMaxInFlight);
       });
+      more = false;
       if (s->failed) break;
       if (s->stop && s->incoming.empty() && s->admitted.empty()) break;
       // 1. Admission, first in first out, while the arena has room.
@@ -225,8 +246,9 @@ void scheduler(sobel4_server_ctx *s) {
         s->admitted.push_back(t);
         s->incoming.pop_front();
       }
-      // 2. One launch of everything admitted (bounded by max_batch).
-      if (!s->admitted.empty() && s->in_flight < kMaxInFlight) {
+      // 2. One launch of everything admitted (bounded by max_batch; in the
+      //    one-stream mode one request per launch, as many as are admitted).
+      if (!s->admitted.empty() && (serial || s->in_flight < kMaxInFlight)) {
         b = new (std::nothrow) Batch();
         cudaEvent_t ev = b ? take_event(s) : nullptr;
         if (!b || !ev) {
@@ -236,39 +258,51 @@ void scheduler(sobel4_server_ctx *s) {
         }
         b->s = s;
         b->done = ev;
-        while (!s->admitted.empty() && (int32_t)members.size() < s->opt.max_batch) {
+        const int32_t cap = serial ? 1 : s->opt.max_batch;
+        while (!s->admitted.empty() && (int32_t)members.size() < cap) {
           const uint64_t t = s->admitted.front();
           s->admitted.pop_front();
           Request &r = s->reqs[t];
           r.state = kInFlight;
-          b->tickets.push_back(t);
+          b->members.push_back(Member{b, t});
           members.push_back(job_of(t, r));
         }
+        b->remaining = (int)b->members.size();
         s->in_flight += 1;
         s->stats.batches += 1;
         if ((uint64_t)members.size() > s->stats.max_batch_seen)
           s->stats.max_batch_seen = members.size();
       }
+      more = serial && !s->admitted.empty();
     }
     // CUDA work, unlocked.  Only this thread issues work on the three streams.
     cudaError_t e = cudaSuccess;
-    for (const Job &j : uploads) {
+    // One-stream mode: each request's upload goes right before its kernel.
+    for (size_t i = 0; i < uploads.size() && !serial; ++i) {
+      const Job &j = uploads[i];
       e = cudaMemcpy2DAsync(j.d_in, j.d_sp, j.h_src, j.sp, (size_t)j.W, (size_t)j.H,
-                            cudaMemcpyHostToDevice, s->up);
+                            cudaMemcpyHostToDevice, up);
       if (e != cudaSuccess) break;
     }
     sobel4_status st = SOBEL4_OK;
-    if (e == cudaSuccess && b) {
+    if (e == cudaSuccess && b && serial) {
+      const Job &j = members[0];
+      e = cudaMemcpy2DAsync(j.d_in, j.d_sp, j.h_src, j.sp, (size_t)j.W, (size_t)j.H,
+                            cudaMemcpyHostToDevice, up);
+      if (e == cudaSuccess)
+        st = sobel4_run(s->h, j.d_in, j.d_sp, j.d_out, j.d_dp, j.H, j.W,
+                        (sobel4_border)s->opt.border, (sobel4_format)fmt, up);
+    } else if (e == cudaSuccess && b) {
       // The upload stream runs in order: its tail covers every upload of this batch.
-      e = cudaEventRecord(b->done, s->up);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(s->comp, b->done, 0);
+      e = cudaEventRecord(b->done, up);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(comp, b->done, 0);
       if (e == cudaSuccess) {
         // A batch of one runs as a single-image launch: the batched path adds
         // a descriptor upload and gains nothing for one image.
         if (s->opt.plain || members.size() == 1) {
           for (const Job &j : members) {
             st = sobel4_run(s->h, j.d_in, j.d_sp, j.d_out, j.d_dp, j.H, j.W,
-                            (sobel4_border)s->opt.border, (sobel4_format)fmt, s->comp);
+                            (sobel4_border)s->opt.border, (sobel4_format)fmt, comp);
             if (st != SOBEL4_OK) break;
           }
         } else {
@@ -277,24 +311,32 @@ void scheduler(sobel4_server_ctx *s) {
           for (const Job &j : members)
             imgs.push_back(sobel4_image{j.d_in, j.d_sp, j.d_out, j.d_dp, j.H, j.W});
           st = sobel4_run_batched(s->h, imgs.data(), (int32_t)imgs.size(),
-                                  (sobel4_border)s->opt.border, (sobel4_format)fmt, s->comp);
+                                  (sobel4_border)s->opt.border, (sobel4_format)fmt, comp);
         }
       }
-      if (e == cudaSuccess && st == SOBEL4_OK) e = cudaEventRecord(b->done, s->comp);
-      if (e == cudaSuccess && st == SOBEL4_OK) e = cudaStreamWaitEvent(s->down, b->done, 0);
-      for (size_t i = 0; i < members.size() && e == cudaSuccess && st == SOBEL4_OK; ++i) {
-        const Job &j = members[i];
-        e = cudaMemcpy2DAsync(j.h_dst, j.dp, j.d_out, j.d_dp, (size_t)j.W * elem_bytes(fmt),
-                              (size_t)j.H * planes, cudaMemcpyDeviceToHost, s->down);
-      }
-      if (e == cudaSuccess && st == SOBEL4_OK) e = cudaLaunchHostFunc(s->down, batch_finished, b);
+      if (e == cudaSuccess && st == SOBEL4_OK) e = cudaEventRecord(b->done, comp);
+      if (e == cudaSuccess && st == SOBEL4_OK) e = cudaStreamWaitEvent(down, b->done, 0);
+    }
+    // Each member's download, then its completion.
+    size_t enqueued = 0;  // completion host functions on the GPU's queue
+    for (size_t i = 0; b && i < members.size() && e == cudaSuccess && st == SOBEL4_OK; ++i) {
+      const Job &j = members[i];
+      e = cudaMemcpy2DAsync(j.h_dst, j.dp, j.d_out, j.d_dp, (size_t)j.W * elem_bytes(fmt),
+                            (size_t)j.H * planes, cudaMemcpyDeviceToHost, down);
+      if (e == cudaSuccess) e = cudaLaunchHostFunc(down, member_finished, &b->members[i]);
+      if (e == cudaSuccess) ++enqueued;
     }
     if (e != cudaSuccess || st != SOBEL4_OK) {
       std::lock_guard<std::mutex> lock(s->mu);
-      if (b) {  // never reached the GPU: nothing will retire it
-        s->in_flight -= 1;
-        s->event_pool.push_back(b->done);
-        delete b;
+      if (b) {
+        // members whose completion never reached the GPU will not call back;
+        // the batch is retired here once none of the others is outstanding
+        b->remaining -= (int)(members.size() - enqueued);
+        if (b->remaining == 0) {
+          s->in_flight -= 1;
+          s->event_pool.push_back(b->done);
+          delete b;
+        }
       }
       fail_all(s);
       break;
@@ -310,7 +352,7 @@ extern "C" sobel4_status sobel4_server_create(sobel4_handle h, const sobel4_serv
   *out = nullptr;
   if (!h || !opt || opt->border < SOBEL4_BORDER_VALID || opt->border > SOBEL4_BORDER_CONSTANT0 ||
       opt->format < SOBEL4_OUT_F32 || opt->format > SOBEL4_OUT_EDGE8 || opt->max_batch < 0 ||
-      opt->memory_budget < 0 || (opt->plain != 0 && opt->plain != 1))
+      opt->memory_budget < 0 || opt->plain < 0 || opt->plain > 2)
     return SOBEL4_ERR_INVALID_ARG;
   sobel4_server_ctx *s = new (std::nothrow) sobel4_server_ctx();
   if (!s) return SOBEL4_ERR_OOM;

@@ -22,6 +22,11 @@ ragged_shapes(n, seed)
 video_background / video_frame
     A (H+12) x (W+16) rects_noise background; frame k is its crop at offset
     (k mod 17, 2k mod 13) plus fresh N(0, 8^2) noise keyed by (seed, k).
+video_frames_torch(bg, first, count, H, W, seed, device)
+    The same translation schedule with the noise drawn on a torch device
+    (one seeded generator per frame: (seed, k)), for streaming thousands of
+    distinct frames without a CPU noise pass; returns a (count, H, W) uint8
+    tensor on `device`.
 serving_trace(rate, duration, seed)
     Poisson arrival times and a resolution per request drawn from
     {640x480: 40%, 1280x720: 30%, 1920x1080: 20%, 3840x2160: 10%}.
@@ -111,6 +116,22 @@ def video_frame(bg: np.ndarray, k: int, H: int, W: int, seed: int,
     dx, dy = video_offset(k)
     crop = bg[dy:dy + H, dx:dx + W]
     return add_noise(crop, _rng(seed, 5, k), sigma)
+
+
+def video_frames_torch(bg: np.ndarray, first: int, count: int, H: int, W: int, seed: int,
+                       device="cuda", sigma: float = 8.0):
+    import torch
+    bgt = torch.from_numpy(bg).to(device=device, dtype=torch.float32)
+    out = torch.empty((count, H, W), dtype=torch.uint8, device=device)
+    g = torch.Generator(device=device)
+    for i in range(count):
+        k = first + i
+        dx, dy = video_offset(k)
+        g.manual_seed(int(seed) * 1000003 + k)
+        noise = torch.randn((H, W), generator=g, device=device, dtype=torch.float32)
+        noise.mul_(sigma).add_(bgt[dy:dy + H, dx:dx + W])
+        out[i] = noise.round_().clamp_(0, 255).to(torch.uint8)
+    return out
 
 
 def serving_trace(rate: float = 400.0, duration: float = 60.0, seed: int = 4):

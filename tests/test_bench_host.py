@@ -26,6 +26,9 @@ def test_reference_arm_json_line():
     assert line["value"] > 0 and line["higher_is_better"] is True
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    # the same config dict as our arm prints, so the two lines compare
+    assert line["config"] == bench.workload_config(1)
+    assert len(line["input_sha256"]) == 64
 
 
 def test_cpu_baseline_record_has_all_core_and_one_core_rates():

@@ -52,3 +52,63 @@ def test_pipeline_rejects_bad_arguments():
         assert pkg.sobel4_pipeline_submit(p, 5) == 1
         assert pkg.sobel4_pipeline_wait(p, -1) == 1
         assert pkg.sobel4_pipeline_destroy(p) == 0
+
+
+def test_pipeline_submit_from_caller_buffers():
+    """Each frame from its own host buffer (pinned by cudaHostAlloc, or a numpy
+    array registered with cudaHostRegister), results into caller buffers."""
+    H, W = 120, 256
+    bg = synth.video_background(H, W, 8)
+    frames = [synth.video_frame(bg, k, H, W, 8) for k in range(6)]
+    pinned_in = [torch.from_numpy(f).pin_memory() for f in frames[:3]]
+    ring = np.stack(frames[3:])  # registered page-locked numpy memory
+    cudart = torch.cuda.cudart()
+    assert int(cudart.cudaHostRegister(ring.ctypes.data, ring.nbytes, 0)) == 0
+    outs = [torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in frames]
+    try:
+        with pkg.Sobel4(0) as s:
+            pipe = pkg.Pipeline(s, H, W, "valid", "f32", slots=2)
+            for k in range(len(frames)):
+                slot = k % 2
+                pipe.wait(slot)
+                src = pinned_in[k].data_ptr() if k < 3 else ring.ctypes.data + (k - 3) * H * W
+                st = pkg.sobel4_pipeline_submit_from(pipe.p, slot, src, outs[k].data_ptr())
+                assert st == 0, (k, pkg.sobel4_last_cuda_error(s.handle))
+            for slot in range(2):
+                pipe.wait(slot)
+            # back to the slot's own buffers
+            pipe.inputs[0][:] = frames[0]
+            pipe.submit(0)
+            pipe.wait(0)
+            own = pipe.outputs[0].copy()
+            pipe.close()
+    finally:
+        cudart.cudaHostUnregister(ring.ctypes.data)
+    for k, frame in enumerate(frames):
+        assert same_bits(outs[k].numpy(), oracle.sobel4(frame, "valid", "f32")), k
+    assert same_bits(own, oracle.sobel4(frames[0], "valid", "f32"))
+
+
+def test_pipeline_4k_frames():
+    """3840x2160 frames, the video configuration's size, through the pipeline."""
+    H, W = 2160, 3840
+    bg = synth.video_background(H, W, 3)
+    ks = (0, 1, 17, 220)
+    frames = {k: synth.video_frame(bg, k, H, W, 3) for k in ks}
+    with pkg.Sobel4(0) as s:
+        pipe = pkg.Pipeline(s, H, W, "valid", "f32", slots=2)
+        got = {}
+        for i, k in enumerate(ks):
+            slot = i % 2
+            pipe.wait(slot)
+            if i >= 2:
+                got[ks[i - 2]] = pipe.outputs[slot].copy()
+            pipe.inputs[slot][:] = frames[k]
+            pipe.submit(slot)
+        for i in range(len(ks) - 2, len(ks)):
+            pipe.wait(i % 2)
+            got[ks[i]] = pipe.outputs[i % 2].copy()
+        pipe.close()
+    for k in ks:
+        want = oracle.sobel4(frames[k], "valid", "f32", threads=oracle.cpu_count())
+        assert same_bits(got[k], want), k

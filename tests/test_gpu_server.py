@@ -1,7 +1,9 @@
 """The continuous-batching server: every request's result equals the oracle
-whether it ran alone, in a batch with others, or in plain one-launch-per-
-request mode; admission respects the device-memory budget; the batched mode
-really packs concurrent requests into shared launches."""
+and its own standalone sobel4_run, whether it ran in a batch with others, as
+its own launch, or in the one-stream plain mode; admission respects the
+device-memory budget; the batched mode really packs concurrent requests into
+shared launches (a large first request keeps the GPU busy while the others
+arrive, so they meet in the next batch)."""
 import threading
 
 import numpy as np
@@ -22,11 +24,13 @@ def pinned(shape, dtype):
     return t, t.numpy().view(dtype).reshape(shape)
 
 
-def make_requests(n, seed, fmt):
+def make_requests(n, seed, fmt, first=None):
     rng = np.random.default_rng(seed)
     reqs = []
     for i in range(n):
         H, W = (int(v) for v in rng.integers(5, 400, size=2))
+        if i == 0 and first:
+            H, W = first
         _, src = pinned((H, W), np.uint8)
         src[:] = synth.rects_noise(H, W, seed * 100 + i)
         dt = {"f32": np.float32, "u8": np.uint8, "s16x4": np.int16}[fmt]
@@ -67,22 +71,32 @@ def run_server(reqs, fmt, border, plain, budget=0, threads=1):
     return lats, stats
 
 
-@pytest.mark.parametrize("plain", [0, 1])
+def run_alone(img, border, fmt):
+    """The request's image through its own sobel4_run (no server, no batch)."""
+    with pkg.Sobel4(0) as s:
+        out = s.run(torch.from_numpy(np.ascontiguousarray(img)).cuda(), border=border, fmt=fmt)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("plain", [0, 1, 2])
 @pytest.mark.parametrize("fmt,border", [("f32", "valid"), ("u8", "reflect101"),
                                         ("s16x4", "constant0")])
-def test_server_results_match_oracle(plain, fmt, border):
-    reqs = make_requests(24, 3 + plain, fmt)
-    lats, stats = run_server(reqs, fmt, border, plain, threads=2)
+def test_server_results_match_oracle_alone_and_in_the_mix(plain, fmt, border):
+    # request 0 is a 3840x2160 frame: while it is on the GPU the others arrive
+    reqs = make_requests(24, 3 + plain, fmt, first=(2160, 3840))
+    lats, stats = run_server(reqs, fmt, border, plain, threads=1)
     assert stats["submitted"] == stats["completed"] == len(reqs)
     assert all(l > 0 for l in lats)
-    # how many requests share a launch depends on arrival timing; every request is in one
     assert 1 <= stats["batches"] <= len(reqs)
-    assert stats["max_batch_seen"] >= 1
-    if plain == 1:
-        assert stats["max_batch_seen"] >= 1
+    if plain == 0:
+        assert stats["max_batch_seen"] >= 2, "no two requests ever shared a launch"
+    elif plain == 2:
+        assert stats["max_batch_seen"] == 1  # one request per step on the one stream
     assert stats["device_bytes_in_use"] == 0
     for src, dst, _ in reqs:
         assert same_bits(dst, oracle.sobel4(src, border, fmt))
+        assert same_bits(dst, run_alone(src, border, fmt))
 
 
 def test_server_admission_under_small_budget():
