@@ -67,6 +67,9 @@ def parse_args():
     ap.add_argument("--profile-batch", type=int, default=0, metavar="N",
                     help="run the first N images of the 512-image ragged batch (seed 1) through "
                          "sobel4_run_batched twice and exit (a capture target for ncu)")
+    ap.add_argument("--profile-single", choices=["rgb", "weights"], default=None,
+                    help="launch one 8192x8192 image twice through the colour input or the "
+                         "runtime-weight path, then exit (for ncu)")
     ap.add_argument("--profile-variants", action="store_true",
                     help="run every kernel variant twice on the workload image and exit "
                          "(a capture target for ncu; prints no JSON line)")
@@ -417,6 +420,57 @@ def bench_rgb(torch, pkg, synth, peak: float, reps: int = 20):
             "frac": H * W * 7 / (us * 1e-6) / 1e9 / peak,
             "rows_match_oracle": bool(np.array_equal(got.view(np.uint32), want.view(np.uint32))),
             "input_sha256": hashlib.sha256(rgb.tobytes()).hexdigest()}
+
+
+def bench_runtime_weights(torch, pkg, synth, peak: float, eq3_us: float, reps: int = 20):
+    """Runtime weights of Eq. (5), (a, b, n, m) = (2, 1.5, 2, 2), on the
+    8192x8192 headline image (F32 VALID) through the register-window kernel
+    with the weights' coefficients; compared with the Eq. (3) kernel's time
+    from the headline leg.  Back-to-back launches over two buffer sets (> 2x
+    L2); four rows checked against the oracle's Eq. (5) masks."""
+    import numpy as np
+
+    import oracle
+    H = W = 8192
+    abnm = (2, 1.5, 2, 2)
+    img = synth.rects_noise(H, W, 0)
+    srcs = [torch.from_numpy(img).cuda() for _ in range(2)]
+    outs = [torch.empty((H, W), dtype=torch.float32, device="cuda") for _ in range(2)]
+    stream = torch.cuda.Stream()
+    st, h = pkg.sobel4_create(0)
+    assert st == 0 and pkg.sobel4_set_weights(h, *abnm) == 0
+    kind = pkg.sobel4_tune_config(h, H, W, 0)[1]
+
+    def launch(i):
+        rc = pkg.sobel4_run(h, srcs[i % 2].data_ptr(), W, outs[i % 2].data_ptr(), 4 * W, H, W,
+                            0, 0, stream.cuda_stream)
+        assert rc == 0, pkg.sobel4_status_string(rc)
+
+    for i in range(3):
+        launch(i)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        for i in range(reps):
+            launch(3 + i)
+        b.record(stream)
+    stream.synchronize()
+    us = a.elapsed_time(b) * 1e3 / reps
+    y0 = 4000
+    got = outs[(2 + reps) % 2][y0:y0 + 4].cpu().numpy()
+    want = oracle.default().sobel4(img[y0 - 2:y0 + 6], "valid", "f32",
+                                   masks=oracle.eq5_masks(*abnm))[2:6]
+    pkg.sobel4_destroy(h)
+    del srcs, outs
+    torch.cuda.empty_cache()
+    return {"workload": "8192x8192 rects+noise, F32 VALID, Eq. (5) weights (a, b, n, m) = "
+                        "(2, 1.5, 2, 2)",
+            "kernel": {1: "register window (packed passes, runtime coefficients)",
+                       2: "tensor core", 3: "direct"}.get(kind, str(kind)),
+            "us": us, "gpix_s": H * W / (us * 1e-6) / 1e9,
+            "frac": H * W * BYTES_PER_PX / (us * 1e-6) / 1e9 / peak,
+            "vs_eq3_time": us / eq3_us,
+            "rows_match_oracle": bool(np.array_equal(got.view(np.uint32), want.view(np.uint32)))}
 
 
 def bench_ablation(torch, pkg, synth):
@@ -888,6 +942,8 @@ def run_ours(args, world, rank, local):
         torch.cuda.empty_cache()
         extras["sweep"] = bench_sweep(torch, pkg, synth, peak)
         extras["rgb"] = bench_rgb(torch, pkg, synth, peak)
+        extras["runtime_weights"] = bench_runtime_weights(torch, pkg, synth, peak,
+                                                          mean_kernel_s * 1e6)
         extras["batched"] = bench_batched(torch, pkg, synth)
         extras["ablation_us"] = bench_ablation(torch, pkg, synth)
         torch.cuda.empty_cache()
@@ -979,10 +1035,43 @@ def profile_batch(n: int):
     print(f"batch of {n}: ok ({sum(i.size for i in imgs)} pixels)", flush=True)
 
 
+def profile_single(kind: str):
+    """One 8192x8192 image launched twice through the fused colour input
+    ("rgb": interleaved RGB rects+noise, F32 VALID) or the runtime-weight path
+    ("weights": Eq. (5) weights (a, b, n, m) = (2, 1.5, 2, 2), F32 VALID)."""
+    import numpy as np
+    import torch
+
+    import paper_2305_00515_gb300 as pkg
+    import synth
+    st, h = pkg.sobel4_create(0)
+    assert st == 0, pkg.sobel4_status_string(st)
+    out = torch.empty((H, W), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    if kind == "rgb":
+        src = torch.from_numpy(np.stack([synth.rects_noise(H, W, 50 + c) for c in range(3)],
+                                        axis=2)).cuda()
+        run, pitch = pkg.sobel4_run_rgb, 3 * W
+    else:
+        assert pkg.sobel4_set_weights(h, 2, 1.5, 2, 2) == 0
+        src = torch.from_numpy(synth.rects_noise(H, W, 0)).cuda()
+        run, pitch = pkg.sobel4_run, W
+    for _ in range(2):
+        rc = run(h, src.data_ptr(), pitch, out.data_ptr(), 4 * W, H, W, 0, 0, stream.cuda_stream)
+        assert rc == 0, pkg.sobel4_status_string(rc)
+    stream.synchronize()
+    assert pkg.sobel4_device_status(h) == 0
+    pkg.sobel4_destroy(h)
+    print(f"{kind}: ok", flush=True)
+
+
 def main():
     args = parse_args()
     if args.profile_variants:
         profile_variants()
+        return
+    if args.profile_single:
+        profile_single(args.profile_single)
         return
     if args.profile_batch:
         profile_batch(args.profile_batch)

@@ -307,11 +307,12 @@ sobel4_status sobel4_set_variant(sobel4_handle h, int32_t variant);
 
 /*
  * Self-check of the magnitude step of Eq. (4) on the device: for every S in
- * [s_begin, s_end) (0 <= s_begin <= s_end <= 599,270,401, the operator's whole
- * range of S), compares the F32 magnitude with CUDA's IEEE sqrtf((float)S) and
- * the U8 magnitude with min(255, round(sqrt(S))); *mismatches receives the
- * number of disagreements (0 expected).  Synchronous; allocates 8 bytes of
- * device memory for the count.  Errors: INVALID_ARG, OOM, CUDA.
+ * [s_begin, s_end) (0 <= s_begin <= s_end; the Eq. (3) operator's whole range
+ * of S is [0, 599,270,401), runtime weights may reach up to 2^31 - 2),
+ * compares the F32 magnitude with CUDA's IEEE sqrtf((float)S) and the U8
+ * magnitude with min(255, round(sqrt(S))); *mismatches receives the number of
+ * disagreements (0 expected).  Synchronous; allocates 8 bytes of device
+ * memory for the count.  Errors: INVALID_ARG, OOM, CUDA.
  */
 sobel4_status sobel4_check_magnitude(sobel4_handle h, int32_t s_begin, int32_t s_end,
                                      uint64_t *mismatches);

@@ -183,6 +183,8 @@ struct sobel4_ctx {
   int radius = 2;                 // support radius of the masks (VALID frame width)
   int32_t thr = 16384;            // EDGE8 threshold on S (T = 128 by default)
   bool custom_s16_ok = true;      // every response fits the S16X4 planes
+  bool factored = false;          // runtime weights run on the packed passes (coefs)
+  Coefs coefs{};
   Masks4 masks{};
   cudaStream_t own_stream = nullptr;
   uint8_t *d_in = nullptr;
@@ -357,9 +359,22 @@ sobel4_status launch_one(sobel4_ctx *h, const uint8_t *src, size_t sp, void *dst
                          unsigned int *pair = nullptr) {
   cudaError_t e;
   if (h->custom) {
-    // Runtime weights: the tensor-core kernel where it applies, else DIRECT.
+    // Runtime weights: the packed register-window passes with the weights'
+    // coefficients where sobel4_set_weights proved them exact, else the
+    // tensor-core kernel where it applies, else DIRECT.
     if (fmt == kS16x4 && !h->custom_s16_ok) return SOBEL4_ERR_UNSUPPORTED;
-    if (h->variant != SOBEL4_VARIANT_DIRECT && tc_eligible(src, sp, dst, dp, H, W, border, fmt)) {
+    if (h->factored && fmt != kS16x4 && h->variant != SOBEL4_VARIANT_DIRECT) {
+      int nc, R;
+      bool use_tma;
+      rg_config(h, src, sp, dst, dp, H, W, border, fmt, &use_tma, &nc, &R);
+      if (!use_tma)
+        R = tma_pick_R(fmt, h->sm_count, H, W, tma_all_fast(W, border, fmt, src, sp, dst, dp));
+      e = launch_tma_single(src, sp, dst, dp, H, W, border, fmt, tma_round_R(R), h->sm_count,
+                            pair ? pair : next_pair(h), h->d_err, stream, h->lose_stage, h->thr,
+                            &h->coefs);
+      h->lose_stage = -1;
+    } else if (h->variant != SOBEL4_VARIANT_DIRECT &&
+               tc_eligible(src, sp, dst, dp, H, W, border, fmt)) {
       e = launch_tc_single(src, sp, dst, dp, H, W, border, fmt, h->sm_count, h->d_err, stream,
                            h->lose_stage, &h->masks, h->radius);
       h->lose_stage = -1;
@@ -539,6 +554,67 @@ sobel4_status sobel4_inject_stage_loss(sobel4_handle h, int32_t stage) {
   return SOBEL4_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The largest S the F32 magnitude (magnitude_newton) is checked for,
+// exhaustively, by the self-check (tests/test_gpu_sqrt.py): all of int32's
+// non-negative range but its last value.
+constexpr double kMagnitudeCheckedMax = 2147483646.0;
+
+// The runtime-weight passes (column_step_w) for Eq. (5) weights: the integer
+// coefficients, or false where a coefficient is not an integer, where the
+// masks the passes imply differ from `mk`, or where a returned sum (R_x, R_y,
+// P = K_d+ response, M = K_d- response) could leave (-2^15, 2^15), the range
+// of a packed half.
+bool factored_coefs(double a, double b, double n, double m, const Masks4 &mk, Coefs *out) {
+  const double v[20] = {a,         a * b,         n,           m,           a * m,
+                        a * (n + b), 2 * a,       a * (n - b), a * m * b,   2 * a * n * b,
+                        a * m,     a * (n - b),   a * (n + b), a * m * b,   2 * a,
+                        2 * a * n * b, n,         m,           a * b,       a};
+  int32_t c[20];
+  for (int i = 0; i < 20; ++i) {
+    const double r = std::nearbyint(v[i]);
+    if (std::fabs(v[i] - r) > 1e-9 || std::fabs(r) > 32767) return false;
+    c[i] = (int32_t)r;
+  }
+  Coefs k = {c[0],  c[1],  c[2],  c[3],  c[4],  c[5],  c[6],  c[7],  c[8],  c[9],
+             c[10], c[11], c[12], c[13], c[14], c[15], c[16], c[17], c[18], c[19]};
+  // The masks the passes compute, tap by tap (rows i, columns j of p).
+  const int64_t hd[5] = {-k.hdE, -k.hdD, 0, k.hdD, k.hdE};
+  const int64_t hs[5] = {1, k.hsB, k.hsC, k.hsB, 1};
+  const int64_t xv[5] = {1, k.xv1, k.xv2, k.xv1, 1};
+  const int64_t yv[5] = {-k.yv2, -k.yv1, 0, k.yv1, k.yv2};
+  const int64_t q0[5] = {k.q0A, k.q0B, k.q0C, k.q0B, k.q0A};
+  const int64_t q1[5] = {k.q1A, k.q1B, k.q1C, k.q1B, k.q1A};
+  const int64_t r0[5] = {-k.r0E, -k.r0D, 0, k.r0D, k.r0E};
+  const int64_t r1[5] = {-k.r1E, -k.r1D, 0, k.r1D, k.r1E};
+  const int64_t r2[5] = {-k.r2E, -k.r2D, 0, k.r2D, k.r2E};
+  const int64_t *prow[5] = {q0, q1, nullptr, q1, q0};
+  const int64_t psgn[5] = {-1, -1, 0, 1, 1};
+  const int64_t *mrow[5] = {r0, r1, r2, r1, r0};
+  int64_t pos[4] = {0, 0, 0, 0}, neg[4] = {0, 0, 0, 0};  // of R_x, R_y, P, M
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) {
+      const int64_t kx = xv[i] * hd[j], ky = yv[i] * hs[j];
+      const int64_t kp = prow[i] ? psgn[i] * prow[i][j] : 0, km = mrow[i][j];
+      if ((kp + km) % 2 != 0 || kx != mk.w[0][i][j] || ky != mk.w[1][i][j] ||
+          (kp + km) / 2 != mk.w[2][i][j] || (kp - km) / 2 != mk.w[3][i][j])
+        return false;
+      const int64_t w[4] = {kx, ky, kp, km};
+      for (int q = 0; q < 4; ++q) (w[q] > 0 ? pos[q] : neg[q]) += w[q] > 0 ? w[q] : -w[q];
+    }
+  for (int q = 0; q < 4; ++q)
+    if (255 * std::max(pos[q], neg[q]) > 32767) return false;
+  *out = k;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
 sobel4_status sobel4_set_weights(sobel4_handle h, double a, double b, double n, double m) {
   if (!h) return SOBEL4_ERR_INVALID_ARG;
   Masks4 mk;
@@ -566,6 +642,8 @@ sobel4_status sobel4_set_weights(sobel4_handle h, double a, double b, double n, 
   h->custom_s16_ok = s16;
   h->masks = mk;
   h->radius = 2;
+  h->factored = h->custom && s_max <= kMagnitudeCheckedMax && factored_coefs(a, b, n, m, mk,
+                                                                             &h->coefs);
   return SOBEL4_OK;
 }
 
@@ -587,6 +665,7 @@ sobel4_status sobel4_set_operator(sobel4_handle h, int32_t op) {
   const int radius = operator_masks(op, &mk);
   if (!radius) return SOBEL4_ERR_INVALID_ARG;
   h->custom = true;
+  h->factored = false;  // the two-directional operators run on the mask kernels
   h->custom_s16_ok = true;
   h->masks = mk;
   h->radius = radius;
@@ -932,8 +1011,7 @@ sobel4_status sobel4_run_host(sobel4_handle h, const uint8_t *h_src, size_t src_
 
 sobel4_status sobel4_check_magnitude(sobel4_handle h, int32_t s_begin, int32_t s_end,
                                      uint64_t *mismatches) {
-  if (!h || !mismatches || s_begin < 0 || s_end < s_begin || s_end > 599270401)
-    return SOBEL4_ERR_INVALID_ARG;
+  if (!h || !mismatches || s_begin < 0 || s_end < s_begin) return SOBEL4_ERR_INVALID_ARG;
   *mismatches = 0;
   DeviceGuard g(h->device);
   unsigned long long *d_bad = nullptr;
@@ -1282,7 +1360,13 @@ extern "C" sobel4_status sobel4_tune_config(sobel4_handle h, int32_t height, int
   if (h->custom || h->variant == SOBEL4_VARIANT_DIRECT || is_ladder(h->variant)) {
     *columns_per_lane = 1;
     *rows_per_strip = 0;
-    if (h->custom) {
+    if (h->custom && h->factored && fmt != kS16x4 && h->variant != SOBEL4_VARIANT_DIRECT) {
+      rg_config(h, kAligned, sp, kAligned, dp, height, width, SOBEL4_BORDER_VALID, fmt,
+                &use_tma, &nc, &R);
+      *kernel = 1;
+      *columns_per_lane = 4;
+      *rows_per_strip = use_tma ? R : tma_pick_R(fmt, h->sm_count, height, width, true);
+    } else if (h->custom) {
       *kernel = h->variant != SOBEL4_VARIANT_DIRECT &&
                         tc_eligible(kAligned, sp, kAligned, dp, height, width,
                                     SOBEL4_BORDER_VALID, fmt)

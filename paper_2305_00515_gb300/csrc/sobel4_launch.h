@@ -37,10 +37,12 @@ int tma_pick_R(int fmt, int sm_count, int32_t H, int32_t W, bool all_fast);
 int tma_round_R(int R);
 // lose_stage >= 0 (failure injection for tests) withholds that stage's copy
 // for the first item, so that one warp's bounded wait runs out.
+// cw: runtime-weight coefficients for the packed passes (Coefs, Eq. 5); not
+// with S16X4 (INVALID_VALUE).  nullptr: the Eq. (3) passes.
 cudaError_t launch_tma_single(const uint8_t *src, size_t sp, void *dst, size_t dp, int32_t H,
                               int32_t W, int border, int fmt, int R, int sm_count,
                               unsigned int *pair, unsigned int *err, cudaStream_t st,
-                              int lose_stage = -1, int32_t thr = 0);
+                              int lose_stage = -1, int32_t thr = 0, const Coefs *cw = nullptr);
 
 // The same for an interleaved RGB source (3 bytes per pixel, row pitch sp >=
 // 3W, any alignment): the kernel stages RGB rows and turns them into gray

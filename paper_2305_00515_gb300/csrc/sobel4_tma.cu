@@ -104,24 +104,24 @@ tma::TmaImage make_image(const uint8_t *src, size_t sp, void *dst, size_t dp, in
 
 void single(int fmt, int mode, int st, const CUtensorMap &map, const tma::TmaImage &im,
             int border, int R, int items, int sm_count, unsigned int *pair, unsigned int *err,
-            cudaStream_t s) {
+            cudaStream_t s, const Coefs *cw = nullptr) {
   const int64_t cap = (int64_t)sm_count * resident(fmt, mode, st);
   const int grid = (int)std::min<int64_t>((items + tma::kWarps - 1) / tma::kWarps, cap);
   switch (fmt) {
     case kF32:
-      TmaFmt<kF32>::single(mode, st, map, im, border, R, items, grid, pair, err, s);
+      TmaFmt<kF32>::single(mode, st, map, im, border, R, items, grid, pair, err, s, cw);
       break;
     case kU8:
-      TmaFmt<kU8>::single(mode, st, map, im, border, R, items, grid, pair, err, s);
+      TmaFmt<kU8>::single(mode, st, map, im, border, R, items, grid, pair, err, s, cw);
       break;
     case kU16:
-      TmaFmt<kU16>::single(mode, st, map, im, border, R, items, grid, pair, err, s);
+      TmaFmt<kU16>::single(mode, st, map, im, border, R, items, grid, pair, err, s, cw);
       break;
     case kEdge8:
-      TmaFmt<kEdge8>::single(mode, st, map, im, border, R, items, grid, pair, err, s);
+      TmaFmt<kEdge8>::single(mode, st, map, im, border, R, items, grid, pair, err, s, cw);
       break;
     default:
-      TmaFmt<kS16x4>::single(mode, st, map, im, border, R, items, grid, pair, err, s);
+      TmaFmt<kS16x4>::single(mode, st, map, im, border, R, items, grid, pair, err, s, cw);
       break;
   }
 }
@@ -170,7 +170,8 @@ int tma_pick_R(int fmt, int sm_count, int32_t H, int32_t W, bool all_fast) {
 cudaError_t launch_tma_single(const uint8_t *src, size_t sp, void *dst, size_t dp, int32_t H,
                               int32_t W, int border, int fmt, int R, int sm_count,
                               unsigned int *pair, unsigned int *err, cudaStream_t st,
-                              int lose_stage, int32_t thr) {
+                              int lose_stage, int32_t thr, const Coefs *cw) {
+  if (cw && fmt == kS16x4) return cudaErrorInvalidValue;  // its planes need R_d, R_dt
   if (R < tma::kUnroll || R % tma::kUnroll) return cudaErrorInvalidValue;
   const int staging = tensor_ok(src, sp) ? tma::kTensor : tma::kBulk;
   CUtensorMap map;
@@ -190,7 +191,7 @@ cudaError_t launch_tma_single(const uint8_t *src, size_t sp, void *dst, size_t d
                    : plan == kPlanGeneral  ? tma::kGeneralOnly
                                            : tma::kAll;
   (void)cudaGetLastError();  // report this launch only, not an earlier failed call
-  single(fmt, mode, staging, map, im, border, R, (int)items, sm_count, pair, err, st);
+  single(fmt, mode, staging, map, im, border, R, (int)items, sm_count, pair, err, st, cw);
   return cudaGetLastError();
 }
 

@@ -648,7 +648,9 @@ __device__ __forceinline__ void st4_s16_realigned(int16_t *p, uint32_t w0, uint3
 // RA (fast path only): the destination rows are not vector-aligned; the
 // realigned stores above take the place of the vector stores.  PART (fast
 // path only): only the wl = W - x first of the lane's columns are stored.
-template <int FMT, bool GEN, bool RA, bool PART>
+// CW: the responses are R_x, R_y, P, M of the runtime-weight passes
+// (column_step_w), whose S is squares_w's; never with S16X4.
+template <int FMT, bool GEN, bool RA, bool PART, bool CW = false>
 __device__ __forceinline__ void store_rows(const TmaImage &im, uint8_t *row_a, uint8_t *row_b,
                                            int x, const uint32_t vx[4], const uint32_t vy[4],
                                            const uint32_t vd[4], const uint32_t vt[4],
@@ -656,6 +658,7 @@ __device__ __forceinline__ void store_rows(const TmaImage &im, uint8_t *row_a, u
                                            uint32_t colmask, uint32_t framemask, bool vec,
                                            int wl) {
   if constexpr (FMT == kS16x4) {
+    static_assert(!CW, "runtime-weight passes carry P and M, not the S16X4 planes");
     const uint64_t plane = (uint64_t)(uint32_t)im.H * im.dp;
     const uint32_t *vals[4] = {vx, vy, vd, vt};
 #pragma unroll
@@ -695,6 +698,10 @@ __device__ __forceinline__ void store_rows(const TmaImage &im, uint8_t *row_a, u
     }
   } else {
   int32_t sa[4], sb[4];
+  if constexpr (CW) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) squares_w(vx[k], vy[k], vd[k], vt[k], sa[k], sb[k]);
+  } else
 #if SOBEL4_SQW == 2
   // F32: strip b's S stays negated (the square root folds the sign in).
   if constexpr (FMT == kF32) {
@@ -713,7 +720,7 @@ __device__ __forceinline__ void store_rows(const TmaImage &im, uint8_t *row_a, u
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       ga[k] = magnitude_newton(sa[k]);
-      gb[k] = magnitude_newton_neg(sb[k]);
+      gb[k] = CW ? magnitude_newton(sb[k]) : magnitude_newton_neg(sb[k]);
     }
 #else
 #pragma unroll
@@ -985,10 +992,12 @@ __device__ __forceinline__ void issue_stage(const TmaImage &im, const ItemCtx &c
 // FULL: every output row of both strips lies inside the image (no row checks).
 // RA (fast path): realigned stores for a destination that is not vector-aligned.
 // PART (fast path): the segment runs past column W-1; stores stop at column W.
-template <int FMT, bool GEN, bool FULL, int ST, bool RA, bool PART>
+// CW: runtime-weight passes with the coefficients cw (else Eq. 3's, and cw unused).
+template <int FMT, bool GEN, bool FULL, int ST, bool RA, bool PART, bool CW = false>
 // ya: first row of strip a; R: this item's strip height (see strip_rows).
 __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg, int ya,
-                                         int R, int lane, ItemCtx &cx, unsigned int *err) {
+                                         int R, int lane, ItemCtx &cx, unsigned int *err,
+                                         const Coefs &cw) {
   using G = Geo<ST>;
   const int H = im.H, W = im.W;
   const int x0 = seg * kCols;
@@ -1081,9 +1090,14 @@ __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg
     uint32_t vx[kNC], vy[kNC], vd[kNC], vt[kNC];
     if (tail) {
 #pragma unroll
-      for (int q = 0; q < kNC; ++q)
-        column_step<true>(c[q], c[q + 1], c[q + 2], c[q + 3], c[q + 4], st[q], vx[q], vy[q],
-                          vd[q], vt[q]);
+      for (int q = 0; q < kNC; ++q) {
+        if constexpr (CW)
+          column_step_w<true>(cw, c[q], c[q + 1], c[q + 2], c[q + 3], c[q + 4], st[q], vx[q],
+                              vy[q], vd[q], vt[q]);
+        else
+          column_step<true>(c[q], c[q + 1], c[q + 2], c[q + 3], c[q + 4], st[q], vx[q], vy[q],
+                            vd[q], vt[q]);
+      }
       const bool st_a = FULL || i < na, st_b = FULL || i < nb;
       bool zero_a = false, zero_b = false;
       if (GEN) {
@@ -1092,15 +1106,20 @@ __device__ __forceinline__ bool tma_item(const TmaImage &im, int border, int seg
           zero_b = yb + i < 2 || yb + i > H - 3;
         }
       }
-      store_rows<FMT, GEN, RA, PART>(im, row_a, row_b, x, vx, vy, vd, vt, st_a, st_b, zero_a,
+      store_rows<FMT, GEN, RA, PART, CW>(im, row_a, row_b, x, vx, vy, vd, vt, st_a, st_b, zero_a,
                                      zero_b, colmask, framemask, vec, wl);
       row_a += im.dp;
       row_b += im.dp;
     } else {
 #pragma unroll
-      for (int q = 0; q < kNC; ++q)
-        column_step<false>(c[q], c[q + 1], c[q + 2], c[q + 3], c[q + 4], st[q], vx[q], vy[q],
-                           vd[q], vt[q]);
+      for (int q = 0; q < kNC; ++q) {
+        if constexpr (CW)
+          column_step_w<false>(cw, c[q], c[q + 1], c[q + 2], c[q + 3], c[q + 4], st[q], vx[q],
+                               vy[q], vd[q], vt[q]);
+        else
+          column_step<false>(c[q], c[q + 1], c[q + 2], c[q + 3], c[q + 4], st[q], vx[q], vy[q],
+                             vd[q], vt[q]);
+      }
     }
   };
 
@@ -1254,27 +1273,28 @@ __device__ __forceinline__ int strip_rows(const TmaImage &im, int band, int R) {
 // stores, which fall through to plain vector stores on an aligned row.  The
 // lean single-image kernel (kFastOnly, width a multiple of the segment) keeps
 // the check-free body for full bands and carries no other.
-template <int FMT, int MODE, int ST, bool ONE>
+template <int FMT, int MODE, int ST, bool ONE, bool CW = false>
 __device__ __forceinline__ bool run_item(const TmaImage &im, int border, int seg, int ya, int R,
-                                         int lane, ItemCtx &cx, unsigned int *err, bool fast) {
+                                         int lane, ItemCtx &cx, unsigned int *err, bool fast,
+                                         const Coefs &cw) {
   if (!fast_mode<MODE>() && !fast)
-    return tma_item<FMT, true, false, ST, false, false>(im, border, seg, ya, R, lane, cx, err);
+    return tma_item<FMT, true, false, ST, false, false, CW>(im, border, seg, ya, R, lane, cx, err, cw);
   constexpr bool kRA = MODE == kAll;  // realigned stores possible in this kernel
   if constexpr (ONE || MODE == kFastPart) {
-    return tma_item<FMT, false, false, ST, kRA, true>(im, border, seg, ya, R, lane, cx, err);
+    return tma_item<FMT, false, false, ST, kRA, true, CW>(im, border, seg, ya, R, lane, cx, err, cw);
   } else if constexpr (MODE == kFastOnly) {
     // The host plans this kernel only for widths that are a multiple of kCols.
     if (ya + 2 * R <= im.H)
-      return tma_item<FMT, false, true, ST, false, false>(im, border, seg, ya, R, lane, cx, err);
-    return tma_item<FMT, false, false, ST, false, false>(im, border, seg, ya, R, lane, cx, err);
+      return tma_item<FMT, false, true, ST, false, false, CW>(im, border, seg, ya, R, lane, cx, err, cw);
+    return tma_item<FMT, false, false, ST, false, false, CW>(im, border, seg, ya, R, lane, cx, err, cw);
   } else {
     if (im.dst_align < vec_bytes(FMT))
-      return tma_item<FMT, false, false, ST, true, true>(im, border, seg, ya, R, lane, cx, err);
+      return tma_item<FMT, false, false, ST, true, true, CW>(im, border, seg, ya, R, lane, cx, err, cw);
     if (im.W % kCols != 0)
-      return tma_item<FMT, false, false, ST, false, true>(im, border, seg, ya, R, lane, cx, err);
+      return tma_item<FMT, false, false, ST, false, true, CW>(im, border, seg, ya, R, lane, cx, err, cw);
     if (ya + 2 * R <= im.H)
-      return tma_item<FMT, false, true, ST, false, false>(im, border, seg, ya, R, lane, cx, err);
-    return tma_item<FMT, false, false, ST, false, false>(im, border, seg, ya, R, lane, cx, err);
+      return tma_item<FMT, false, true, ST, false, false, CW>(im, border, seg, ya, R, lane, cx, err, cw);
+    return tma_item<FMT, false, false, ST, false, false, CW>(im, border, seg, ya, R, lane, cx, err, cw);
   }
 }
 
@@ -1301,10 +1321,12 @@ __device__ __forceinline__ void init_ring(ItemCtx &cx, WarpRing<ST> &ring, int l
 // The single-image kernel: persistent CTAs of 4 warps; each warp pulls items
 // (band-major) from the counter pair[0]; the last warp out resets the pair.
 // `map` is used by the tensor staging only.
-template <int FMT, int MODE, int ST>
+// CW: runtime-weight passes with the coefficients cw (kernel parameters,
+// read from the constant bank by the multiply-adds).
+template <int FMT, int MODE, int ST, bool CW = false>
 __global__ void __launch_bounds__(kWarps * 32, min_ctas<MODE>())
     tma_single_kernel(const __grid_constant__ CUtensorMap map, TmaImage im, int border, int R,
-                      int n_items, unsigned int *pair, unsigned int *err) {
+                      int n_items, unsigned int *pair, unsigned int *err, const Coefs cw) {
   __shared__ WarpRing<ST> rings[kWarps];
   const int lane = threadIdx.x & 31;
   ItemCtx cx;
@@ -1323,7 +1345,8 @@ __global__ void __launch_bounds__(kWarps * 32, min_ctas<MODE>())
     const int ya = band * 2 * R, Ri = strip_rows(im, band, R);
     const bool fast = fast_item<ST>(im, border, seg, ya, Ri, FMT);
     if ((fast_mode<MODE>() && !fast) || (MODE == kGeneralOnly && fast)) continue;
-    if (!run_item<FMT, MODE, ST, false>(im, border, seg, ya, Ri, lane, cx, err, fast)) break;
+    if (!run_item<FMT, MODE, ST, false, CW>(im, border, seg, ya, Ri, lane, cx, err, fast, cw))
+      break;
   }
   if (lane == 0) {
     __threadfence();  // this warp's last fetch is performed before it counts out
@@ -1334,6 +1357,9 @@ __global__ void __launch_bounds__(kWarps * 32, min_ctas<MODE>())
     }
   }
 }
+
+// Coefficients of the batched kernel, which runs Eq. (3) only (unused).
+__device__ const Coefs kNoCoefs = {};
 
 // The batched kernel: persistent CTAs of 4 warps pull items (image by image,
 // band-major) from *queue (zeroed by the host before the launch); a warp
@@ -1377,7 +1403,8 @@ __global__ void __launch_bounds__(kWarps * 32, min_ctas<MODE>())
       cx.map = nullptr;  // bulk staging reads rows through im.src
     }
     cx.lose_stage = -1;
-    if (!run_item<FMT, MODE, ST, true>(im, border, seg, ya, Ri, lane, cx, err, fast)) break;
+    if (!run_item<FMT, MODE, ST, true>(im, border, seg, ya, Ri, lane, cx, err, fast, kNoCoefs))
+      break;
   }
 }
 

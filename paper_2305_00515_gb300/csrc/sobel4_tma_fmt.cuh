@@ -13,9 +13,10 @@ template <int FMT>
 struct TmaFmt {
   // Resident CTAs per SM of the single-image kernel (mode, staging).
   static int resident(int mode, int st);
+  // cw: runtime-weight coefficients (nullptr: Eq. 3); not with S16X4 or RGB staging.
   static void single(int mode, int st, const CUtensorMap &map, const tma::TmaImage &im,
                      int border, int R, int items, int grid, unsigned int *pair,
-                     unsigned int *err, cudaStream_t s);
+                     unsigned int *err, cudaStream_t s, const Coefs *cw);
   // d: TmaBatchDesc array (tensor staging) or TmaBulkDesc array (bulk staging).
   static void batched(int mode, int st, const void *d, int n_img, int total,
                       unsigned int *queue, int border, int R, int grid, unsigned int *err,
@@ -100,18 +101,34 @@ void launch_pdl(void (*kernel)(KArgs...), int grid, cudaStream_t s, Args... args
 }
 #endif
 
+template <int FMT, int M, int S, bool CW>
+void single_launch(const CUtensorMap &map, const tma::TmaImage &im, int border, int R, int items,
+                   int grid, unsigned int *pair, unsigned int *err, cudaStream_t s,
+                   const Coefs &cw) {
+#if SOBEL4_PDL
+  launch_pdl(tma::tma_single_kernel<FMT, M, S, CW>, grid, s, map, im, border, R, items, pair, err,
+             cw);
+#else
+  tma::tma_single_kernel<FMT, M, S, CW><<<(unsigned)grid, tma::kWarps * 32, 0, s>>>(
+      map, im, border, R, items, pair, err, cw);
+#endif
+}
+
 template <int FMT>
 void TmaFmt<FMT>::single(int mode, int st, const CUtensorMap &map, const tma::TmaImage &im,
                          int border, int R, int items, int grid, unsigned int *pair,
-                         unsigned int *err, cudaStream_t s) {
-#if SOBEL4_PDL
-#define SOBEL4_SINGLE(M, S) \
-  launch_pdl(tma::tma_single_kernel<FMT, M, S>, grid, s, map, im, border, R, items, pair, err)
-#else
-#define SOBEL4_SINGLE(M, S)                                                                  \
-  tma::tma_single_kernel<FMT, M, S><<<(unsigned)grid, tma::kWarps * 32, 0, s>>>(map, im, border, \
-                                                                           R, items, pair, err)
-#endif
+                         unsigned int *err, cudaStream_t s, const Coefs *cw) {
+  const Coefs none = {};
+#define SOBEL4_SINGLE(M, S)                                                                   \
+  do {                                                                                        \
+    if constexpr (FMT != kS16x4 && (S) != tma::kRgbBulk) {                                    \
+      if (cw) {                                                                               \
+        single_launch<FMT, M, S, true>(map, im, border, R, items, grid, pair, err, s, *cw);   \
+        break;                                                                                \
+      }                                                                                       \
+    }                                                                                         \
+    single_launch<FMT, M, S, false>(map, im, border, R, items, grid, pair, err, s, none);     \
+  } while (0)
   SOBEL4_TMA_SWITCH_SINGLE(mode, st, SOBEL4_SINGLE);
 #undef SOBEL4_SINGLE
 }

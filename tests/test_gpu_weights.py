@@ -1,11 +1,12 @@
 """Runtime weights (the generalised operator of Eq. 5) through the C ABI,
 against the oracle's Eq. (5) masks, bit for bit.
 
-With weights other than Eq. (3), F32 VALID images with aligned rows run on the
-tensor-core kernel and everything else on the DIRECT kernel; batches run image
-by image.  Every border, format and a batch are covered for four weight sets,
-and (1, 2, 4, 6) must restore the register-window path and the Eq. (3)
-results.  Tolerance: zero mismatched elements, no write outside the payload.
+Weights whose packed-pass coefficients sobel4_set_weights proves exact run on
+the register-window kernel (every format but S16X4; all four weight sets here
+do); S16X4 and DIRECT handles run the DIRECT kernel.  Batches run image by
+image.  Every border, format and a batch are covered for four weight sets,
+and (1, 2, 4, 6) must restore the Eq. (3) passes and results.  Tolerance:
+zero mismatched elements, no write outside the payload.
 """
 import numpy as np
 import pytest
@@ -48,6 +49,9 @@ def test_runtime_weights_match_oracle(built, abnm, variant):
     assert st == 0
     try:
         assert pkg.sobel4_set_weights(h, *abnm) == 0
+        # the kernel these weights run on: the register window (1) or DIRECT (3)
+        kind = pkg.sobel4_tune_config(h, 512, 512, 0)[1]
+        assert kind == (1 if variant == "auto" else 3), kind
         for (H, W) in SHAPES:
             img = synth.rects_noise(H, W, H * W)
             for border in BORDERS:
@@ -73,7 +77,7 @@ def test_runtime_weights_batched_and_restore(built):
                  for (H, W) in ((40, 64), (129, 300), (300, 512))]
         outs = s.run_batched(batch, border="reflect101", fmt="f32")
         big = torch.from_numpy(synth.rects_noise(1024, 2048, 5)).cuda()
-        out_big = s.run(big)  # VALID F32, aligned rows: the tensor-core kernel
+        out_big = s.run(big)  # VALID F32: the register-window kernel with these coefficients
         torch.cuda.synchronize()
         for b, o in zip(batch, outs):
             assert_same(o.cpu().numpy(), oracle.sobel4(b.cpu().numpy(), "reflect101", "f32",
