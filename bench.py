@@ -425,8 +425,8 @@ def bench_rgb(torch, pkg, synth, peak: float, reps: int = 20):
 def bench_runtime_weights(torch, pkg, synth, peak: float, eq3_us: float, reps: int = 20):
     """Runtime weights of Eq. (5), (a, b, n, m) = (2, 1.5, 2, 2), on the
     8192x8192 headline image (F32 VALID) through the register-window kernel
-    with the weights' coefficients; compared with the Eq. (3) kernel's time
-    from the headline leg.  Back-to-back launches over two buffer sets (> 2x
+    with the weights' coefficients (strip height autotuned like the headline
+    leg's); compared with the Eq. (3) kernel's time from the headline leg.  Back-to-back launches over two buffer sets (> 2x
     L2); four rows checked against the oracle's Eq. (5) masks."""
     import numpy as np
 
@@ -439,7 +439,9 @@ def bench_runtime_weights(torch, pkg, synth, peak: float, eq3_us: float, reps: i
     stream = torch.cuda.Stream()
     st, h = pkg.sobel4_create(0)
     assert st == 0 and pkg.sobel4_set_weights(h, *abnm) == 0
-    kind = pkg.sobel4_tune_config(h, H, W, 0)[1]
+    st, _ = pkg.sobel4_tune(h, H, W, 0, 0)  # strip height for these coefficients
+    assert st == 0, pkg.sobel4_status_string(st)
+    _, kind, _, rows = pkg.sobel4_tune_config(h, H, W, 0)
 
     def launch(i):
         rc = pkg.sobel4_run(h, srcs[i % 2].data_ptr(), W, outs[i % 2].data_ptr(), 4 * W, H, W,
@@ -467,6 +469,7 @@ def bench_runtime_weights(torch, pkg, synth, peak: float, eq3_us: float, reps: i
                         "(2, 1.5, 2, 2)",
             "kernel": {1: "register window (packed passes, runtime coefficients)",
                        2: "tensor core", 3: "direct"}.get(kind, str(kind)),
+            "autotuned_rows_per_strip": rows,
             "us": us, "gpix_s": H * W / (us * 1e-6) / 1e9,
             "frac": H * W * BYTES_PER_PX / (us * 1e-6) / 1e9 / peak,
             "vs_eq3_time": us / eq3_us,
@@ -552,8 +555,8 @@ def bench_video(torch, pkg, synth, frames: int, slots: int = 4):
     D2H per frame, `slots` frame slots).  All `frames` frames are distinct --
     frame k is the background translated by (k mod 17, 2k mod 13) with fresh
     noise keyed by k -- and are generated, untimed, into a page-locked host
-    ring before the timed loop; each submit points the slot's graph at its
-    frame.  Reported against a plain-copy ceiling of the host link; then an
+    ring (sobel4_host_alloc) before the timed loop; each submit hands the
+    slot its frame (upload, the slot's kernel graph, download).  Reported against a plain-copy ceiling of the host link; then an
     untimed pass checks every frame's output against a single-image launch on
     the same frame (bit for bit, on the device) and three frames against the
     CPU oracle."""
@@ -563,9 +566,8 @@ def bench_video(torch, pkg, synth, frames: int, slots: int = 4):
     H, W = 2160, 3840
     fb = H * W
     bg = synth.video_background(H, W, 3)
-    ring = np.empty((frames, H, W), dtype=np.uint8)
-    cudart = torch.cuda.cudart()
-    assert cudart.cudaHostRegister(ring.ctypes.data, ring.nbytes, 0) == 0
+    ring_buf = pkg.HostBuffer((frames, H, W), "uint8")  # page-locked (sobel4_host_alloc)
+    ring = ring_buf.array
     try:
         t0 = time.perf_counter()
         for k0 in range(0, frames, 64):
@@ -616,7 +618,8 @@ def bench_video(torch, pkg, synth, frames: int, slots: int = 4):
                         np.ascontiguousarray(pipe.outputs[0]).view(np.uint32), want.view(np.uint32)))
             pipe.close()
     finally:
-        cudart.cudaHostUnregister(ring.ctypes.data)
+        ring = None
+        ring_buf.close()
     fps = frames / dt
     return {"workload": f"{frames} distinct frames of 3840x2160 u8 -> f32 through {slots} graph "
                         "slots, from a page-locked host ring generated beforehand (untimed)",

@@ -361,7 +361,12 @@ sobel4_status sobel4_run_batched_static(const sobel4_image *h_images, int32_t n,
  * the handle's table under the bucket (ceil log2 height, ceil log2 width,
  * fmt).  Later sobel4_run calls whose shape falls in that bucket use it.
  * *best_us (may be NULL) receives the chosen candidate's median time in
- * microseconds.  Synchronous.  Errors: INVALID_ARG, OOM, CUDA.
+ * microseconds.  On a handle with runtime weights (sobel4_set_weights other
+ * than Eq. 3's) it times only the TMA-staged kernel with the weights'
+ * coefficients, and answers UNSUPPORTED where those weights do not run on the
+ * packed passes (S16X4, the DIRECT variant, weights outside the proven range,
+ * the two-directional operators).  Synchronous.  Errors: INVALID_ARG,
+ * UNSUPPORTED, OOM, CUDA.
  */
 sobel4_status sobel4_tune(sobel4_handle h, int32_t height, int32_t width, sobel4_border border,
                           sobel4_format fmt, float *best_us);
@@ -458,6 +463,21 @@ sobel4_status sobel4_pipeline_wait(sobel4_pipeline p, int32_t slot);
 
 /* Wait for all slots and release everything.  NULL is a no-op. */
 sobel4_status sobel4_pipeline_destroy(sobel4_pipeline p);
+
+/*
+ * Page-locked host memory (cudaHostAlloc, portable to every device) for
+ * frames and results that cross the host link, such as a ring of frames fed
+ * to sobel4_pipeline_submit_from or the buffers of server requests.  On a
+ * Grace host the copy engines stream such memory at the link rate on every
+ * pass, where pages locked after allocation (cudaHostRegister) can fall far
+ * below it once a ring is larger than the translation caches.  *out receives
+ * the buffer, `bytes` long, uninitialised (NULL on error).  Errors:
+ * INVALID_ARG (out NULL or bytes 0), OOM, CUDA.
+ */
+sobel4_status sobel4_host_alloc(size_t bytes, void **out);
+
+/* Release a buffer from sobel4_host_alloc.  NULL is a no-op.  Errors: CUDA. */
+sobel4_status sobel4_host_free(void *p);
 
 /*
  * Continuous-batching request server.  A scheduler thread admits submitted

@@ -24,7 +24,8 @@ __all__ = [
     "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched", "sobel4_tune_entries",
     "sobel4_tune_config", "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create",
     "sobel4_pipeline_buffers", "sobel4_pipeline_submit", "sobel4_pipeline_submit_from",
-    "sobel4_pipeline_wait", "sobel4_pipeline_destroy", "Pipeline",
+    "sobel4_pipeline_wait", "sobel4_pipeline_destroy", "Pipeline", "sobel4_host_alloc",
+    "sobel4_host_free", "HostBuffer",
     "sobel4_server_create", "sobel4_server_submit", "sobel4_server_wait", "sobel4_server_stats",
     "sobel4_server_destroy", "ServerOptions", "ServerStats", "EXPORTED_SYMBOLS",
 ]
@@ -48,7 +49,8 @@ EXPORTED_SYMBOLS = (
     "sobel4_run_batched_static", "sobel4_tune", "sobel4_tune_batched", "sobel4_tune_entries",
     "sobel4_tune_config", "sobel4_tune_save", "sobel4_tune_load", "sobel4_pipeline_create",
     "sobel4_pipeline_buffers", "sobel4_pipeline_submit", "sobel4_pipeline_submit_from",
-    "sobel4_pipeline_wait", "sobel4_pipeline_destroy", "sobel4_server_create", "sobel4_server_submit", "sobel4_server_wait", "sobel4_server_stats",
+    "sobel4_pipeline_wait", "sobel4_pipeline_destroy", "sobel4_host_alloc", "sobel4_host_free",
+    "sobel4_server_create", "sobel4_server_submit", "sobel4_server_wait", "sobel4_server_stats",
     "sobel4_server_destroy",
 )
 
@@ -143,6 +145,8 @@ def load() -> ctypes.CDLL:
         lib.sobel4_pipeline_submit_from.argtypes = [vp, i32, vp, vp]
         lib.sobel4_pipeline_wait.argtypes = [vp, i32]
         lib.sobel4_pipeline_destroy.argtypes = [vp]
+        lib.sobel4_host_alloc.argtypes = [sz, ctypes.POINTER(vp)]
+        lib.sobel4_host_free.argtypes = [vp]
         lib.sobel4_server_create.argtypes = [vp, ctypes.POINTER(ServerOptions), ctypes.POINTER(vp)]
         lib.sobel4_server_submit.argtypes = [vp, vp, sz, vp, sz, i32, i32,
                                              ctypes.POINTER(ctypes.c_uint64)]
@@ -320,6 +324,44 @@ def sobel4_pipeline_wait(p, slot: int) -> int:
 
 def sobel4_pipeline_destroy(p) -> int:
     return load().sobel4_pipeline_destroy(p)
+
+
+def sobel4_host_alloc(nbytes: int):
+    """(status, address) of `nbytes` of page-locked host memory."""
+    p = ctypes.c_void_p()
+    st = load().sobel4_host_alloc(nbytes, ctypes.byref(p))
+    return st, p.value or 0
+
+
+def sobel4_host_free(address: int) -> int:
+    return load().sobel4_host_free(address or None)
+
+
+class HostBuffer:
+    """Page-locked host memory from sobel4_host_alloc with a numpy view
+    (``.array``, `dtype` x `shape`); freed by close() or garbage collection."""
+
+    def __init__(self, shape, dtype="uint8"):
+        import numpy as np
+        self.shape = tuple(shape) if hasattr(shape, "__len__") else (int(shape),)
+        self.dtype = np.dtype(dtype)
+        nbytes = int(np.prod(self.shape)) * self.dtype.itemsize
+        st, self.address = sobel4_host_alloc(nbytes)
+        _check(st, "sobel4_host_alloc")
+        raw = (ctypes.c_uint8 * nbytes).from_address(self.address)
+        self.array = np.frombuffer(raw, dtype=self.dtype).reshape(self.shape)
+
+    def close(self):
+        if self.address:
+            self.array = None
+            _check(sobel4_host_free(self.address), "sobel4_host_free")
+            self.address = 0
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Pipeline:

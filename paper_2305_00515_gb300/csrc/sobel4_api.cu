@@ -580,7 +580,8 @@ bool factored_coefs(double a, double b, double n, double m, const Masks4 &mk, Co
     c[i] = (int32_t)r;
   }
   Coefs k = {c[0],  c[1],  c[2],  c[3],  c[4],  c[5],  c[6],  c[7],  c[8],  c[9],
-             c[10], c[11], c[12], c[13], c[14], c[15], c[16], c[17], c[18], c[19]};
+             c[10], c[11], c[12], c[13], c[14], c[15], c[16], c[17], c[18], c[19],
+             -c[18], -c[19]};
   // The masks the passes compute, tap by tap (rows i, columns j of p).
   const int64_t hd[5] = {-k.hdE, -k.hdD, 0, k.hdD, k.hdE};
   const int64_t hs[5] = {1, k.hsB, k.hsC, k.hsB, 1};
@@ -670,6 +671,27 @@ sobel4_status sobel4_set_operator(sobel4_handle h, int32_t op) {
   h->masks = mk;
   h->radius = radius;
   return SOBEL4_OK;
+}
+
+sobel4_status sobel4_host_alloc(size_t bytes, void **out) {
+  if (!out) return SOBEL4_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!bytes) return SOBEL4_ERR_INVALID_ARG;
+  void *p = nullptr;
+  const cudaError_t e = cudaHostAlloc(&p, bytes, cudaHostAllocPortable);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? SOBEL4_ERR_OOM : SOBEL4_ERR_CUDA;
+  }
+  *out = p;
+  return SOBEL4_OK;
+}
+
+sobel4_status sobel4_host_free(void *p) {
+  if (!p) return SOBEL4_OK;
+  const cudaError_t e = cudaFreeHost(p);
+  if (e != cudaSuccess) (void)cudaGetLastError();
+  return e == cudaSuccess ? SOBEL4_OK : SOBEL4_ERR_CUDA;
 }
 
 sobel4_status sobel4_device_status(sobel4_handle h) {
@@ -1202,6 +1224,13 @@ extern "C" sobel4_status sobel4_tune(sobel4_handle h, int32_t height, int32_t wi
   const size_t sp = ((size_t)width + 15) & ~(size_t)15;
   const size_t dp = ((size_t)width * elem_size(fmt) + 15) & ~(size_t)15;
   if (!valid_shape(sp, dp, height, width, border, fmt)) return SOBEL4_ERR_INVALID_ARG;
+  // Runtime weights that sobel4_set_weights proved exact on the packed passes
+  // run on the TMA-staged kernel alone (with their coefficients), so only its
+  // strip heights are timed; other runtime weights have nothing to tune.
+  const bool weights = h->custom;
+  const Coefs *cw = weights && h->factored && fmt != kS16x4 &&
+                            h->variant != SOBEL4_VARIANT_DIRECT ? &h->coefs : nullptr;
+  if (weights && !cw) return SOBEL4_ERR_UNSUPPORTED;
   DeviceGuard g(h->device);
   uint8_t *src = nullptr, *dst = nullptr;
   cudaError_t e = cudaMalloc((void **)&src, sp * (size_t)height);
@@ -1220,7 +1249,7 @@ extern "C" sobel4_status sobel4_tune(sobel4_handle h, int32_t height, int32_t wi
     }
   };
   // Tensor-core kernel (AUTO and TC handles, the images it covers).
-  if (e == cudaSuccess &&
+  if (e == cudaSuccess && !weights &&
       (h->variant == SOBEL4_VARIANT_AUTO || h->variant == SOBEL4_VARIANT_TC) && !h->nc_forced &&
       h->rows_per_strip <= 0 && tc_eligible(src, sp, dst, dp, height, width, border, fmt)) {
     float us = 0.f;
@@ -1254,14 +1283,14 @@ extern "C" sobel4_status sobel4_tune(sobel4_handle h, int32_t height, int32_t wi
       e = median_us(h->own_stream, [&]() {
         h->launches += 1;
         return launch_tma_single(src, sp, dst, dp, height, width, border, fmt, R, h->sm_count,
-                                 next_pair(h), h->d_err, h->own_stream);
+                                 next_pair(h), h->d_err, h->own_stream, -1, h->thr, cw);
       }, &us);
       if (e == cudaSuccess) consider(1, 4, R, us);
     }
   }
   const int ncs[2] = {2, 4};
   const int Rs[4] = {8, 16, 32, 64};
-  for (int a = 0; a < 2 && e == cudaSuccess && fmt != kU16 && fmt != kEdge8; ++a) {
+  for (int a = 0; a < 2 && e == cudaSuccess && fmt != kU16 && fmt != kEdge8 && !weights; ++a) {
     if (h->nc_forced && ncs[a] != h->nc) continue;
     for (int b = 0; b < 4 && e == cudaSuccess; ++b) {
       if (h->rows_per_strip > 0 && Rs[b] != h->rows_per_strip) continue;

@@ -89,6 +89,33 @@ def test_pipeline_submit_from_caller_buffers():
     assert same_bits(own, oracle.sobel4(frames[0], "valid", "f32"))
 
 
+def test_host_alloc_ring_through_the_pipeline():
+    """A frame ring and result buffers in sobel4_host_alloc memory: every
+    frame equals the oracle; the allocator rejects a zero size and frees NULL."""
+    H, W, n = 96, 256, 5  # rows at the pipeline pitches (multiples of 16 bytes)
+    bg = synth.video_background(H, W, 12)
+    frames = [synth.video_frame(bg, k, H, W, 12) for k in range(n)]
+    ring = pkg.HostBuffer((n, H, W), "uint8")
+    outs = pkg.HostBuffer((n, H, W), "float32")
+    try:
+        ring.array[:] = np.stack(frames)
+        with pkg.Sobel4(0) as s:
+            pipe = pkg.Pipeline(s, H, W, "replicate", "f32", slots=3)
+            for k in range(n):
+                pipe.wait(k % 3)
+                pipe.submit_from(k % 3, ring.address + k * H * W, outs.address + k * H * W * 4)
+            for slot in range(3):
+                pipe.wait(slot)
+            pipe.close()
+        for k in range(n):
+            assert same_bits(outs.array[k], oracle.sobel4(frames[k], "replicate", "f32")), k
+    finally:
+        ring.close()
+        outs.close()
+    assert pkg.sobel4_host_alloc(0)[0] == 1
+    assert pkg.sobel4_host_free(0) == 0
+
+
 def test_pipeline_4k_frames():
     """3840x2160 frames, the video configuration's size, through the pipeline."""
     H, W = 2160, 3840

@@ -92,6 +92,40 @@ def test_runtime_weights_batched_and_restore(built):
                                                      threads=oracle.cpu_count()), "restored")
 
 
+def test_tune_with_runtime_weights(built):
+    """sobel4_tune on a runtime-weight handle times the register-window kernel
+    with the weights' coefficients; the chosen strip height then serves runs
+    in that shape bucket, still bit-equal to the oracle.  Weights that do not
+    run on the packed passes have nothing to tune (UNSUPPORTED)."""
+    abnm = (2, 1.5, 2, 2)
+    K = oracle.eq5_masks(*abnm)
+    st, h = pkg.sobel4_create(0)
+    assert st == 0
+    try:
+        assert pkg.sobel4_set_weights(h, *abnm) == 0
+        st, us = pkg.sobel4_tune(h, 1024, 2048, 0, 0)
+        assert st == 0 and us > 0
+        _, kind, _, R = pkg.sobel4_tune_config(h, 1024, 2048, 0)
+        assert kind == 1 and R > 0
+        for (H, W) in ((1024, 2048), (1000, 1999)):
+            img = synth.rects_noise(H, W, H + W)
+            got, guards = run_placed(torch, h, img, "valid", "f32")
+            assert guards
+            assert_same(got, oracle.sobel4(img, "valid", "f32", masks=K,
+                                           threads=oracle.cpu_count()), f"tuned {H}x{W}")
+        assert pkg.sobel4_tune(h, 256, 256, 0, pkg.FORMATS["s16x4"])[0] == 2
+        assert pkg.sobel4_set_operator(h, pkg.OPERATORS["2dir5x5"]) == 0
+        assert pkg.sobel4_tune(h, 256, 256, 0, 0)[0] == 2
+    finally:
+        pkg.sobel4_destroy(h)
+    st, h = pkg.sobel4_create(0, pkg.VARIANTS["direct"])
+    try:
+        assert pkg.sobel4_set_weights(h, *abnm) == 0
+        assert pkg.sobel4_tune(h, 256, 256, 0, 0)[0] == 2
+    finally:
+        pkg.sobel4_destroy(h)
+
+
 def test_runtime_weights_rejected(built):
     st, h = pkg.sobel4_create(0)
     assert st == 0
