@@ -422,8 +422,10 @@ sobel4_status sobel4_tune_load(sobel4_handle h, const char *path);
  * its IO bottleneck (Section 5.2, Section 6).  A pipeline owns `slots` (2..64)
  * frame slots for height x width frames of one border rule and format; each
  * slot has pinned host input and output buffers, device buffers, its own
- * stream and an instantiated CUDA graph of host->device copy, kernel and
- * device->host copy.  While one slot's kernel runs, other slots' copies run.
+ * stream and an instantiated CUDA graph of host->device copy and kernel; the
+ * kernel stores the result straight into the slot's pinned output (mapped
+ * page-locked memory), with no device->host copy.  While one slot's kernel
+ * runs, other slots' uploads run.
  * Usage per frame: wait(slot) (its previous frame is done and its output
  * readable), write the frame into the slot's input buffer, submit(slot).
  * Host buffers use the pitches reported by sobel4_pipeline_buffers; S16X4
@@ -447,13 +449,14 @@ sobel4_status sobel4_pipeline_submit(sobel4_pipeline p, int32_t slot);
 /*
  * One frame from caller host buffers: h_in (the frame, height rows at the
  * pipeline's input pitch) is copied to the slot's device buffer and the
- * result to h_out (the pipeline's output pitch and planes); NULL keeps the
- * slot's own buffer.  With both NULL (or the slot's own buffers) this is
- * sobel4_pipeline_submit, one graph launch; otherwise the slot's stream gets
- * the upload, a graph of the kernel alone and the download.  The buffers
- * should be pinned (cudaHostAlloc / cudaHostRegister) for the copies to run
- * asynchronously, and must stay valid until wait(slot) returns.  Errors:
- * INVALID_ARG (as submit), CUDA (sobel4_last_cuda_error has the code).
+ * result goes to h_out (the pipeline's output pitch and planes); NULL keeps
+ * the slot's own buffer.  With both NULL (or the slot's own buffers) this is
+ * sobel4_pipeline_submit, one graph launch.  Otherwise the slot's stream gets
+ * the upload and then either the kernel storing into h_out itself (h_out
+ * mapped page-locked memory, as sobel4_host_alloc gives) or a graph of the
+ * kernel alone and a download.  h_in should be page-locked for the upload to
+ * run asynchronously; both buffers must stay valid until wait(slot) returns.
+ * Errors: INVALID_ARG (as submit), CUDA (sobel4_last_cuda_error has the code).
  */
 sobel4_status sobel4_pipeline_submit_from(sobel4_pipeline p, int32_t slot, const uint8_t *h_in,
                                           void *h_out);
@@ -483,17 +486,23 @@ sobel4_status sobel4_host_free(void *p);
  * Continuous-batching request server.  A scheduler thread admits submitted
  * requests first-in first-out while a device-memory arena of
  * `memory_budget` bytes (allocated once, at creation) has room for their
- * input and output, uploads them on a copy stream, packs everything admitted
- * into one persistent batched launch (sobel4_run_batched; at most two batches
- * on the GPU at once, so requests arriving while a batch runs join the next;
- * a batch of one runs as a sobel4_run launch), and downloads results on a
- * third stream; each request completes when its own download has landed.
- * Comparison modes: plain = 1 makes each request its own sobel4_run launch
- * on the same three streams; plain = 2 runs one request at a time in arrival
- * order on ONE stream (upload, sobel4_run, download).  Host buffers
- * passed to submit must stay valid until wait returns; pinned host memory
- * keeps the copies asynchronous (pageable memory serialises them).  Every
- * result equals sobel4_run's output for that image.
+ * input (and their output where it is staged, below), uploads them on a copy
+ * stream, and packs everything admitted into one persistent batched launch
+ * (sobel4_run_batched; at most two batches on the GPU at once, so requests
+ * arriving while a batch runs join the next; a batch of up to three runs as
+ * sobel4_run launches).  A result buffer that is mapped page-locked host memory
+ * (sobel4_host_alloc, cudaHostAlloc, or cudaHostRegister where the device
+ * maps it at the same address) with pitch and address multiples of the
+ * element size is written by the kernel itself, over the host link; any
+ * other result buffer is staged in the arena and downloaded on a third
+ * stream.  A completion thread waits on one event per request in order; a
+ * request completes when its result is in host memory.  Comparison modes:
+ * plain = 1 makes each request its own sobel4_run launch on the same
+ * streams; plain = 2 runs one request at a time in arrival order on ONE
+ * stream (upload, sobel4_run, download where staged).  Host buffers passed
+ * to submit must stay valid, and the result buffer untouched, until wait
+ * returns; page-locked input keeps the uploads asynchronous (pageable memory
+ * serialises them).  Every result equals sobel4_run's output for that image.
  */
 typedef struct sobel4_server_ctx *sobel4_server;
 

@@ -206,6 +206,21 @@ void note_launches(sobel4_handle h, int64_t delta) { h->launches += (uint64_t)de
 void note_cuda_error(sobel4_handle h, cudaError_t e) {
   if (h) h->last_err = (int32_t)e;
 }
+bool host_kernel_writable(const void *p, size_t pitch, size_t rows, size_t row_bytes,
+                          size_t elem) {
+  if (!p || !rows || !row_bytes || (uintptr_t)p % elem || pitch % elem || pitch > kMaxPitch)
+    return false;
+  const char *ends[2] = {(const char *)p, (const char *)p + pitch * (rows - 1) + row_bytes - 1};
+  for (const char *q : ends) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, q) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return false;
+    }
+    if (a.type != cudaMemoryTypeHost || a.devicePointer != (const void *)q) return false;
+  }
+  return true;
+}
 }  // namespace sobel4
 
 namespace {
@@ -826,7 +841,7 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
   // the handle asks for lane copies: staged by tensor copies when every
   // source is 16-byte aligned, else all by bulk row copies (which take any
   // alignment), so that a mixed batch is still one persistent launch.
-  const bool tma_ok = fmt == kU16 || fmt == kEdge8 ||
+  const bool tma_ok = (int)fmt == kU16 || (int)fmt == kEdge8 ||
                       (h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced && !bl);
   // TMA strip height: explicit option, else the tuned one, else about four
   // items per resident warp (8 .. 128 rows): taller strips spend less on the
@@ -1085,7 +1100,7 @@ extern "C" sobel4_status sobel4_run_batched_static(const sobel4_image *imgs, int
                                                    sobel4_border border, sobel4_format fmt,
                                                    cudaStream_t stream) {
   if (!imgs || n < 1 || !valid_enum(border, fmt)) return SOBEL4_ERR_INVALID_ARG;
-  if (n > kStaticMaxImages || fmt == kU16 || fmt == kEdge8)
+  if (n > kStaticMaxImages || (int)fmt == kU16 || (int)fmt == kEdge8)
     return SOBEL4_ERR_UNSUPPORTED;  // the lane-copy kernel has no such output
   const int R = kBatchR;
   int64_t total = 0;  // work items of the whole batch
@@ -1228,7 +1243,7 @@ extern "C" sobel4_status sobel4_tune(sobel4_handle h, int32_t height, int32_t wi
   // run on the TMA-staged kernel alone (with their coefficients), so only its
   // strip heights are timed; other runtime weights have nothing to tune.
   const bool weights = h->custom;
-  const Coefs *cw = weights && h->factored && fmt != kS16x4 &&
+  const Coefs *cw = weights && h->factored && (int)fmt != kS16x4 &&
                             h->variant != SOBEL4_VARIANT_DIRECT ? &h->coefs : nullptr;
   if (weights && !cw) return SOBEL4_ERR_UNSUPPORTED;
   DeviceGuard g(h->device);
@@ -1262,7 +1277,7 @@ extern "C" sobel4_status sobel4_tune(sobel4_handle h, int32_t height, int32_t wi
   }
   // TMA-staged kernel: a few strip heights, including the one that gives every
   // resident warp about one item.
-  if ((fmt == kU16 || fmt == kEdge8 ||
+  if (((int)fmt == kU16 || (int)fmt == kEdge8 ||
        (h->variant != SOBEL4_VARIANT_RG_LANECOPY && !h->nc_forced)) &&
       tma_eligible(src, sp)) {
     std::vector<int> cands;
@@ -1290,7 +1305,7 @@ extern "C" sobel4_status sobel4_tune(sobel4_handle h, int32_t height, int32_t wi
   }
   const int ncs[2] = {2, 4};
   const int Rs[4] = {8, 16, 32, 64};
-  for (int a = 0; a < 2 && e == cudaSuccess && fmt != kU16 && fmt != kEdge8 && !weights; ++a) {
+  for (int a = 0; a < 2 && e == cudaSuccess && (int)fmt != kU16 && (int)fmt != kEdge8 && !weights; ++a) {
     if (h->nc_forced && ncs[a] != h->nc) continue;
     for (int b = 0; b < 4 && e == cudaSuccess; ++b) {
       if (h->rows_per_strip > 0 && Rs[b] != h->rows_per_strip) continue;
@@ -1354,7 +1369,7 @@ extern "C" sobel4_status sobel4_tune_batched(sobel4_handle h, const sobel4_image
     }
   }
   // Lane-copy kernel: columns per lane, strip height, CTAs per SM.
-  for (int a = 0; a < 2 && st == SOBEL4_OK && fmt != kU16 && fmt != kEdge8; ++a) {
+  for (int a = 0; a < 2 && st == SOBEL4_OK && (int)fmt != kU16 && (int)fmt != kEdge8; ++a) {
     if (h->nc_forced && ncs[a] != h->nc) continue;
     for (int b = 0; b < 3 && st == SOBEL4_OK; ++b) {
       if (h->rows_per_strip > 0 && Rs[b] != h->rows_per_strip) continue;
@@ -1389,7 +1404,7 @@ extern "C" sobel4_status sobel4_tune_config(sobel4_handle h, int32_t height, int
   if (h->custom || h->variant == SOBEL4_VARIANT_DIRECT || is_ladder(h->variant)) {
     *columns_per_lane = 1;
     *rows_per_strip = 0;
-    if (h->custom && h->factored && fmt != kS16x4 && h->variant != SOBEL4_VARIANT_DIRECT) {
+    if (h->custom && h->factored && (int)fmt != kS16x4 && h->variant != SOBEL4_VARIANT_DIRECT) {
       rg_config(h, kAligned, sp, kAligned, dp, height, width, SOBEL4_BORDER_VALID, fmt,
                 &use_tma, &nc, &R);
       *kernel = 1;

@@ -139,6 +139,14 @@ __attribute__((visibility("hidden"))) sobel4_status run_with_pair(
     sobel4_handle h, const uint8_t *d_src, size_t src_pitch, void *d_dst, size_t dst_pitch,
     int32_t height, int32_t width, int border, int fmt, cudaStream_t stream, unsigned int *pair);
 
+// True where a kernel can store a result of `rows` rows of `row_bytes` bytes
+// at `pitch` straight into host buffer p: the first and the last byte it
+// writes are page-locked host memory that the device maps at the same
+// addresses, and p and pitch are multiples of the element size `elem`.
+__attribute__((visibility("hidden"))) bool host_kernel_writable(const void *p, size_t pitch,
+                                                                size_t rows, size_t row_bytes,
+                                                                size_t elem);
+
 // Make `dev` current for the lifetime of the guard.
 class DeviceScope {
  public:

@@ -1,6 +1,7 @@
 // sobel4_pipeline.cu — graph-captured video pipeline: per frame slot, one CUDA
-// graph of host->device copy, the RG kernel and device->host copy, launched
-// on the slot's own stream so the copies of one slot overlap the kernel of
+// graph of host->device copy and the kernel, which stores the result straight
+// into the slot's page-locked host output (no device->host copy), launched on
+// the slot's own stream so the upload of one slot overlaps the kernel of
 // another.  This is the stream processing that the paper proposes for its
 // IO bottleneck (Section 5.2, Section 6).
 #include <cuda_runtime.h>
@@ -25,6 +26,7 @@ struct Slot {
   cudaGraphExec_t kexec = nullptr;  // the slot's kernel alone (caller buffers)
   cudaEvent_t done = nullptr;
   bool pending = false;
+  bool out_direct = false;  // exec's kernel stores into h_out itself
 };
 
 size_t elem_bytes(int fmt) {
@@ -59,6 +61,36 @@ void release(sobel4_pipeline_ctx *p) {
     if (s.d_pair) cudaFree(s.d_pair);
   }
   delete p;
+}
+
+// Captures the slot's kernel (input s.d_in, output dst at the pipeline's
+// output pitch) into *g.
+cudaError_t capture(sobel4_pipeline_ctx *p, Slot &s, void *dst, cudaGraph_t *g,
+                    sobel4_status *st) {
+  *g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  *st = sobel4::run_with_pair(p->h, s.d_in, p->in_pitch, dst, p->out_pitch, p->H, p->W,
+                              p->border, p->fmt, s.stream, s.d_pair);
+  return cudaStreamEndCapture(s.stream, g);
+}
+
+// A graph's roots (nodes without dependencies) and leaves (nodes nothing
+// depends on).
+cudaError_t ends_of(cudaGraph_t g, std::vector<cudaGraphNode_t> *roots,
+                    std::vector<cudaGraphNode_t> *leaves) {
+  size_t n = 0;
+  cudaError_t e = cudaGraphGetNodes(g, nullptr, &n);
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (e == cudaSuccess && n) e = cudaGraphGetNodes(g, nodes.data(), &n);
+  for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
+    size_t nd = 0, nu = 0;
+    e = cudaGraphNodeGetDependencies(nodes[i], nullptr, nullptr, &nd);
+    if (e == cudaSuccess) e = cudaGraphNodeGetDependentNodes(nodes[i], nullptr, nullptr, &nu);
+    if (e == cudaSuccess && nd == 0) roots->push_back(nodes[i]);
+    if (e == cudaSuccess && nu == 0) leaves->push_back(nodes[i]);
+  }
+  return e;
 }
 
 }  // namespace
@@ -102,47 +134,37 @@ extern "C" sobel4_status sobel4_pipeline_create(sobel4_handle h, int32_t height,
     e = cudaMemsetAsync(s.d_in, 0, p->in_bytes, s.stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s.stream);
     if (e != cudaSuccess) break;
-    // The kernel is captured alone (kexec, for frames in caller buffers),
-    // then the slot's two copies are added as 1-D memcpy nodes before and
-    // after it (exec: upload, kernel, download as one graph).
+    // Two captures of the slot's kernel.  kexec: the kernel alone, into the
+    // slot's device output (caller frames whose results must be copied out).
+    // exec: the upload as a 1-D memcpy node, then the kernel storing straight
+    // into the slot's page-locked output (mapped at the same address on the
+    // device), so no download; where that memory is not kernel-writable the
+    // kernel writes the device output and a download node follows.
     cudaGraph_t g = nullptr;
-    e = cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) break;
-    st = sobel4::run_with_pair(h, s.d_in, p->in_pitch, s.d_out, p->out_pitch, height, width,
-                               border, fmt, s.stream, s.d_pair);
-    e = cudaStreamEndCapture(s.stream, &g);
-    if (st != SOBEL4_OK || e != cudaSuccess) {
-      if (g) cudaGraphDestroy(g);
-      break;
-    }
-    e = cudaGraphInstantiate(&s.kexec, g, 0);
-    if (e == cudaSuccess) {
-      size_t n = 0;
-      e = cudaGraphGetNodes(g, nullptr, &n);
-      std::vector<cudaGraphNode_t> kernels(n);
-      if (e == cudaSuccess && n) e = cudaGraphGetNodes(g, kernels.data(), &n);
-      // roots: nodes without dependencies; leaves: nodes nothing depends on
+    e = capture(p, s, s.d_out, &g, &st);
+    if (e == cudaSuccess && st == SOBEL4_OK) e = cudaGraphInstantiate(&s.kexec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    g = nullptr;
+    if (e != cudaSuccess || st != SOBEL4_OK) break;
+    s.out_direct = sobel4::host_kernel_writable(s.h_out, p->out_pitch, (size_t)height * planes,
+                                                (size_t)width * elem_bytes(fmt), elem_bytes(fmt));
+    e = capture(p, s, s.out_direct ? s.h_out : s.d_out, &g, &st);
+    if (e == cudaSuccess && st == SOBEL4_OK) {
       std::vector<cudaGraphNode_t> roots, leaves;
-      for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
-        size_t nd = 0, nu = 0;
-        e = cudaGraphNodeGetDependencies(kernels[i], nullptr, nullptr, &nd);
-        if (e == cudaSuccess) e = cudaGraphNodeGetDependentNodes(kernels[i], nullptr, nullptr, &nu);
-        if (e == cudaSuccess && nd == 0) roots.push_back(kernels[i]);
-        if (e == cudaSuccess && nu == 0) leaves.push_back(kernels[i]);
-      }
+      e = ends_of(g, &roots, &leaves);
       cudaGraphNode_t copy_in = nullptr, copy_out = nullptr;
       if (e == cudaSuccess)
         e = cudaGraphAddMemcpyNode1D(&copy_in, g, nullptr, 0, s.d_in, s.h_in, p->in_bytes,
                                      cudaMemcpyHostToDevice);
       for (size_t i = 0; i < roots.size() && e == cudaSuccess; ++i)
         e = cudaGraphAddDependencies(g, &copy_in, &roots[i], nullptr, 1);
-      if (e == cudaSuccess)
+      if (e == cudaSuccess && !s.out_direct)
         e = cudaGraphAddMemcpyNode1D(&copy_out, g, leaves.data(), leaves.size(), s.h_out,
                                      s.d_out, p->out_bytes, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&s.exec, g, 0);
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&s.exec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) break;
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess || st != SOBEL4_OK) break;
   }
   if (st == SOBEL4_OK && e != cudaSuccess)
     st = e == cudaErrorMemoryAllocation ? SOBEL4_ERR_OOM : SOBEL4_ERR_CUDA;
@@ -154,7 +176,7 @@ extern "C" sobel4_status sobel4_pipeline_create(sobel4_handle h, int32_t height,
   // Capturing recorded the kernels into the graphs without launching them.
   // Captures are not launches; each replay launches this many kernels.
   const uint64_t captured = sobel4_launch_count(h) - launches0;
-  p->kernels_per_frame = p->slots.empty() ? 1 : (int64_t)(captured / p->slots.size());
+  p->kernels_per_frame = p->slots.empty() ? 1 : (int64_t)(captured / (2 * p->slots.size()));
   sobel4::note_launches(h, -(int64_t)captured);
   *out = p;
   return SOBEL4_OK;
@@ -177,22 +199,35 @@ namespace {
 // upload, the kernel's graph and the caller's download on the slot's stream.
 sobel4_status launch_slot(sobel4_pipeline p, Slot &s, const void *in, void *out) {
   cudaError_t e = cudaSuccess;
+  sobel4_status st = SOBEL4_OK;
+  bool graph = true;  // the launch replays a captured graph (counted here)
   if (in == s.h_in && out == s.h_out) {
     e = cudaGraphLaunch(s.exec, s.stream);
   } else {
+    const size_t planes = p->fmt == SOBEL4_OUT_S16X4 ? 4 : 1;
     e = cudaMemcpyAsync(s.d_in, in, p->in_bytes, cudaMemcpyHostToDevice, s.stream);
-    if (e == cudaSuccess) e = cudaGraphLaunch(s.kexec, s.stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(out, s.d_out, p->out_bytes, cudaMemcpyDeviceToHost, s.stream);
+    if (e == cudaSuccess &&
+        sobel4::host_kernel_writable(out, p->out_pitch, (size_t)p->H * planes,
+                                     (size_t)p->W * elem_bytes(p->fmt), elem_bytes(p->fmt))) {
+      // the kernel stores the result into the caller's page-locked buffer
+      graph = false;
+      st = sobel4::run_with_pair(p->h, s.d_in, p->in_pitch, out, p->out_pitch, p->H, p->W,
+                                 p->border, p->fmt, s.stream, s.d_pair);
+    } else if (e == cudaSuccess) {
+      e = cudaGraphLaunch(s.kexec, s.stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, s.d_out, p->out_bytes, cudaMemcpyDeviceToHost, s.stream);
+    }
   }
-  if (e == cudaSuccess) e = cudaEventRecord(s.done, s.stream);
+  if (e == cudaSuccess && st == SOBEL4_OK) e = cudaEventRecord(s.done, s.stream);
   if (e != cudaSuccess) {
     (void)cudaGetLastError();
     sobel4::note_cuda_error(p->h, e);
     return SOBEL4_ERR_CUDA;
   }
+  if (st != SOBEL4_OK) return st;
   s.pending = true;
-  sobel4::note_launches(p->h, p->kernels_per_frame);
+  if (graph) sobel4::note_launches(p->h, p->kernels_per_frame);
   return SOBEL4_OK;
 }
 

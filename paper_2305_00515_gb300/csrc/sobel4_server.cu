@@ -1,19 +1,26 @@
 // sobel4_server.cu — a continuous-batching request server around the batched
 // kernel.  Requests (host images of any size) are admitted first-in
-// first-out while a device-memory arena has room for their input and output,
-// uploaded on a copy stream, packed into one persistent batched launch per
-// scheduling step (at most kMaxInFlight batches on the GPU at once, so
-// requests that arrive while a batch runs join the next one), and downloaded
-// on a third stream (a batch of one runs as a single-image launch).  Each
-// request completes when its own download has landed: a host function after
-// each download signals it, so the scheduler never polls the GPU and a small
-// request never waits for a large one's download.  Two comparison modes:
-// every request its own single-image launch on the same three streams
+// first-out while a device-memory arena has room for their input (and their
+// output, where it must be staged), uploaded on a copy stream, packed into
+// one persistent batched launch per scheduling step (at most kMaxInFlight
+// batches on the GPU at once, so requests that arrive while a batch runs join
+// the next one; a batch of up to three runs as single-image launches).  A result
+// buffer in mapped page-locked host memory is the kernel's own output: the
+// kernel's stores cross the host link directly, with no device-to-host copy
+// (whose rate on a Grace host drops after idle gaps: 4K downloads measured
+// 184 us median, up to 2 ms at the 99th percentile with 2.5 ms between
+// requests, against 185 / 218 us for the kernel's own stores).  Any other
+// result buffer gets an arena block and a download on a third stream.  An
+// event after each request's last operation marks it; a completion thread
+// waits on those events in order, so a small request never waits for a large
+// one's download and no CUDA host function is involved.  Two comparison
+// modes: every request its own single-image launch on the same streams
 // (plain = 1), or one sobel4_run per request in arrival order on ONE stream,
 // upload, kernel and download back to back (plain = 2).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -31,6 +38,7 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 constexpr int kMaxInFlight = 2;
+constexpr size_t kSinglesUpTo = 3;  // larger batches take one persistent batched launch
 constexpr size_t kAlign = 256;
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -95,14 +103,26 @@ struct Request {
   size_t dp = 0;
   int32_t H = 0, W = 0;
   size_t in_bytes = 0, out_bytes = 0, d_sp = 0, d_dp = 0, off = 0;
-  // arena bytes: the input block, then the output block, each 256-byte aligned
-  size_t arena_bytes() const { return round_up(in_bytes, kAlign) + round_up(out_bytes, kAlign); }
+  bool direct = false;  // the kernel writes h_dst itself (mapped page-locked memory)
+  // arena bytes: the input block, then (staged results only) the output
+  // block, each 256-byte aligned
+  size_t arena_bytes() const {
+    return round_up(in_bytes, kAlign) + (direct ? 0 : round_up(out_bytes, kAlign));
+  }
   uint8_t *d_in = nullptr, *d_out = nullptr;
   Clock::time_point t_submit, t_done;
   State state = kQueued;
 };
 
 struct Batch;
+
+// A request whose last operation has been enqueued: the completion thread
+// waits on `ev` (recorded after it) and then retires member `idx` of `b`.
+struct Pending {
+  cudaEvent_t ev;
+  Batch *b;
+  size_t idx;
+};
 
 }  // namespace
 
@@ -113,13 +133,15 @@ struct sobel4_server_ctx {
   uint8_t *arena_mem = nullptr;
   Arena arena;
   cudaStream_t up = nullptr, comp = nullptr, down = nullptr;
-  std::thread sched;
+  std::thread sched, completer;
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
-  bool stop = false;
+  std::condition_variable cv_work, cv_done, cv_cq;
+  bool stop = false;       // no more submissions; the scheduler drains and exits
+  bool sched_done = false;  // the scheduler has exited; the completer drains and exits
   bool failed = false;
   std::deque<uint64_t> incoming, admitted;
   std::unordered_map<uint64_t, Request> reqs;
+  std::deque<Pending> cq;  // in the order of the GPU work they follow
   int in_flight = 0;
   uint64_t next_ticket = 1;
   std::vector<cudaEvent_t> event_pool;
@@ -128,47 +150,50 @@ struct sobel4_server_ctx {
 
 namespace {
 
-struct Batch;
-
-// One request of a batch, the argument of its completion host function.
+// One request of a batch.
 struct Member {
-  Batch *b;
   uint64_t ticket;
+  cudaEvent_t ev;  // recorded after the request's last operation
 };
 
 struct Batch {
-  sobel4_server_ctx *s;
   std::vector<Member> members;
-  int remaining = 0;  // members whose download has not landed yet
-  cudaEvent_t done;
+  int remaining = 0;  // members not yet retired
+  cudaEvent_t done;   // orders upload -> kernel -> downloads across the streams
 };
 
-// A request's download has landed: its result is in host memory.  The batch
-// leaves the GPU with its last member.
-void CUDART_CB member_finished(void *arg) {
-  Member *m = (Member *)arg;
-  Batch *b = m->b;
-  sobel4_server_ctx *s = b->s;
-  bool last = false;
-  {
-    std::lock_guard<std::mutex> lock(s->mu);
-    auto it = s->reqs.find(m->ticket);
-    if (it != s->reqs.end()) {
-      Request &r = it->second;
-      r.t_done = Clock::now();
+cudaEvent_t take_event(sobel4_server_ctx *s) {
+  if (!s->event_pool.empty()) {
+    cudaEvent_t e = s->event_pool.back();
+    s->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// With the lock held: a request's result is in host memory.  The batch
+// leaves the GPU with its last member; returns the batch to delete, if any.
+Batch *retire(sobel4_server_ctx *s, Batch *b, size_t idx) {
+  auto it = s->reqs.find(b->members[idx].ticket);
+  if (it != s->reqs.end()) {
+    Request &r = it->second;
+    r.t_done = Clock::now();
+    if (r.state != kFailed) {
       r.state = kDone;
-      s->arena.release(r.off, r.arena_bytes());
       s->stats.completed += 1;
     }
-    last = --b->remaining == 0;
-    if (last) {
-      s->in_flight -= 1;
-      s->event_pool.push_back(b->done);
-    }
+    s->arena.release(r.off, r.arena_bytes());
   }
-  s->cv_done.notify_all();
-  s->cv_work.notify_one();
-  if (last) delete b;
+  s->event_pool.push_back(b->members[idx].ev);
+  if (--b->remaining > 0) return nullptr;
+  s->in_flight -= 1;
+  s->event_pool.push_back(b->done);
+  return b;
 }
 
 void fail_all(sobel4_server_ctx *s) {
@@ -181,20 +206,38 @@ void fail_all(sobel4_server_ctx *s) {
   s->cv_done.notify_all();
 }
 
-cudaEvent_t take_event(sobel4_server_ctx *s) {
-  if (!s->event_pool.empty()) {
-    cudaEvent_t e = s->event_pool.back();
-    s->event_pool.pop_back();
-    return e;
+// Waits for each pending request's event in order: every request's last
+// operation is on the download stream (the one stream in the one-stream
+// mode), whose events complete in the order they were recorded.
+void completer(sobel4_server_ctx *s) {
+  sobel4::DeviceScope scope(s->device);
+  for (;;) {
+    Pending p;
+    {
+      std::unique_lock<std::mutex> lock(s->mu);
+      s->cv_cq.wait(lock, [&] { return !s->cq.empty() || s->sched_done; });
+      if (s->cq.empty()) break;
+      p = s->cq.front();
+    }
+    const cudaError_t e = cudaEventSynchronize(p.ev);
+    Batch *gone = nullptr;
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      s->cq.pop_front();
+      if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        fail_all(s);
+      }
+      gone = retire(s, p.b, p.idx);
+    }
+    s->cv_done.notify_all();
+    s->cv_work.notify_one();
+    delete gone;
   }
-  cudaEvent_t e = nullptr;
-  if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
-  return e;
 }
 
 // One upload or one batch member, copied out of the request table so that
-// CUDA calls run without the lock held (a blocking copy must never wait on a
-// host function that needs the lock).
+// CUDA calls run without the lock held.
 struct Job {
   uint64_t ticket;
   const uint8_t *h_src;
@@ -204,10 +247,12 @@ struct Job {
   int32_t H, W;
   uint8_t *d_in, *d_out;
   size_t d_sp, d_dp;
+  bool direct;
 };
 
 Job job_of(uint64_t t, const Request &r) {
-  return Job{t, r.h_src, r.sp, r.h_dst, r.dp, r.H, r.W, r.d_in, r.d_out, r.d_sp, r.d_dp};
+  return Job{t, r.h_src, r.sp, r.h_dst, r.dp, r.H, r.W, r.d_in, r.d_out, r.d_sp, r.d_dp,
+             r.direct};
 }
 
 void scheduler(sobel4_server_ctx *s) {
@@ -240,7 +285,8 @@ void scheduler(sobel4_server_ctx *s) {
         if (!s->arena.alloc(r.arena_bytes(), &off)) break;
         r.off = off;
         r.d_in = s->arena_mem + off;
-        r.d_out = r.d_in + round_up(r.in_bytes, kAlign);
+        r.d_out = r.direct ? (uint8_t *)r.h_dst : r.d_in + round_up(r.in_bytes, kAlign);
+        if (r.direct) r.d_dp = r.dp;
         r.state = kAdmitted;
         uploads.push_back(job_of(t, r));
         s->admitted.push_back(t);
@@ -249,29 +295,38 @@ void scheduler(sobel4_server_ctx *s) {
       // 2. One launch of everything admitted (bounded by max_batch; in the
       //    one-stream mode one request per launch, as many as are admitted).
       if (!s->admitted.empty() && (serial || s->in_flight < kMaxInFlight)) {
+        const int32_t cap = serial ? 1 : s->opt.max_batch;
+        const size_t n = std::min<size_t>(s->admitted.size(), (size_t)cap);
         b = new (std::nothrow) Batch();
-        cudaEvent_t ev = b ? take_event(s) : nullptr;
-        if (!b || !ev) {
+        bool ok = b != nullptr;
+        if (ok) b->done = take_event(s);
+        ok = ok && b->done;
+        for (size_t i = 0; ok && i < n; ++i) {
+          cudaEvent_t ev = take_event(s);
+          ok = ev != nullptr;
+          if (ok) b->members.push_back(Member{0, ev});
+        }
+        if (!ok) {
+          if (b) {
+            for (const Member &m : b->members) s->event_pool.push_back(m.ev);
+            if (b->done) s->event_pool.push_back(b->done);
+          }
           delete b;
           fail_all(s);
           break;
         }
-        b->s = s;
-        b->done = ev;
-        const int32_t cap = serial ? 1 : s->opt.max_batch;
-        while (!s->admitted.empty() && (int32_t)members.size() < cap) {
+        for (size_t i = 0; i < n; ++i) {
           const uint64_t t = s->admitted.front();
           s->admitted.pop_front();
           Request &r = s->reqs[t];
           r.state = kInFlight;
-          b->members.push_back(Member{b, t});
+          b->members[i].ticket = t;
           members.push_back(job_of(t, r));
         }
-        b->remaining = (int)b->members.size();
+        b->remaining = (int)n;
         s->in_flight += 1;
         s->stats.batches += 1;
-        if ((uint64_t)members.size() > s->stats.max_batch_seen)
-          s->stats.max_batch_seen = members.size();
+        if ((uint64_t)n > s->stats.max_batch_seen) s->stats.max_batch_seen = n;
       }
       more = serial && !s->admitted.empty();
     }
@@ -297,9 +352,11 @@ void scheduler(sobel4_server_ctx *s) {
       e = cudaEventRecord(b->done, up);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(comp, b->done, 0);
       if (e == cudaSuccess) {
-        // A batch of one runs as a single-image launch: the batched path adds
-        // a descriptor upload and gains nothing for one image.
-        if (s->opt.plain || members.size() == 1) {
+        // Batches of up to kSinglesUpTo images run as single-image launches:
+        // the batched path adds a descriptor upload and gains nothing there
+        // (results into pinned host memory: two 1080p images 111 us batched
+        // against 102 us as two launches; four mixed images level).
+        if (s->opt.plain || members.size() <= kSinglesUpTo) {
           for (const Job &j : members) {
             st = sobel4_run(s->h, j.d_in, j.d_sp, j.d_out, j.d_dp, j.H, j.W,
                             (sobel4_border)s->opt.border, (sobel4_format)fmt, comp);
@@ -312,36 +369,60 @@ void scheduler(sobel4_server_ctx *s) {
             imgs.push_back(sobel4_image{j.d_in, j.d_sp, j.d_out, j.d_dp, j.H, j.W});
           st = sobel4_run_batched(s->h, imgs.data(), (int32_t)imgs.size(),
                                   (sobel4_border)s->opt.border, (sobel4_format)fmt, comp);
+          // The batched launch refuses results that overlap (two pending
+          // requests sharing one result buffer, written in place): those run
+          // one launch each rather than failing the server.
+          if (st == SOBEL4_ERR_INVALID_ARG) {
+            st = SOBEL4_OK;
+            for (size_t i = 0; i < members.size() && st == SOBEL4_OK; ++i) {
+              const Job &j = members[i];
+              st = sobel4_run(s->h, j.d_in, j.d_sp, j.d_out, j.d_dp, j.H, j.W,
+                              (sobel4_border)s->opt.border, (sobel4_format)fmt, comp);
+            }
+          }
         }
       }
       if (e == cudaSuccess && st == SOBEL4_OK) e = cudaEventRecord(b->done, comp);
       if (e == cudaSuccess && st == SOBEL4_OK) e = cudaStreamWaitEvent(down, b->done, 0);
     }
-    // Each member's download, then its completion.
-    size_t enqueued = 0;  // completion host functions on the GPU's queue
+    // Each member's download (results the kernel did not write in place),
+    // then its event, then its place in the completion queue.
+    size_t enqueued = 0;
     for (size_t i = 0; b && i < members.size() && e == cudaSuccess && st == SOBEL4_OK; ++i) {
       const Job &j = members[i];
-      e = cudaMemcpy2DAsync(j.h_dst, j.dp, j.d_out, j.d_dp, (size_t)j.W * elem_bytes(fmt),
-                            (size_t)j.H * planes, cudaMemcpyDeviceToHost, down);
-      if (e == cudaSuccess) e = cudaLaunchHostFunc(down, member_finished, &b->members[i]);
-      if (e == cudaSuccess) ++enqueued;
+      if (!j.direct)
+        e = cudaMemcpy2DAsync(j.h_dst, j.dp, j.d_out, j.d_dp, (size_t)j.W * elem_bytes(fmt),
+                              (size_t)j.H * planes, cudaMemcpyDeviceToHost, down);
+      if (e == cudaSuccess) e = cudaEventRecord(b->members[i].ev, down);
+      if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->cq.push_back(Pending{b->members[i].ev, b, i});
+        ++enqueued;
+      }
+      s->cv_cq.notify_one();
     }
     if (e != cudaSuccess || st != SOBEL4_OK) {
-      std::lock_guard<std::mutex> lock(s->mu);
-      if (b) {
-        // members whose completion never reached the GPU will not call back;
-        // the batch is retired here once none of the others is outstanding
-        b->remaining -= (int)(members.size() - enqueued);
-        if (b->remaining == 0) {
-          s->in_flight -= 1;
-          s->event_pool.push_back(b->done);
-          delete b;
+      if (e != cudaSuccess) (void)cudaGetLastError();
+      Batch *gone = nullptr;
+      {
+        std::lock_guard<std::mutex> lock(s->mu);
+        fail_all(s);
+        // members that never reached the completion queue are retired here;
+        // the batch goes with the last of its members
+        for (size_t i = enqueued; b && i < members.size(); ++i) {
+          Batch *g = retire(s, b, i);
+          if (g) gone = g;
         }
       }
-      fail_all(s);
+      delete gone;
       break;
     }
   }
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->sched_done = true;
+  }
+  s->cv_cq.notify_all();
 }
 
 }  // namespace
@@ -373,6 +454,7 @@ extern "C" sobel4_status sobel4_server_create(sobel4_handle h, const sobel4_serv
   }
   s->arena.reset((size_t)s->opt.memory_budget);
   s->sched = std::thread(scheduler, s);
+  s->completer = std::thread(completer, s);
   *out = s;
   return SOBEL4_OK;
 }
@@ -394,7 +476,14 @@ extern "C" sobel4_status sobel4_server_submit(sobel4_server s, const uint8_t *h_
   r.d_sp = round_up((size_t)width, 16);
   r.d_dp = round_up((size_t)width * elem_bytes(s->opt.format), 16);
   r.in_bytes = r.d_sp * (size_t)height;
-  r.out_bytes = r.d_dp * (size_t)height * (s->opt.format == SOBEL4_OUT_S16X4 ? 4 : 1);
+  const size_t planes = s->opt.format == SOBEL4_OUT_S16X4 ? 4 : 1;
+  r.out_bytes = r.d_dp * (size_t)height * planes;
+  {
+    sobel4::DeviceScope scope(s->device);
+    r.direct = sobel4::host_kernel_writable(h_dst, dst_pitch, (size_t)height * planes,
+                                            (size_t)width * elem_bytes(s->opt.format),
+                                            elem_bytes(s->opt.format));
+  }
   if (r.arena_bytes() > (size_t)s->opt.memory_budget)
     return SOBEL4_ERR_UNSUPPORTED;  // could never be admitted
   r.t_submit = Clock::now();
@@ -454,14 +543,17 @@ extern "C" sobel4_status sobel4_server_destroy(sobel4_server s) {
     s->cv_work.notify_all();
     s->sched.join();
   }
+  // the scheduler has exited (or never started): the completer retires what
+  // is still on the GPU, then exits
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->sched_done = true;
+  }
+  s->cv_cq.notify_all();
+  if (s->completer.joinable()) s->completer.join();
   sobel4::DeviceScope scope(s->device);
   for (cudaStream_t st : {s->up, s->comp, s->down})
     if (st) cudaStreamSynchronize(st);
-  {
-    // the final host functions have run once the download stream is idle
-    std::unique_lock<std::mutex> lock(s->mu);
-    s->cv_done.wait_for(lock, std::chrono::seconds(5), [&] { return s->in_flight == 0; });
-  }
   for (cudaStream_t st : {s->up, s->comp, s->down})
     if (st) cudaStreamDestroy(st);
   for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);

@@ -56,7 +56,9 @@ def test_pipeline_rejects_bad_arguments():
 
 def test_pipeline_submit_from_caller_buffers():
     """Each frame from its own host buffer (pinned by cudaHostAlloc, or a numpy
-    array registered with cudaHostRegister), results into caller buffers."""
+    array registered with cudaHostRegister), results into caller buffers:
+    pinned ones, which the kernel writes itself, and one pageable buffer,
+    which gets the staged kernel and a download."""
     H, W = 120, 256
     bg = synth.video_background(H, W, 8)
     frames = [synth.video_frame(bg, k, H, W, 8) for k in range(6)]
@@ -65,6 +67,7 @@ def test_pipeline_submit_from_caller_buffers():
     cudart = torch.cuda.cudart()
     assert int(cudart.cudaHostRegister(ring.ctypes.data, ring.nbytes, 0)) == 0
     outs = [torch.empty((H, W), dtype=torch.float32).pin_memory() for _ in frames]
+    outs[4] = torch.full((H, W), 7.0)  # pageable: the kernel graph and a download
     try:
         with pkg.Sobel4(0) as s:
             pipe = pkg.Pipeline(s, H, W, "valid", "f32", slots=2)

@@ -1,6 +1,7 @@
 """The continuous-batching server: every request's result equals the oracle
 and its own standalone sobel4_run, whether it ran in a batch with others, as
-its own launch, or in the one-stream plain mode; admission respects the
+its own launch, or in the one-stream plain mode, and whether the kernel wrote
+it into pinned host memory or it was staged and downloaded; admission respects the
 device-memory budget; the batched mode really packs concurrent requests into
 shared launches (a large first request keeps the GPU busy while the others
 arrive, so they meet in the next batch)."""
@@ -25,6 +26,9 @@ def pinned(shape, dtype):
 
 
 def make_requests(n, seed, fmt, first=None):
+    """Pinned inputs; every third result buffer is pageable (numpy) memory,
+    which the server stages in its arena and downloads, the others pinned,
+    which the kernel writes itself."""
     rng = np.random.default_rng(seed)
     reqs = []
     for i in range(n):
@@ -34,7 +38,11 @@ def make_requests(n, seed, fmt, first=None):
         _, src = pinned((H, W), np.uint8)
         src[:] = synth.rects_noise(H, W, seed * 100 + i)
         dt = {"f32": np.float32, "u8": np.uint8, "s16x4": np.int16}[fmt]
-        keep, dst = pinned((4, H, W) if fmt == "s16x4" else (H, W), dt)
+        shape = (4, H, W) if fmt == "s16x4" else (H, W)
+        if i % 3 == 2:
+            keep, dst = None, np.full(shape, 7, dt)
+        else:
+            keep, dst = pinned(shape, dt)
         reqs.append((src, dst, keep))
     return reqs
 
@@ -68,6 +76,7 @@ def run_server(reqs, fmt, border, plain, budget=0, threads=1):
         rc, stats = pkg.sobel4_server_stats(srv)
         assert rc == 0
         assert pkg.sobel4_server_destroy(srv) == 0
+        stats["launches"] = s.launches
     return lats, stats
 
 
@@ -90,9 +99,13 @@ def test_server_results_match_oracle_alone_and_in_the_mix(plain, fmt, border):
     assert all(l > 0 for l in lats)
     assert 1 <= stats["batches"] <= len(reqs)
     if plain == 0:
-        assert stats["max_batch_seen"] >= 2, "no two requests ever shared a launch"
-    elif plain == 2:
-        assert stats["max_batch_seen"] == 1  # one request per step on the one stream
+        # batches of four or more take one batched launch (plus its descriptor upload)
+        assert stats["max_batch_seen"] >= 4, "no four requests ever met in a batch"
+        assert stats["launches"] < len(reqs), "no two requests ever shared a launch"
+    else:
+        assert stats["launches"] >= len(reqs)  # a sobel4_run (one or more kernels) per request
+        if plain == 2:
+            assert stats["max_batch_seen"] == 1  # one request per step on the one stream
     assert stats["device_bytes_in_use"] == 0
     for src, dst, _ in reqs:
         assert same_bits(dst, oracle.sobel4(src, border, fmt))
