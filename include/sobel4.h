@@ -360,13 +360,14 @@ sobel4_status sobel4_run_batched_static(const sobel4_image *h_images, int32_t n,
  * candidates.  It records the fastest in
  * the handle's table under the bucket (ceil log2 height, ceil log2 width,
  * fmt).  Later sobel4_run calls whose shape falls in that bucket use it.
- * *best_us (may be NULL) receives the chosen candidate's median time in
- * microseconds.  On a handle with runtime weights (sobel4_set_weights other
- * than Eq. 3's) it times only the TMA-staged kernel with the weights'
- * coefficients, and answers UNSUPPORTED where those weights do not run on the
- * packed passes (S16X4, the DIRECT variant, weights outside the proven range,
- * the two-directional operators).  Synchronous.  Errors: INVALID_ARG,
- * UNSUPPORTED, OOM, CUDA.
+ * Each candidate is timed as three regions of ten back-to-back launches;
+ * *best_us (may be NULL) receives the chosen candidate's time per launch in
+ * microseconds (the median of the three regions' means).  On a handle with
+ * runtime weights (sobel4_set_weights other than Eq. 3's) it times only the
+ * TMA-staged kernel with the weights' coefficients, and answers UNSUPPORTED
+ * where those weights do not run on the packed passes (S16X4, the DIRECT
+ * variant, weights outside the proven range, the two-directional operators).
+ * Synchronous.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.
  */
 sobel4_status sobel4_tune(sobel4_handle h, int32_t height, int32_t width, sobel4_border border,
                           sobel4_format fmt, float *best_us);

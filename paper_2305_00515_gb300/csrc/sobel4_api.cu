@@ -1188,29 +1188,36 @@ extern "C" sobel4_status sobel4_run_batched_static(const sobel4_image *imgs, int
 namespace {
 
 constexpr int kTuneWarmup = 2;
-constexpr int kTuneReps = 9;
+// Each candidate runs kTuneRegions regions of kTuneLaunches back-to-back
+// launches between two events (steady-state throughput, as a stream of
+// launches sees it: per-launch event pairs add their own gaps); its time is
+// the median of the regions' means.
+constexpr int kTuneRegions = 3;
+constexpr int kTuneLaunches = 10;
 
 template <class Launch>
 cudaError_t median_us(cudaStream_t st, Launch launch, float *us) {
-  cudaEvent_t ev[2 * kTuneReps];
-  for (int i = 0; i < 2 * kTuneReps; ++i) ev[i] = nullptr;
+  cudaEvent_t ev[kTuneRegions + 1];
+  for (int i = 0; i <= kTuneRegions; ++i) ev[i] = nullptr;
   cudaError_t e = cudaSuccess;
-  for (int i = 0; i < 2 * kTuneReps && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
+  for (int i = 0; i <= kTuneRegions && e == cudaSuccess; ++i) e = cudaEventCreate(&ev[i]);
   for (int i = 0; i < kTuneWarmup && e == cudaSuccess; ++i) e = launch();
-  for (int i = 0; i < kTuneReps && e == cudaSuccess; ++i) {
-    e = cudaEventRecord(ev[2 * i], st);
-    if (e == cudaSuccess) e = launch();
-    if (e == cudaSuccess) e = cudaEventRecord(ev[2 * i + 1], st);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+  for (int r = 0; r < kTuneRegions && e == cudaSuccess; ++r) {
+    for (int i = 0; i < kTuneLaunches && e == cudaSuccess; ++i) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(ev[r + 1], st);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  float t[kTuneReps];
-  for (int i = 0; i < kTuneReps && e == cudaSuccess; ++i)
-    e = cudaEventElapsedTime(&t[i], ev[2 * i], ev[2 * i + 1]);
-  for (int i = 0; i < 2 * kTuneReps; ++i)
+  float t[kTuneRegions];
+  for (int r = 0; r < kTuneRegions && e == cudaSuccess; ++r) {
+    e = cudaEventElapsedTime(&t[r], ev[r], ev[r + 1]);
+    t[r] /= (float)kTuneLaunches;
+  }
+  for (int i = 0; i <= kTuneRegions; ++i)
     if (ev[i]) cudaEventDestroy(ev[i]);
   if (e != cudaSuccess) return e;
-  std::sort(t, t + kTuneReps);
-  *us = 1000.0f * t[kTuneReps / 2];
+  std::sort(t, t + kTuneRegions);
+  *us = 1000.0f * t[kTuneRegions / 2];
   return cudaSuccess;
 }
 
