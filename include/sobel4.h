@@ -135,12 +135,25 @@ typedef enum {
   SOBEL4_VARIANT_LADDER_RG_V2 = 9
 } sobel4_variant;
 
-/* Creation options; pass NULL for defaults (all fields 0). */
+/*
+ * Creation options; pass NULL for defaults (all fields 0 / NULL).
+ * autotune = 1: the first sobel4_run of a shape bucket (ceil log2 height,
+ * ceil log2 width, format) that has no tuned entry first runs sobel4_tune
+ * for that shape (synchronous: scratch buffers, ~30 timed launches per
+ * candidate; the call returns after the tune and its own launch are
+ * enqueued); skipped while the call's stream is capturing, and each bucket
+ * is tried once.  Batches are tuned only by sobel4_tune_batched.
+ * cache_path: a tuning cache file (the sobel4_tune_save format), loaded at
+ * creation when present (before SOBEL4_TUNE_CACHE, which it replaces) and
+ * rewritten (atomically) after every automatic tune.  The string is copied.
+ */
 typedef struct {
   int32_t variant;               /* sobel4_variant; 0 = AUTO */
   int32_t rows_per_strip;        /* RG strip height R (rows per thread per strip); 0 = auto */
   int32_t persistent_ctas_per_sm;/* batched kernel CTAs per SM; 0 = auto */
   int32_t columns_per_lane;      /* RG columns per thread: 2 or 4; 0 = default */
+  int32_t autotune;              /* 1 = tune each new single-image shape bucket on first use */
+  const char *cache_path;        /* tuning cache file, or NULL */
 } sobel4_options;
 
 /* One image of a batch (all pointers are device pointers). */
@@ -336,7 +349,7 @@ sobel4_status sobel4_check_magnitude(sobel4_handle h, int32_t s_begin, int32_t s
  * of the RG_LANECOPY variant) over all n images.  `h_images` is read before
  * the call returns.  Every call looks up the array's device address on the
  * current device; the first call on a device can also load the library's
- * device code there, so make that first call before any stream capture.
+ * device code there.
  * Every call shares the one array and overwrites it: calls that overlap on
  * the GPU race, so serialise them (for example on one stream).  The call uses
  * about 4 KB of the calling thread's stack.  Results equal

@@ -84,7 +84,8 @@ class ServerStats(ctypes.Structure):
 class Options(ctypes.Structure):
     """``sobel4_options``."""
     _fields_ = [("variant", ctypes.c_int32), ("rows_per_strip", ctypes.c_int32),
-                ("persistent_ctas_per_sm", ctypes.c_int32), ("columns_per_lane", ctypes.c_int32)]
+                ("persistent_ctas_per_sm", ctypes.c_int32), ("columns_per_lane", ctypes.c_int32),
+                ("autotune", ctypes.c_int32), ("cache_path", ctypes.c_char_p)]
 
 
 _lock = threading.Lock()
@@ -172,9 +173,11 @@ def load() -> ctypes.CDLL:
 
 # -- one-to-one C ABI wrappers (raw pointers; return the status code) ----------
 def sobel4_create(device: int = 0, variant: int = 0, rows_per_strip: int = 0,
-                  persistent_ctas_per_sm: int = 0, columns_per_lane: int = 0):
+                  persistent_ctas_per_sm: int = 0, columns_per_lane: int = 0, autotune: int = 0,
+                  cache_path: str = None):
     h = ctypes.c_void_p()
-    opt = Options(variant, rows_per_strip, persistent_ctas_per_sm, columns_per_lane)
+    opt = Options(variant, rows_per_strip, persistent_ctas_per_sm, columns_per_lane, autotune,
+                  cache_path.encode() if cache_path else None)
     st = load().sobel4_create(ctypes.byref(h), device, ctypes.byref(opt))
     return st, h
 
@@ -460,9 +463,10 @@ class Sobel4:
     """A library handle bound to one CUDA device."""
 
     def __init__(self, device: int = 0, variant: str = "auto", rows_per_strip: int = 0,
-                 persistent_ctas_per_sm: int = 0, columns_per_lane: int = 0):
+                 persistent_ctas_per_sm: int = 0, columns_per_lane: int = 0,
+                 autotune: bool = False, cache_path: str = None):
         st, h = sobel4_create(device, VARIANTS[variant], rows_per_strip, persistent_ctas_per_sm,
-                              columns_per_lane)
+                              columns_per_lane, int(autotune), cache_path)
         _check(st, "sobel4_create")
         self.handle = h
         self.device = device

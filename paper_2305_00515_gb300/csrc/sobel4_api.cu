@@ -198,6 +198,9 @@ struct sobel4_ctx {
   size_t d_ring_bytes = 0;
   std::vector<TuneEntry> tuned;
   char device_name[256] = {0};
+  bool autotune = false;          // tune each new single-image shape bucket on first use
+  std::string cache_path;         // tuning cache rewritten after each automatic tune
+  std::vector<uint32_t> autotried;  // buckets the automatic tune has already handled
 };
 
 namespace sobel4 {
@@ -486,7 +489,8 @@ const char *sobel4_status_string(sobel4_status s) {
 sobel4_status sobel4_create(sobel4_handle *out, int32_t device, const sobel4_options *opt) {
   if (!out) return SOBEL4_ERR_INVALID_ARG;
   *out = nullptr;
-  if (opt && (opt->variant < 0 || opt->variant > SOBEL4_VARIANT_LADDER_RG_V2 || opt->rows_per_strip < 0 ||
+  if (opt && (opt->autotune < 0 || opt->autotune > 1 ||
+              opt->variant < 0 || opt->variant > SOBEL4_VARIANT_LADDER_RG_V2 || opt->rows_per_strip < 0 ||
               opt->rows_per_strip > 4096 || opt->persistent_ctas_per_sm < 0 ||
               opt->persistent_ctas_per_sm > 64 ||
               (opt->columns_per_lane != 0 && opt->columns_per_lane != 2 &&
@@ -528,8 +532,10 @@ sobel4_status sobel4_create(sobel4_handle *out, int32_t device, const sobel4_opt
       h->nc = opt->columns_per_lane;
       h->nc_forced = true;
     }
+    h->autotune = opt->autotune == 1;
+    if (opt->cache_path && *opt->cache_path) h->cache_path = opt->cache_path;
   }
-  const char *cache = getenv("SOBEL4_TUNE_CACHE");
+  const char *cache = h->cache_path.empty() ? getenv("SOBEL4_TUNE_CACHE") : h->cache_path.c_str();
   if (cache && *cache) sobel4_tune_load(h, cache);  // a missing or foreign cache is ignored
   *out = h;
   return SOBEL4_OK;
@@ -732,6 +738,25 @@ sobel4_status sobel4_set_variant(sobel4_handle h, int32_t variant) {
 sobel4_status sobel4_run(sobel4_handle h, const uint8_t *d_src, size_t src_pitch, void *d_dst,
                          size_t dst_pitch, int32_t height, int32_t width, sobel4_border border,
                          sobel4_format fmt, cudaStream_t stream) {
+  if (h && h->autotune && valid_shape(src_pitch, dst_pitch, height, width, border, fmt)) {
+    // The creation option autotune: the first run of a shape bucket without a
+    // tuned entry tunes it (scratch buffers, the handle's own stream), unless
+    // the call's stream is capturing.  A failed tune leaves the defaults.
+    const uint32_t key = ((uint32_t)ceil_log2(height) << 16) | ((uint32_t)ceil_log2(width) << 8) |
+                         (uint32_t)fmt;
+    if (std::find(h->autotried.begin(), h->autotried.end(), key) == h->autotried.end()) {
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) {
+        (void)cudaGetLastError();
+      } else if (cs == cudaStreamCaptureStatusNone) {
+        h->autotried.push_back(key);
+        if (!find_tuned(h, 0, height, width, fmt) &&
+            sobel4_tune(h, height, width, border, fmt, nullptr) == SOBEL4_OK &&
+            !h->cache_path.empty())
+          sobel4_tune_save(h, h->cache_path.c_str());
+      }
+    }
+  }
   return sobel4::run_with_pair(h, d_src, src_pitch, d_dst, dst_pitch, height, width, border, fmt,
                                stream, nullptr);
 }

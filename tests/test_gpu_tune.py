@@ -1,6 +1,7 @@
 """The autotuner: tuned configurations keep the output bit-exact, and the
-tuned table survives a save / load round trip and the SOBEL4_TUNE_CACHE
-variable."""
+tuned table survives a save / load round trip, the SOBEL4_TUNE_CACHE
+variable and the creation options' cache path; the autotune option tunes
+each new shape bucket on its first run."""
 import numpy as np
 import pytest
 
@@ -40,6 +41,32 @@ def test_tune_single_then_run(handle, tmp_path):
         assert same_bits(got2, got)
     finally:
         pkg.sobel4_destroy(h2)
+
+
+def test_autotune_option_and_cache_path(tmp_path):
+    """sobel4_options.autotune: the first sobel4_run of a shape bucket tunes
+    it (one entry per bucket, results exact); cache_path is rewritten after
+    each automatic tune and loaded by the next handle that names it."""
+    from paper_2305_00515_gb300 import build
+    build.build()
+    path = str(tmp_path / "auto.json")
+    st, h = pkg.sobel4_create(0, autotune=1, cache_path=path)
+    assert st == 0
+    try:
+        assert pkg.sobel4_tune_entries(h) == 0
+        for (H, W, n_after) in ((1000, 1500, 1), (900, 1100, 1), (300, 200, 2)):
+            img = synth.rects_noise(H, W, H + W)
+            got, guards = run_placed(torch, h, img, "replicate", "f32")
+            assert guards and same_bits(got, oracle.sobel4(img, "replicate", "f32", threads=8))
+            assert pkg.sobel4_tune_entries(h) == n_after, (H, W)
+    finally:
+        pkg.sobel4_destroy(h)
+    st, h2 = pkg.sobel4_create(0, cache_path=path)  # no autotune: the cache alone
+    try:
+        assert st == 0 and pkg.sobel4_tune_entries(h2) == 2
+    finally:
+        pkg.sobel4_destroy(h2)
+    assert pkg.sobel4_create(0, autotune=2)[0] == 1
 
 
 def test_tune_cache_rejections(handle, tmp_path, monkeypatch):
