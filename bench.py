@@ -67,9 +67,10 @@ def parse_args():
     ap.add_argument("--profile-batch", type=int, default=0, metavar="N",
                     help="run the first N images of the 512-image ragged batch (seed 1) through "
                          "sobel4_run_batched twice and exit (a capture target for ncu)")
-    ap.add_argument("--profile-single", choices=["rgb", "weights"], default=None,
-                    help="launch one 8192x8192 image twice through the colour input or the "
-                         "runtime-weight path, then exit (for ncu)")
+    ap.add_argument("--profile-single", choices=["rgb", "weights", "pitch"], default=None,
+                    help="launch one image twice, then exit (for ncu): 8192x8192 through the "
+                         "colour input or the runtime-weight path, or the size sweep's "
+                         "1920x1080 pitch-1937/7748 case")
     ap.add_argument("--profile-variants", action="store_true",
                     help="run every kernel variant twice on the workload image and exit "
                          "(a capture target for ncu; prints no JSON line)")
@@ -1074,9 +1075,11 @@ def profile_batch(n: int):
 
 
 def profile_single(kind: str):
-    """One 8192x8192 image launched twice through the fused colour input
+    """One image launched twice: 8192x8192 through the fused colour input
     ("rgb": interleaved RGB rects+noise, F32 VALID) or the runtime-weight path
-    ("weights": Eq. (5) weights (a, b, n, m) = (2, 1.5, 2, 2), F32 VALID)."""
+    ("weights": Eq. (5) weights (a, b, n, m) = (2, 1.5, 2, 2), F32 VALID), or
+    the size sweep's 1920x1080 rects+noise image at source pitch 1937 and
+    output pitch 7748 ("pitch", F32 VALID)."""
     import numpy as np
     import torch
 
@@ -1084,8 +1087,23 @@ def profile_single(kind: str):
     import synth
     st, h = pkg.sobel4_create(0)
     assert st == 0, pkg.sobel4_status_string(st)
-    out = torch.empty((H, W), dtype=torch.float32, device="cuda")
     stream = torch.cuda.Stream()
+    if kind == "pitch":
+        # the size sweep's pitch variant: 1920x1080, source pitch 1937, output pitch 7748
+        h1, w1, sp, dp = 1080, 1920, 1937, 7748
+        src = torch.zeros(h1 * sp, dtype=torch.uint8, device="cuda")
+        src.view(h1, sp)[:, :w1] = torch.from_numpy(synth.rects_noise(h1, w1, 0)).cuda()
+        out = torch.empty(h1 * dp, dtype=torch.uint8, device="cuda")
+        for _ in range(2):
+            rc = pkg.sobel4_run(h, src.data_ptr(), sp, out.data_ptr(), dp, h1, w1, 0, 0,
+                                stream.cuda_stream)
+            assert rc == 0, pkg.sobel4_status_string(rc)
+        stream.synchronize()
+        assert pkg.sobel4_device_status(h) == 0
+        pkg.sobel4_destroy(h)
+        print(f"{kind}: ok", flush=True)
+        return
+    out = torch.empty((H, W), dtype=torch.float32, device="cuda")
     if kind == "rgb":
         src = torch.from_numpy(np.stack([synth.rects_noise(H, W, 50 + c) for c in range(3)],
                                         axis=2)).cuda()

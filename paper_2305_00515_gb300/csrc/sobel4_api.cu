@@ -887,7 +887,8 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
   }
   int n_lane = 0, n_tma = 0;
   int64_t total = 0, total_tma = 0;
-  bool all_fast = true, bulk = false;
+  int fast = kBatchFastVec;
+  bool bulk = false;
   if (tma_ok) {
     for (int32_t i = 0; i < n && !bulk; ++i) bulk = !tma_eligible(imgs[i].src, imgs[i].src_pitch);
     const size_t db = tma_batch_desc_bytes(bulk);
@@ -899,8 +900,8 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
       if (e != cudaSuccess) return cuda_fail(h, e);
       total_tma += items;
       ++n_tma;
-      // the lean kernel needs every item on the fast path with vector stores
-      all_fast = all_fast && tma_all_fast_staged(m.width, border, fmt, bulk, m.dst, m.dst_pitch);
+      // the batch runs the kernel its least fast image needs (BatchFast)
+      fast = std::min(fast, tma_fast_level(m.width, border, fmt, bulk, m.dst, m.dst_pitch));
     }
   } else {
     for (int32_t i = 0; i < n; ++i) {
@@ -927,7 +928,7 @@ sobel4_status sobel4_run_batched(sobel4_handle h, const sobel4_image *imgs, int3
     const int64_t want = (total_tma + kWarpsPerCta - 1) / kWarpsPerCta;
     const int grid = (int)std::min<int64_t>(want, 1 << 30);  // capped at residency below
     e = launch_tma_batched(slot.d_tma, n_tma, total_tma, slot.d_queue + 32, border, fmt, Rt,
-                           std::max(grid, 1), h->sm_count, h->d_err, stream, all_fast, bulk);
+                           std::max(grid, 1), h->sm_count, h->d_err, stream, fast, bulk);
     if (e != cudaSuccess) return cuda_fail(h, e);
     h->launches += 1;
   }

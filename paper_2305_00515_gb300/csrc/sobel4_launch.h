@@ -65,16 +65,23 @@ size_t tma_batch_desc_bytes(bool bulk);
 cudaError_t tma_fill_batch_desc(void *out, bool bulk, const uint8_t *src, size_t sp, void *dst,
                                 size_t dp, int32_t H, int32_t W, int R, int64_t item0,
                                 int64_t *items, int32_t thr = 0);
-// d_queue: one zeroed counter; all_fast (every image's items on the fast
-// path with vector stores, see tma_all_fast) selects the lean kernel.
+// Which batched kernel a batch needs: every item of every image on the fast
+// path with vector stores (the lean kernel), every item on the fast path but
+// some destination rows not vector-aligned (the fast kernel with split
+// stores), or some items on the general path (the kernel that carries both).
+// A batch takes the lowest level of its images.
+enum BatchFast : int { kBatchGeneral = 0, kBatchFastSplit = 1, kBatchFastVec = 2 };
+// d_queue: one zeroed counter; fast: the batch's BatchFast level.
 cudaError_t launch_tma_batched(const void *d_descs, int n_img, int64_t total,
                                unsigned int *d_queue, int border, int fmt, int R, int grid,
-                               int sm_count, unsigned int *err, cudaStream_t st, bool all_fast,
+                               int sm_count, unsigned int *err, cudaStream_t st, int fast,
                                bool bulk);
 bool tma_all_fast(int32_t W, int border, int fmt, const uint8_t *src, size_t sp, const void *dst,
                   size_t dp);
 // The same with the staging given (bulk: bulk row copies, else tensor copies).
 bool tma_all_fast_staged(int32_t W, int border, int fmt, bool bulk, const void *dst, size_t dp);
+// One image's BatchFast level under the staging given.
+int tma_fast_level(int32_t W, int border, int fmt, bool bulk, const void *dst, size_t dp);
 // A 2-D tensor map (uint8 or float32 elements) over `base` with row pitch
 // `pitch` bytes, H x W elements, a box of box_w x box_h elements, zero fill,
 // and optionally the 128-byte shared-memory swizzle; `map` points to a

@@ -53,15 +53,17 @@ bool tensor_ok(const uint8_t *src, size_t sp) {
 
 // Which kernel an image needs: every item on the fast path with vector
 // stores (the lean kernel when the width is a multiple of the segment, the
-// ragged-width fast kernel otherwise), none (the general kernel), or anything
-// else (one kernel that carries both paths and the realigned stores, and
-// hands the edge items out first).
-enum Plan { kPlanFast, kPlanFastPart, kPlanGeneral, kPlanAll };
+// ragged-width fast kernel otherwise), every item on the fast path with
+// destination rows that are not vector-aligned (the one-body fast kernel with
+// split stores), none (the general kernel), or anything else (one kernel that
+// carries both paths and the split stores, and hands the edge items out
+// first).
+enum Plan { kPlanFast, kPlanFastPart, kPlanFastRA, kPlanGeneral, kPlanAll };
 
 Plan plan_for(int32_t W, int border, int fmt, int dst_align, int st) {
   const int vec_need = vec_bytes(fmt);
   if (border == kValid || (st == tma::kTensor && border == kConstant0)) {
-    if (dst_align < vec_need) return kPlanAll;
+    if (dst_align < vec_need) return kPlanFastRA;
     return W % tma::kCols == 0 ? kPlanFast : kPlanFastPart;
   }
   if (W < tma::kCols) return kPlanGeneral;
@@ -188,6 +190,7 @@ cudaError_t launch_tma_single(const uint8_t *src, size_t sp, void *dst, size_t d
   const Plan plan = plan_for(W, border, fmt, im.dst_align, staging);
   const int mode = plan == kPlanFast       ? tma::kFastOnly
                    : plan == kPlanFastPart ? tma::kFastPart
+                   : plan == kPlanFastRA   ? tma::kFastRA
                    : plan == kPlanGeneral  ? tma::kGeneralOnly
                                            : tma::kAll;
   (void)cudaGetLastError();  // report this launch only, not an earlier failed call
@@ -209,6 +212,7 @@ cudaError_t launch_tma_single_rgb(const uint8_t *src, size_t sp, void *dst, size
   const Plan plan = plan_for(W, border, fmt, im.dst_align, tma::kBulk);
   const int mode = plan == kPlanFast       ? tma::kFastOnly
                    : plan == kPlanFastPart ? tma::kFastPart
+                   : plan == kPlanFastRA   ? tma::kFastRA
                    : plan == kPlanGeneral  ? tma::kGeneralOnly
                                            : tma::kAll;
   (void)cudaGetLastError();  // report this launch only, not an earlier failed call
@@ -244,10 +248,16 @@ cudaError_t tma_fill_batch_desc(void *out, bool bulk, const uint8_t *src, size_t
 }
 
 bool tma_all_fast_staged(int32_t W, int border, int fmt, bool bulk, const void *dst, size_t dp) {
+  return tma_fast_level(W, border, fmt, bulk, dst, dp) == kBatchFastVec;
+}
+
+int tma_fast_level(int32_t W, int border, int fmt, bool bulk, const void *dst, size_t dp) {
   int a = 1;
   while (a < 16 && (((uintptr_t)dst | (uintptr_t)dp) % (uintptr_t)(2 * a)) == 0) a *= 2;
   const Plan plan = plan_for(W, border, fmt, a, bulk ? tma::kBulk : tma::kTensor);
-  return plan == kPlanFast || plan == kPlanFastPart;
+  return plan == kPlanFast || plan == kPlanFastPart ? kBatchFastVec
+         : plan == kPlanFastRA                      ? kBatchFastSplit
+                                                    : kBatchGeneral;
 }
 
 bool tma_all_fast(int32_t W, int border, int fmt, const uint8_t *src, size_t sp,
@@ -257,7 +267,7 @@ bool tma_all_fast(int32_t W, int border, int fmt, const uint8_t *src, size_t sp,
 
 cudaError_t launch_tma_batched(const void *d_descs, int n_img, int64_t total,
                                unsigned int *d_queue, int border, int fmt, int R, int grid,
-                               int sm_count, unsigned int *err, cudaStream_t st, bool all_fast,
+                               int sm_count, unsigned int *err, cudaStream_t st, int fast,
                                bool bulk) {
   if (R < tma::kUnroll || R % tma::kUnroll || total >= (1ll << 31)) return cudaErrorInvalidValue;
   const void *d = d_descs;
@@ -286,7 +296,8 @@ cudaError_t launch_tma_batched(const void *d_descs, int n_img, int64_t total,
         break;
     }
   };
-  go(all_fast ? tma::kFastOnly : tma::kAll, d_queue);
+  go(fast == kBatchFastVec ? tma::kFastOnly : fast == kBatchFastSplit ? tma::kFastRA : tma::kAll,
+     d_queue);
   return cudaGetLastError();
 }
 

@@ -106,11 +106,14 @@ static_assert(kUnroll == 2 || kUnroll == 4, "the stage length must be a multiple
 #endif
 // Kernel modes: every item, only fast-path items, only the other items, and
 // (single images) only fast-path items of a width that is not a multiple of
-// the segment.  A kernel without the general path needs fewer registers and
-// no spills.
-enum Mode : int { kAll = 0, kFastOnly = 1, kGeneralOnly = 2, kFastPart = 3 };
+// the segment, and only fast-path items with destination rows that are not
+// vector-aligned.  A kernel without the general path needs fewer registers
+// and no spills.
+enum Mode : int { kAll = 0, kFastOnly = 1, kGeneralOnly = 2, kFastPart = 3, kFastRA = 4 };
 template <int MODE>
-__host__ __device__ constexpr bool fast_mode() { return MODE == kFastOnly || MODE == kFastPart; }
+__host__ __device__ constexpr bool fast_mode() {
+  return MODE == kFastOnly || MODE == kFastPart || MODE == kFastRA;
+}
 template <int MODE>
 constexpr int min_ctas() { return fast_mode<MODE>() ? SOBEL4_TMA_FAST_CTAS : SOBEL4_TMA_MIN_CTAS; }
 
@@ -1267,10 +1270,11 @@ __device__ __forceinline__ int strip_rows(const TmaImage &im, int band, int R) {
 // is a large unrolled body, and warps of one SM running several of them at
 // once miss in the instruction cache (measured on ragged batches: 56 % hits
 // with three fast variants live, 98 % with one).  So the batched kernel
-// (ONE) and the single-image kernel of a ragged width (kFastPart) send every
-// fast item through a single body: row checks, stores that stop at column W,
-// and, in a kernel that may meet unaligned destinations (kAll), the realigned
-// stores, which fall through to plain vector stores on an aligned row.  The
+// (ONE) and the single-image kernels of a ragged width (kFastPart) or of
+// unaligned destination rows (kFastRA) send every fast item through a single
+// body: row checks, stores that stop at column W, and, in a kernel that may
+// meet unaligned destinations (kAll, kFastRA), the realigned stores, which
+// fall through to plain vector stores on an aligned row.  The
 // lean single-image kernel (kFastOnly, width a multiple of the segment) keeps
 // the check-free body for full bands and carries no other.
 template <int FMT, int MODE, int ST, bool ONE, bool CW = false>
@@ -1279,8 +1283,8 @@ __device__ __forceinline__ bool run_item(const TmaImage &im, int border, int seg
                                          const Coefs &cw) {
   if (!fast_mode<MODE>() && !fast)
     return tma_item<FMT, true, false, ST, false, false, CW>(im, border, seg, ya, R, lane, cx, err, cw);
-  constexpr bool kRA = MODE == kAll;  // realigned stores possible in this kernel
-  if constexpr (ONE || MODE == kFastPart) {
+  constexpr bool kRA = MODE == kAll || MODE == kFastRA;  // realigned stores possible
+  if constexpr (ONE || MODE == kFastPart || MODE == kFastRA) {
     return tma_item<FMT, false, false, ST, kRA, true, CW>(im, border, seg, ya, R, lane, cx, err, cw);
   } else if constexpr (MODE == kFastOnly) {
     // The host plans this kernel only for widths that are a multiple of kCols.

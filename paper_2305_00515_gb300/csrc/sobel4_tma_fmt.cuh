@@ -49,22 +49,26 @@ int resident_of() {
   do {                                                                              \
     if ((ST_) == tma::kTensor) {                                                    \
       if ((MODE_) == tma::kFastOnly) { CALL(tma::kFastOnly, tma::kTensor); }        \
+      else if ((MODE_) == tma::kFastRA) { CALL(tma::kFastRA, tma::kTensor); }      \
       else if ((MODE_) == tma::kGeneralOnly) { CALL(tma::kGeneralOnly, tma::kTensor); } \
       else { CALL(tma::kAll, tma::kTensor); }                                       \
     } else {                                                                        \
       if ((MODE_) == tma::kFastOnly) { CALL(tma::kFastOnly, tma::kBulk); }          \
+      else if ((MODE_) == tma::kFastRA) { CALL(tma::kFastRA, tma::kBulk); }        \
       else if ((MODE_) == tma::kGeneralOnly) { CALL(tma::kGeneralOnly, tma::kBulk); } \
       else { CALL(tma::kAll, tma::kBulk); }                                         \
     }                                                                               \
   } while (0)
 
-// The single-image kernel has one more mode (fast items of a ragged width)
-// and one more staging (RGB sources).
+// The single-image kernel has two more modes (fast items of a ragged width;
+// fast items with unaligned destination rows) and one more staging (RGB
+// sources).
 #define SOBEL4_TMA_SWITCH_SINGLE(MODE_, ST_, CALL)                                  \
   do {                                                                              \
     if ((ST_) == tma::kRgbBulk) {                                                   \
       if ((MODE_) == tma::kFastOnly) { CALL(tma::kFastOnly, tma::kRgbBulk); }       \
       else if ((MODE_) == tma::kFastPart) { CALL(tma::kFastPart, tma::kRgbBulk); }  \
+      else if ((MODE_) == tma::kFastRA) { CALL(tma::kFastRA, tma::kRgbBulk); }      \
       else if ((MODE_) == tma::kGeneralOnly) { CALL(tma::kGeneralOnly, tma::kRgbBulk); } \
       else { CALL(tma::kAll, tma::kRgbBulk); }                                      \
     } else if ((MODE_) == tma::kFastPart) {                                         \
