@@ -51,6 +51,34 @@ def test_ragged_512_batch_matches_oracle(h):
         assert same_bits(got, want), f"image {i} {img.shape} differs from the oracle"
 
 
+def test_ragged_512_batch_at_the_tuned_configuration():
+    """The configuration the bench times: sobel4_tune_batched on the 512-image
+    batch, then the batch again; every image against the oracle."""
+    imgs = synth.batch_images(512, 1)
+    st, ht = pkg.sobel4_create(0)
+    assert st == 0
+    try:
+        srcs = [Placed(torch, img, img.shape[1], 0) for img in imgs]
+        outs = [Output(torch, *img.shape, "f32", 4 * img.shape[1], 0) for img in imgs]
+        descs = [pkg.Image(s.ptr, s.pitch, o.ptr, o.pitch, *img.shape)
+                 for s, o, img in zip(srcs, outs, imgs)]
+        st, us = pkg.sobel4_tune_batched(ht, descs, 0, 0)
+        assert st == 0 and us > 0
+        for o in outs:  # the tuning runs wrote results; start from other bytes (tight rows)
+            o.buf[o.offset:o.offset + o.H * o.pitch].fill_(0x7F)
+        rc = pkg.sobel4_run_batched(ht, descs, 0, 0, torch.cuda.current_stream().cuda_stream)
+        assert rc == 0, pkg.sobel4_status_string(rc)
+        torch.cuda.synchronize()
+        for i, (img, o) in enumerate(zip(imgs, outs)):
+            got, guards = o.read()
+            assert guards, f"image {i}: write outside its output"
+            want = oracle.sobel4(img, "valid", "f32", threads=NCPU)
+            assert same_bits(got, want), f"image {i} {img.shape} differs at the tuned configuration"
+        assert pkg.sobel4_device_status(ht) == 0
+    finally:
+        pkg.sobel4_destroy(ht)
+
+
 def test_batch_equals_single_runs_all_modes(h):
     rng = np.random.default_rng(3)
     shapes = [(int(a), int(b)) for a, b in rng.integers(3, 400, size=(24, 2))] + [(3, 3), (1000, 7)]
